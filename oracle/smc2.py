@@ -1,0 +1,181 @@
+"""Outer SMC^2 sampler of Sec. III in FP64 numpy (test infrastructure only).
+
+One iteration k, in the order used throughout this project:
+  propose (Eq. proposal; SMC0 random walk or SMC1 Langevin of Sec. III-D)
+  -> CRN particle filter per sample (the C oracle, key (seed^k, seed_hi^i))
+  -> weight (Eq. l_weights with the Langevin L-kernel of Sec. III-E)
+  -> normalise (Eq. normalise_smc2) -> estimate (Eq. realised_estimates)
+  -> recycling statistic l_k (Eq. recycling_I) -> ESS (Eq. ess_smc2)
+  -> systematic resampling when ESS < N/2 (Sec. III-B), sum of weights kept.
+Iteration 1 draws theta from the prior q_1 and weights by pi/q_1, i.e. by the
+estimated likelihood (Eqs. init_sample, init_weights).
+
+Readings (listed with their reasons in the design doc):
+  * Langevin drift F(theta) = 0.5 gamma^2 grad log pi(theta) (the definition of
+    F in Sec. III-D; the later display without the 1/2 is not used);
+  * L(theta_{k-1}|theta_k) = N(theta_{k-1}; theta_k + F(theta_k), gamma^2 I),
+    the one-step leapfrog reversal, so the weight is the MALA ratio used as an
+    importance weight with no accept/reject;
+  * log pi-hat and its gradient travel with each sample through resampling;
+  * the prior is N(prior_mean, diag(prior_std^2)).
+"""
+import numpy as np
+
+from . import pf as _pf, normals as _normals, uniform_open as _uniform_open
+from . import STREAM_OUTER_XI, STREAM_OUTER_NU, SYSTEMATIC
+
+LOG_2PI = np.log(2.0 * np.pi)
+
+
+def log_prior(theta, m, s):
+    z = (theta - m) / s
+    return np.sum(-0.5 * z * z - np.log(s) - 0.5 * LOG_2PI, axis=-1)
+
+
+def grad_log_prior(theta, m, s):
+    return -(theta - m) / (s * s)
+
+
+def log_normal_iso(x, mean, gamma):
+    D = x.shape[-1]
+    d = x - mean
+    return -0.5 * np.sum(d * d, axis=-1) / (gamma * gamma) - D * np.log(gamma) - 0.5 * D * LOG_2PI
+
+
+def _lse(v):
+    m = np.max(v)
+    return m + np.log(np.sum(np.exp(v - m)))
+
+
+def systematic_ancestors(logw, nu, hint=None, band=1e-6):
+    """Systematic ancestors a_i = min{j : c_j >= (i + nu)/N} with follow-mode accounting."""
+    N = logw.shape[0]
+    w = np.exp(logw - _lse(logw))
+    c = np.cumsum(w)
+    c = c / c[-1]
+    c[-1] = 1.0
+    tau = (np.arange(N) + nu) / N
+    own = np.searchsorted(c, tau, side="left")           # first j with c_j >= tau
+    own = np.minimum(own, N - 1)
+    stats = {"near_ties": 0, "tie_followed": 0, "nontie_mismatch": 0}
+    a = own.copy()
+    for i in range(N):
+        j = own[i]
+        if (c[j] - tau[i] < band) or (j > 0 and tau[i] - c[j - 1] <= band):
+            stats["near_ties"] += 1
+        if hint is not None and int(hint[i]) != j:
+            h = int(hint[i])
+            lo = c[h - 1] if h > 0 else 0.0
+            dist = max(tau[i] - c[h], lo - tau[i])
+            if dist < band:
+                stats["tie_followed"] += 1
+            else:
+                stats["nontie_mismatch"] += 1
+            a[i] = h
+    return a, stats
+
+
+def run(family, dx, dy, H, y, N, M, K, gamma, proposal, seed, prior_mean=None, prior_std=None,
+        scheme=SYSTEMATIC, ess_frac=0.5, hints=None, band=1e-6, flag_band=1e-6,
+        outer_band=1e-4, D=None, loglik_grad_fn=None):
+    """Run K iterations; returns (list of per-iteration records, recycled mean).
+
+    proposal: "rw" (SMC0) or "langevin" (SMC1).
+    hints: optional list, per iteration, of dicts with keys pf_anc (N,T,M), pf_flag (N,T),
+      outer_anc (N,), outer_flag (bool): decisions taken elsewhere, followed at near-ties
+      (PF level: |c - tau| < band; outer level: |c - tau| < outer_band).
+    loglik_grad_fn: optional theta -> (log p, grad) used in place of the particle filter
+      (e.g. the exact Kalman likelihood, to test the sampler on its own).
+    """
+    if D is None:
+        D = 3 if family == 1 else 2 * dx + dy
+    m0 = np.zeros(D) if prior_mean is None else np.asarray(prior_mean, dtype=np.float64)
+    s0 = np.ones(D) if prior_std is None else np.asarray(prior_std, dtype=np.float64)
+    seed = int(seed)
+    records = []
+
+    def run_pfs(theta, k, hint):
+        ll = np.zeros(N)
+        g = np.zeros((N, D))
+        agg = {}
+        if loglik_grad_fn is not None:
+            for i in range(N):
+                ll[i], g[i] = loglik_grad_fn(theta[i])
+            return ll, g, agg
+        for i in range(N):
+            ha = hf = None
+            if hint is not None:
+                ha = hint["pf_anc"][i]
+                hf = hint["pf_flag"][i]
+            r = _pf(family, dx, dy, H, theta[i], y, M, seed, k, i, scheme=scheme,
+                    ess_frac=ess_frac, want_grad=True, hint_anc=ha, hint_flag=hf,
+                    band=band, flag_band=flag_band, want_tape=False)
+            ll[i] = r["loglik"]
+            g[i] = r["grad"]
+            for key, v in r["stats"].items():
+                agg[key] = agg.get(key, 0) + v
+        return ll, g, agg
+
+    theta = np.zeros((N, D))
+    logw = np.zeros(N)
+    logpi = np.zeros(N)
+    gradpi = np.zeros((N, D))
+    loglik = np.zeros(N)
+    for k in range(1, K + 1):
+        hint = hints[k - 1] if hints is not None else None
+        xi = np.stack([_normals(seed, k, i, 0, STREAM_OUTER_XI, D) for i in range(N)])
+        if k == 1:
+            # theta_1 ~ q_1 = prior (Eq. init_sample); w_1 = pi/q_1 = p-hat(y|theta) (Eq. init_weights)
+            theta_new = m0 + s0 * xi
+            ll_new, g_new, pfstats = run_pfs(theta_new, k, hint)
+            lp_new = log_prior(theta_new, m0, s0) + ll_new
+            gp_new = grad_log_prior(theta_new, m0, s0) + g_new
+            logw = ll_new.copy()
+        else:
+            if proposal == "langevin":
+                drift = 0.5 * gamma * gamma * gradpi
+            else:
+                drift = np.zeros_like(gradpi)
+            theta_new = theta + drift + gamma * xi
+            ll_new, g_new, pfstats = run_pfs(theta_new, k, hint)
+            lp_new = log_prior(theta_new, m0, s0) + ll_new
+            gp_new = grad_log_prior(theta_new, m0, s0) + g_new
+            if proposal == "langevin":
+                drift_new = 0.5 * gamma * gamma * gp_new
+            else:
+                drift_new = np.zeros_like(gp_new)
+            log_q = log_normal_iso(theta_new, theta + drift, gamma)     # q(theta_k | theta_{k-1})
+            log_L = log_normal_iso(theta, theta_new + drift_new, gamma)  # L(theta_{k-1} | theta_k)
+            logw = logw + lp_new - logpi + log_L - log_q                 # Eq. l_weights
+        theta, logpi, gradpi, loglik = theta_new, lp_new, gp_new, ll_new
+
+        # normalise, estimate, recycling statistic, ESS
+        L = _lse(logw)
+        wn = np.exp(logw - L)
+        mean = wn @ theta
+        ess = 1.0 / np.sum(wn * wn)
+        l_k = np.exp(2.0 * _lse(logw) - _lse(2.0 * logw))        # (sum w)^2 / sum w^2
+        rec = {"k": k, "ess": float(ess), "l_k": float(l_k), "mean": mean.copy(),
+               "theta": theta.copy(), "logw": logw.copy(), "loglik": loglik.copy(),
+               "grad": gradpi.copy(), "pf_stats": pfstats, "resampled": False,
+               "outer_stats": {}}
+        own_flag = ess < N / 2.0
+        flag = own_flag
+        if hint is not None and "outer_flag" in hint and bool(hint["outer_flag"]) != own_flag:
+            rec["outer_stats"]["flag_disagree"] = 1
+            flag = bool(hint["outer_flag"])
+        if flag:
+            nu = _uniform_open(seed, k, 0, 0, STREAM_OUTER_NU)
+            hint_a = hint["outer_anc"] if (hint is not None and "outer_anc" in hint) else None
+            a, st = systematic_ancestors(logw, nu, hint_a, band=outer_band)
+            rec["outer_stats"].update(st)
+            rec["ancestors"] = a
+            theta, logpi, gradpi, loglik = theta[a], logpi[a], gradpi[a], loglik[a]
+            logw = np.full(N, L - np.log(N))
+            rec["resampled"] = True
+        records.append(rec)
+
+    lks = np.array([r["l_k"] for r in records])
+    ck = lks / lks.sum()                                             # Eq. opt_recycling_constant
+    recycled = sum(c * r["mean"] for c, r in zip(ck, records))       # Sec. III-C
+    return records, recycled
