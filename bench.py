@@ -1,0 +1,345 @@
+"""Benchmark of one SMC^2 iteration of the CRN particle filter on synthetic data.
+
+A step is one pass of the whole hot path: the outer proposal (Langevin), one CRN
+particle filter per sample with its reverse-time adjoint, the L-kernel weights,
+normalisation, ESS, estimate, recycling statistic and resampling.  The default
+workload is the differentiable batched linear-Gaussian filter (d_x=4, d_y=2,
+D=10, T=250, N=1024 samples, M=1024 particles).
+
+Metric: fwd+grad CRN-PF particle-steps/s = N*M*T per step / step time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload lg4]
+
+--impl reference times the FP64 CPU oracle (the plain reference implementation
+of the same method) on the host cores on a bounded sample of the same workload.
+Prints one JSON line on rank 0.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fwd+grad CRN-PF particle-steps/s"
+UNIT = "particle-steps/s"
+
+# Algorithmic FP32/INT32 lane-operations per particle-step (forward + adjoint), counted
+# from the algorithm at source level for each model shape ("Roofline").
+ALG_OPS = {"lg1": 60 + 24, "lg4": 94 + 47, "sv": 64 + 30, "lg16": 4 * 84 + 16 * 25 + 16 * 12}
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="lg4")
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU baseline sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def _dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.th = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.th:
+            self.th.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle (baseline / reference arm)
+
+def _oracle_filter(args):
+    import oracle
+    fam, dx, dy, H, theta, y, M, seed, it, row = args
+    r = oracle.pf(fam, dx, dy, H, theta, y, M, seed, it, row, want_tape=False)
+    return r["loglik"]
+
+
+def cpu_oracle_rate(w, budget_s, procs=None):
+    """Time the oracle's filter forward + forward-mode gradient on a bounded sample of the
+    workload's filters with a spawn pool over all host cores; returns (rate, info)."""
+    import multiprocessing as mp
+
+    import numpy as np
+    from paper_2407_17296_gb300 import workloads
+    procs = procs or os.cpu_count() or 1
+    theta = workloads.thetas_near(w, w.N, 0.05, seed=99)
+    H = None if w.H is None else np.asarray(w.H, dtype=np.float64)
+    # calibrate on one filter, then size the sample to the budget
+    t0 = time.perf_counter()
+    _oracle_filter((w.family, w.dx, w.dy, H, theta[0], w.y, w.M, w.seed, 2, 0))
+    one = time.perf_counter() - t0
+    n = int(max(procs, min(w.N, budget_s * procs / max(one, 1e-6))))
+    n = max(procs, (n // procs) * procs)
+    jobs = [(w.family, w.dx, w.dy, H, theta[i % w.N], w.y, w.M, w.seed, 2, i % w.N) for i in range(n)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs) as pool:
+        pool.map(_oracle_filter, jobs[:procs])  # start-up outside the timing
+        t0 = time.perf_counter()
+        pool.map(_oracle_filter, jobs, chunksize=1)
+        dt = time.perf_counter() - t0
+    rate = n * w.M * w.T / dt
+    info = {"filters": n, "of": w.N, "seconds": dt, "single_filter_s": one}
+    return rate, procs, info
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_gpu(a, rank, world, local):
+    import numpy as np
+    import torch
+    from paper_2407_17296_gb300 import binding, workloads
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    w = workloads.ALL[a.workload]()
+    # weak scaling: every rank runs its own independent job (own seed), no data-path collective
+    w.seed = w.seed + 1000 * rank
+    binding.load()
+    stream = torch.cuda.Stream(device=dev)
+    cfg = binding.config_for(w, stream=stream.cuda_stream)
+    ppt, kc = binding.ctypes.c_int(0), binding.ctypes.c_int(0)
+    binding.check(binding.load().smc2_autotune(binding.ctypes.byref(cfg), binding.ctypes.byref(ppt),
+                                               binding.ctypes.byref(kc)), "smc2_autotune")
+    cfg = binding.config_for(w, stream=stream.cuda_stream, particles_per_thread=ppt.value,
+                             ckpt_every=kc.value)
+    h = binding.Handle(cfg)
+    ps_per_step = w.N * w.M * w.T
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(a.warmup):
+        h.step(want_means=False)
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    launches0 = binding.kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    stats = []
+    for _ in range(a.steps):
+        stats.append(h.step(want_means=False))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = binding.kernel_launches() - launches0
+    ms_total = ev0.elapsed_time(ev1)
+
+    # dominant kernels (filter forward + adjoint): pf_loglik_grad on the same stream and inputs
+    theta, _ = h.samples()
+    th = torch.tensor(theta, dtype=torch.float64, device=dev)
+    ll = torch.empty(w.N, dtype=torch.float64, device=dev)
+    g = torch.empty(w.N, w.D, dtype=torch.float64, device=dev)
+    with torch.cuda.stream(stream):
+        h.pf_loglik_grad(th, 1, ll, g)
+        reps = max(3, a.steps // 2)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for r in range(reps):
+            h.pf_loglik_grad(th, 2 + r, ll, g)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    pf_ms = e0.elapsed_time(e1) / reps
+
+    # end to end through the C ABI with host buffers: observations in, stats + samples out
+    y_host = torch.tensor(w.y, dtype=torch.float32).pin_memory().numpy()
+    th_host = np.zeros((w.N, w.D))
+    lw_host = np.zeros(w.N)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        h.set_observations(y_host)
+        h.step(want_means=True)
+        binding.check(binding.load().smc2_get_samples(h.h, binding._ptr(th_host), binding._ptr(lw_host)),
+                      "smc2_get_samples")
+    e2e_s = time.perf_counter() - t0
+
+    times = torch.tensor([ms_total, e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(times, op=dist.ReduceOp.MAX)
+    ms_total, e2e_s = float(times[0]), float(times[1])
+    ms_step = ms_total / a.steps
+    value = world * ps_per_step * a.steps / (ms_total / 1e3)
+    e2e_value = world * ps_per_step * a.steps / e2e_s
+    h.close()
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return None
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    props = torch.cuda.get_device_properties(dev)
+    sm_count = props.multi_processor_count
+    max_mhz = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
+    peak_tops = sm_count * 128 * max_mhz * 1e6 / 1e12
+    achieved_tops = ALG_OPS.get(w.name, 0) * ps_per_step / (pf_ms / 1e3) / 1e12
+    traffic = None
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": a.steps,
+        "warmup": a.warmup,
+        "ms_per_step": ms_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded simulation of the model; no dataset)",
+        "config": {"workload": f"{w.name}: LG-diag d_x={w.dx} d_y={w.dy}" if w.family == 0 else f"{w.name}: SV",
+                   "N": w.N, "M": w.M, "T": w.T, "D": w.D, "proposal": w.proposal, "gamma": w.gamma,
+                   "particles_per_thread": ppt.value, "ckpt_every": kc.value,
+                   "step": "one SMC2 iteration: propose, N filters fwd+adjoint, L-kernel weights, resample",
+                   "l2": "inputs larger than L2 (particle trajectory of several GB written and read per step)",
+                   "parallelism": f"replicas x{world} (independent jobs)"},
+        "smc2_iters_per_s": 1e3 / ms_step,
+        "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s",
+                     "frac": achieved_tops / peak_tops if peak_tops else None, "traffic": traffic,
+                     "kernel": "pf_forward_kernel + pf_backward_kernel",
+                     "kernel_ms": pf_ms, "ops_per_particle_step": ALG_OPS.get(w.name),
+                     "peak_basis": f"{sm_count} SMs x 128 FP32/INT32 lanes x {max_mhz:.0f} MHz"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(w.T * w.dy * 4),
+                "d2h_bytes_per_step": int(w.N * w.D * 8 + w.N * 8 + 8 * (6 + 2 * w.D))},
+        "clocks": clocks,
+        "gpu_launches": int(launches),
+    }
+    if not a.no_cpu_baseline:
+        rate, cores, info = cpu_oracle_rate(w, a.cpu_seconds)
+        out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": f"{info['filters']} of {info['of']} filters of one iteration "
+                                         f"(forward + forward-mode gradient, FP64), spawn pool, "
+                                         f"{info['seconds']:.1f} s"}
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return out
+
+
+def run_reference(a, rank, world):
+    """The CPU oracle as the reference arm: each step a bounded sample of the workload."""
+    if rank != 0:
+        return None
+    from paper_2407_17296_gb300 import workloads
+    w = workloads.ALL[a.workload]()
+    per = max(2.0, a.cpu_seconds / max(1, a.steps + a.warmup))
+    for _ in range(a.warmup):
+        cpu_oracle_rate(w, per / 4)
+    rates, infos = [], []
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        r, cores, info = cpu_oracle_rate(w, per)
+        rates.append(r)
+        infos.append(info)
+    wall = time.perf_counter() - t0
+    value = statistics.mean(rates)
+    ms_step = 1e3 * w.N * w.M * w.T / value
+    return {
+        "impl": "reference",
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded simulation of the model; no dataset)",
+        "config": {"workload": w.name, "N": w.N, "M": w.M, "T": w.T, "D": w.D},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"per step {infos[0]['filters']} of {w.N} filters (forward + gradient), "
+                                   f"{wall:.1f} s total"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    a = _args()
+    rank, world, local = _dist_env()
+    if a.impl == "reference":
+        out = run_reference(a, rank, world)
+    else:
+        out = run_gpu(a, rank, world, local)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

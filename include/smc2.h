@@ -1,0 +1,211 @@
+/*
+ * smc2.h -- C ABI of the GB300 CRN particle filter and gradient-enhanced SMC^2
+ * (arXiv 2407.17296, "Enhanced SMC^2: Leveraging Gradient Information from
+ * Differentiable Particle Filters Within Langevin Proposals").
+ *
+ * Plain C99.  No C++ or torch types cross this boundary; device pointers are
+ * plain addresses in the current CUDA context and streams are passed as
+ * `void*` holding a cudaStream_t.
+ *
+ * Error convention.  Every function returns an int: SMC2_OK (0), SMC2_PENDING
+ * (1, only smc2_poll) or a negative SMC2_E_* code.  smc2_last_error() returns a
+ * thread-local message describing the last failure on the calling thread.  No
+ * exception crosses the ABI; device-side trouble is reported through status
+ * words, never through a device fault.
+ *
+ * Notation follows the paper: N samples theta (the outer SMC sampler, Sec. III),
+ * M particles x per filter (N_x in Sec. II), T observations y_{1:T}, D = |theta|.
+ */
+#ifndef SMC2_H
+#define SMC2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- codes */
+#define SMC2_OK 0
+#define SMC2_PENDING 1
+#define SMC2_E_INVAL (-1)    /* bad argument or unsupported configuration */
+#define SMC2_E_NOMEM (-2)    /* device memory or HBM budget exhausted */
+#define SMC2_E_CUDA (-3)     /* a CUDA runtime call failed */
+#define SMC2_E_TIMEOUT (-4)  /* a bounded wait expired */
+#define SMC2_E_NOTFOUND (-5) /* unknown job id */
+#define SMC2_E_BUSY (-6)     /* resource in use */
+
+/* State-space model families (Sec. II, Eqs. xt and yt).
+ *  SMC2_LG_DIAG: theta = (a[d_x], log q[d_x], log r[d_y]), D = 2 d_x + d_y;
+ *    x_0 ~ N(0, I), x_t = diag(a) x_{t-1} + diag(q) v_t, y_t = H x_t + diag(r) w_t.
+ *    Supported shapes (d_x, d_y): (1,1), (4,2), (16,16) with H = identity.
+ *  SMC2_SV: theta = (mu, atanh phi, log sigma), D = 3, d_x = d_y = 1;
+ *    x_0 = mu + sigma/sqrt(1-phi^2) eps, x_t = mu + phi (x_{t-1} - mu) + sigma eta_t,
+ *    y_t = exp(x_t / 2) eps_t. */
+enum { SMC2_LG_DIAG = 0, SMC2_SV = 1 };
+/* Outer proposals (Sec. III-D): SMC0 random walk, SMC1 Langevin. */
+enum { SMC2_RW = 0, SMC2_LANGEVIN = 1 };
+/* Particle-filter resampler (Sec. II-B, App. B). */
+enum { SMC2_SYSTEMATIC = 0, SMC2_MULTINOMIAL = 1 };
+
+typedef struct smc2_config {
+    uint32_t struct_size;       /* sizeof(smc2_config): versioning */
+    int32_t model_family;       /* SMC2_LG_DIAG or SMC2_SV */
+    int32_t d_x, d_y;
+    const float* H;             /* host, d_y x d_x row-major; NULL = identity; copied */
+    const float* y;             /* T x d_y row-major observations; copied */
+    int32_t y_on_device;        /* nonzero: y is a device pointer */
+    int32_t T, N, M, D;         /* D must equal the family's parameter count */
+    const double* prior_mean;   /* host [D] or NULL (zeros); prior N(mean, diag(std^2)) */
+    const double* prior_std;    /* host [D] or NULL (ones) */
+    int32_t proposal;           /* SMC2_RW or SMC2_LANGEVIN */
+    double gamma;               /* step size, Gamma = gamma^2 I */
+    int32_t K_iters;            /* iterations for a served job (smc2_submit) */
+    int32_t pf_resample;        /* SMC2_SYSTEMATIC or SMC2_MULTINOMIAL */
+    float ess_frac;             /* resample the filter when ESS < ess_frac * M (0.5 in the paper) */
+    uint64_t seed;              /* CRN seed: key (seed_lo ^ k, seed_hi ^ i) per sample i, iteration k */
+    int32_t ckpt_every;         /* adjoint checkpoint interval in steps; 0 = automatic, 1 = store all */
+    int32_t particles_per_thread; /* 0 = automatic (autotuned), else 1, 2, 4 or 8 */
+    void* stream;               /* cudaStream_t for all work of the handle; NULL = a private stream */
+} smc2_config;
+
+/* Fill defaults: struct_size, ess_frac 0.5, K_iters 10, systematic, Langevin, gamma 0.1. */
+void smc2_config_init(smc2_config* cfg);
+
+typedef struct smc2_handle smc2_handle;
+
+/* Per-iteration statistics of smc2_step (Sec. III-A..C). */
+typedef struct smc2_stats {
+    int32_t k;                /* iteration just completed, 1-based */
+    int32_t resampled;        /* outer resampling happened at the end of k */
+    double ess;               /* N_eff of the outer weights before resampling (Eq. ess_smc2) */
+    double l_k;               /* recycling statistic (Eq. recycling_I) */
+    double max_logw;          /* largest outer log-weight (diagnostic) */
+    double* mean;             /* caller host storage [D] or NULL: f~_k = sum_i w~_i theta_i (Eq. realised_estimates) */
+    double* recycled_mean;    /* caller host storage [D] or NULL: sum_k c_k f~_k over iterations so far (Sec. III-C) */
+} smc2_stats;
+
+/*
+ * smc2_create: validate cfg, copy y and H, allocate the device-resident state of
+ * one inference job (theta [N][D], log-weights, log pi-hat, gradients, particle
+ * checkpoints and the ancestor tape).  The library owns every allocation it makes.
+ * Errors: SMC2_E_INVAL (bad or unsupported cfg), SMC2_E_NOMEM, SMC2_E_CUDA.
+ * Problem statement: Sec. II (f, g, y_{1:T}, M) and Sec. III (prior, N, step size).
+ */
+int smc2_create(const smc2_config* cfg, smc2_handle** out);
+
+/*
+ * pf_loglik_grad: the hot path.  For rows i = 0..n-1 of theta_dev ([n][D] row-major
+ * FP64, device) run one CRN particle filter each with Philox key
+ * (seed_lo ^ iter, seed_hi ^ i) and write log p-hat(y|theta_i) to loglik_dev[i]
+ * (FP64, device; the log of Eq. likelihood_pf_) and, if grad_dev is not NULL, its
+ * gradient d log p-hat / d theta (Eq. dloglik, App. A/B, computed by a reverse-time
+ * adjoint) to grad_dev[i*D..] (FP64, device).  A filter whose weights all vanish
+ * or overflow reports log p-hat = -inf and a zero gradient.
+ * Caller owns all buffers; n <= N of the handle.  Asynchronous on the handle's
+ * stream.  Errors: SMC2_E_INVAL, SMC2_E_CUDA.
+ */
+int pf_loglik_grad(smc2_handle* h, const double* theta_dev, int n, uint32_t iter,
+                   double* loglik_dev, double* grad_dev);
+
+/* As pf_loglik_grad with the Philox row index starting at row0 (rows row0..row0+n-1),
+ * for callers that shard the N samples of one iteration across launches or devices. */
+int pf_loglik_grad_rows(smc2_handle* h, const double* theta_dev, int n, uint32_t iter,
+                        uint32_t row0, double* loglik_dev, double* grad_dev);
+
+/* As pf_loglik_grad with HOST buffers: copies theta in, runs, copies loglik/grad out,
+ * and synchronises the handle's stream before returning. */
+int pf_loglik_grad_host(smc2_handle* h, const double* theta_host, int n, uint32_t iter,
+                        double* loglik_host, double* grad_host);
+
+/*
+ * smc2_step: one SMC^2 iteration k (k counts from 1 per handle).
+ *  k = 1: theta ~ prior (Eq. init_sample), PF, w = pi/q_1 (Eq. init_weights).
+ *  k > 1: Langevin or random-walk move (Sec. III-D), PF at the new theta, weight with
+ *         the L-kernel (Eq. l_weights, Sec. III-E).
+ *  then normalise, estimate, recycling statistic, ESS and, if N_eff < N/2,
+ *  systematic resampling (Sec. III-A..C).  Fills *out (may be NULL) on the host:
+ *  this call synchronises the handle's stream.
+ * Errors: SMC2_E_INVAL, SMC2_E_CUDA.
+ */
+int smc2_step(smc2_handle* h, smc2_stats* out);
+
+/* Copy the current samples to host: theta_host [N][D] and logw_host [N] (either may be NULL). */
+int smc2_get_samples(smc2_handle* h, double* theta_host, double* logw_host);
+
+/* Copy per-sample log-likelihood estimates and gradients of the log posterior to host
+ * (loglik_host [N], gradpi_host [N][D]; either may be NULL). */
+int smc2_get_state(smc2_handle* h, double* loglik_host, double* gradpi_host);
+
+/*
+ * smc2_get_trace: decisions taken during the last particle-filter launch and the last
+ * outer step, for verification: pf_anc [N][T][M] (ancestor of particle i before step
+ * t, row t-1; rows of steps without resampling are unspecified), pf_flag [N][T]
+ * (1 if the filter resampled before step t), outer_anc [N] (ancestor of each sample if
+ * the last smc2_step resampled).  Any pointer may be NULL.  Host buffers.
+ */
+int smc2_get_trace(smc2_handle* h, uint16_t* pf_anc, uint8_t* pf_flag, int32_t* outer_anc,
+                   int32_t* outer_resampled);
+
+/* Replace the observations (T x d_y FP32, host) of an existing handle; the copy is
+ * stream-ordered on the handle's stream. */
+int smc2_set_observations(smc2_handle* h, const float* y_host);
+
+/* Bytes of device memory the handle holds (the footprint used for admission). */
+int smc2_footprint(const smc2_config* cfg, size_t* bytes);
+
+int smc2_destroy(smc2_handle* h);
+
+/* Launch-configuration choice for a model shape (the autotuner): particles per thread
+ * and checkpoint interval picked by timing candidates on the current device once per
+ * (family, d_x, d_y, M, T) and cached in-process.  Writes the choice to *ppt and *ckpt. */
+int smc2_autotune(const smc2_config* cfg, int* ppt, int* ckpt);
+
+/* Number of kernels this library launched since load (a device-work counter). */
+uint64_t smc2_kernel_launches(void);
+
+const char* smc2_last_error(void);
+
+/* ---------------------------------------------------------------- serving */
+
+typedef struct smc2_server smc2_server;
+
+typedef struct smc2_result {
+    int32_t status;            /* SMC2_OK or an error code of the job */
+    int32_t K;                 /* iterations run */
+    double latency_s;          /* submit -> completion wall time */
+    double queue_s;            /* submit -> admission wall time */
+    double* theta;             /* caller host storage [N][D] or NULL: final samples */
+    double* logw;              /* caller host storage [N] or NULL: final log-weights */
+    double* recycled_mean;     /* caller host storage [D] or NULL */
+} smc2_result;
+
+/*
+ * smc2_server_create: a continuous-batching request loop on the current device.
+ * Jobs are admitted while their footprint (smc2_footprint) fits hbm_budget bytes and
+ * fewer than max_active jobs run; each admitted job keeps its state on the device and
+ * advances one SMC^2 iteration at a time on its own stream, so iterations of
+ * different jobs overlap on the GPU.  A worker thread drives the loop.
+ */
+int smc2_server_create(size_t hbm_budget, int max_active, smc2_server** out);
+
+/* Queue a job (cfg and y are copied; cfg->K_iters iterations).  Returns immediately.
+ * SMC2_E_NOMEM only if the job can never fit the budget. */
+int smc2_submit(smc2_server* s, const smc2_config* cfg, uint64_t* job_id);
+
+/* SMC2_PENDING while queued or running; SMC2_OK once finished (fills *out and
+ * releases the job's result); SMC2_E_NOTFOUND for unknown ids. */
+int smc2_poll(smc2_server* s, uint64_t job_id, smc2_result* out);
+
+/* Drop a job that has not finished.  SMC2_E_NOTFOUND for unknown ids. */
+int smc2_cancel(smc2_server* s, uint64_t job_id);
+
+/* Stop the worker (running jobs are cancelled) and free everything. */
+int smc2_server_destroy(smc2_server* s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SMC2_H */

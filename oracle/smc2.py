@@ -98,10 +98,11 @@ def run(family, dx, dy, H, y, N, M, K, gamma, proposal, seed, prior_mean=None, p
         ll = np.zeros(N)
         g = np.zeros((N, D))
         agg = {}
+        rows = []
         if loglik_grad_fn is not None:
             for i in range(N):
                 ll[i], g[i] = loglik_grad_fn(theta[i])
-            return ll, g, agg
+            return ll, g, agg, rows
         for i in range(N):
             ha = hf = None
             if hint is not None:
@@ -112,9 +113,10 @@ def run(family, dx, dy, H, y, N, M, K, gamma, proposal, seed, prior_mean=None, p
                     band=band, flag_band=flag_band, want_tape=False)
             ll[i] = r["loglik"]
             g[i] = r["grad"]
+            rows.append(r["stats"])
             for key, v in r["stats"].items():
                 agg[key] = agg.get(key, 0) + v
-        return ll, g, agg
+        return ll, g, agg, rows
 
     theta = np.zeros((N, D))
     logw = np.zeros(N)
@@ -127,7 +129,7 @@ def run(family, dx, dy, H, y, N, M, K, gamma, proposal, seed, prior_mean=None, p
         if k == 1:
             # theta_1 ~ q_1 = prior (Eq. init_sample); w_1 = pi/q_1 = p-hat(y|theta) (Eq. init_weights)
             theta_new = m0 + s0 * xi
-            ll_new, g_new, pfstats = run_pfs(theta_new, k, hint)
+            ll_new, g_new, pfstats, pfrows = run_pfs(theta_new, k, hint)
             lp_new = log_prior(theta_new, m0, s0) + ll_new
             gp_new = grad_log_prior(theta_new, m0, s0) + g_new
             logw = ll_new.copy()
@@ -137,7 +139,7 @@ def run(family, dx, dy, H, y, N, M, K, gamma, proposal, seed, prior_mean=None, p
             else:
                 drift = np.zeros_like(gradpi)
             theta_new = theta + drift + gamma * xi
-            ll_new, g_new, pfstats = run_pfs(theta_new, k, hint)
+            ll_new, g_new, pfstats, pfrows = run_pfs(theta_new, k, hint)
             lp_new = log_prior(theta_new, m0, s0) + ll_new
             gp_new = grad_log_prior(theta_new, m0, s0) + g_new
             if proposal == "langevin":
@@ -157,7 +159,8 @@ def run(family, dx, dy, H, y, N, M, K, gamma, proposal, seed, prior_mean=None, p
         l_k = np.exp(2.0 * _lse(logw) - _lse(2.0 * logw))        # (sum w)^2 / sum w^2
         rec = {"k": k, "ess": float(ess), "l_k": float(l_k), "mean": mean.copy(),
                "theta": theta.copy(), "logw": logw.copy(), "loglik": loglik.copy(),
-               "grad": gradpi.copy(), "pf_stats": pfstats, "resampled": False,
+               "grad": gradpi.copy(), "pf_stats": pfstats, "pf_stats_rows": pfrows,
+               "resampled": False,
                "outer_stats": {}}
         own_flag = ess < N / 2.0
         flag = own_flag

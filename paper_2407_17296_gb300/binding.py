@@ -1,0 +1,291 @@
+"""Thin ctypes binding of the C ABI in ``include/smc2.h`` (argument marshalling only).
+
+Every computation runs in the CUDA library ``libsmc2.so``; this module only
+converts Python/torch arguments into plain pointers and sizes.  torch supplies
+device memory and streams.  If the library was not built, ``load()`` raises:
+there is no CPU fallback.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsmc2.so")
+
+SMC2_OK = 0
+SMC2_PENDING = 1
+ERRORS = {-1: "SMC2_E_INVAL", -2: "SMC2_E_NOMEM", -3: "SMC2_E_CUDA", -4: "SMC2_E_TIMEOUT",
+          -5: "SMC2_E_NOTFOUND", -6: "SMC2_E_BUSY"}
+LG_DIAG, SV = 0, 1
+RW, LANGEVIN = 0, 1
+SYSTEMATIC, MULTINOMIAL = 0, 1
+
+# every symbol include/smc2.h declares
+EXPORTS = ("smc2_config_init", "smc2_create", "pf_loglik_grad", "pf_loglik_grad_rows",
+           "pf_loglik_grad_host", "smc2_step", "smc2_get_samples", "smc2_get_state",
+           "smc2_get_trace", "smc2_set_observations", "smc2_footprint", "smc2_destroy",
+           "smc2_autotune", "smc2_kernel_launches", "smc2_last_error", "smc2_server_create",
+           "smc2_submit", "smc2_poll", "smc2_cancel", "smc2_server_destroy")
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("struct_size", ctypes.c_uint32),
+        ("model_family", ctypes.c_int32),
+        ("d_x", ctypes.c_int32),
+        ("d_y", ctypes.c_int32),
+        ("H", ctypes.c_void_p),
+        ("y", ctypes.c_void_p),
+        ("y_on_device", ctypes.c_int32),
+        ("T", ctypes.c_int32),
+        ("N", ctypes.c_int32),
+        ("M", ctypes.c_int32),
+        ("D", ctypes.c_int32),
+        ("prior_mean", ctypes.c_void_p),
+        ("prior_std", ctypes.c_void_p),
+        ("proposal", ctypes.c_int32),
+        ("gamma", ctypes.c_double),
+        ("K_iters", ctypes.c_int32),
+        ("pf_resample", ctypes.c_int32),
+        ("ess_frac", ctypes.c_float),
+        ("seed", ctypes.c_uint64),
+        ("ckpt_every", ctypes.c_int32),
+        ("particles_per_thread", ctypes.c_int32),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("k", ctypes.c_int32),
+        ("resampled", ctypes.c_int32),
+        ("ess", ctypes.c_double),
+        ("l_k", ctypes.c_double),
+        ("max_logw", ctypes.c_double),
+        ("mean", ctypes.c_void_p),
+        ("recycled_mean", ctypes.c_void_p),
+    ]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int32),
+        ("K", ctypes.c_int32),
+        ("latency_s", ctypes.c_double),
+        ("queue_s", ctypes.c_double),
+        ("theta", ctypes.c_void_p),
+        ("logw", ctypes.c_void_p),
+        ("recycled_mean", ctypes.c_void_p),
+    ]
+
+
+class Smc2Error(RuntimeError):
+    pass
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libsmc2.so and declare its signatures.  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise Smc2Error(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    vp, i32, u32, u64, dp = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p
+    sig = {
+        "smc2_config_init": (None, [ctypes.POINTER(Config)]),
+        "smc2_create": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(vp)]),
+        "pf_loglik_grad": (ctypes.c_int, [vp, dp, ctypes.c_int, u32, dp, dp]),
+        "pf_loglik_grad_rows": (ctypes.c_int, [vp, dp, ctypes.c_int, u32, u32, dp, dp]),
+        "pf_loglik_grad_host": (ctypes.c_int, [vp, dp, ctypes.c_int, u32, dp, dp]),
+        "smc2_step": (ctypes.c_int, [vp, ctypes.POINTER(Stats)]),
+        "smc2_get_samples": (ctypes.c_int, [vp, dp, dp]),
+        "smc2_get_state": (ctypes.c_int, [vp, dp, dp]),
+        "smc2_get_trace": (ctypes.c_int, [vp, vp, vp, vp, vp]),
+        "smc2_set_observations": (ctypes.c_int, [vp, vp]),
+        "smc2_footprint": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_size_t)]),
+        "smc2_destroy": (ctypes.c_int, [vp]),
+        "smc2_autotune": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_int)]),
+        "smc2_kernel_launches": (u64, []),
+        "smc2_last_error": (ctypes.c_char_p, []),
+        "smc2_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(vp)]),
+        "smc2_submit": (ctypes.c_int, [vp, ctypes.POINTER(Config), ctypes.POINTER(u64)]),
+        "smc2_poll": (ctypes.c_int, [vp, u64, ctypes.POINTER(Result)]),
+        "smc2_cancel": (ctypes.c_int, [vp, u64]),
+        "smc2_server_destroy": (ctypes.c_int, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    c = Config()
+    lib.smc2_config_init(ctypes.byref(c))
+    if c.struct_size != ctypes.sizeof(Config):
+        raise Smc2Error(f"smc2_config layout mismatch: C {c.struct_size} vs ctypes {ctypes.sizeof(Config)}")
+    _lib = lib
+    return lib
+
+
+def check(rc: int, what: str = "") -> int:
+    if rc < 0:
+        msg = load().smc2_last_error().decode(errors="replace")
+        raise Smc2Error(f"{what}: {ERRORS.get(rc, rc)}: {msg}")
+    return rc
+
+
+def last_error() -> str:
+    return load().smc2_last_error().decode(errors="replace")
+
+
+def kernel_launches() -> int:
+    return int(load().smc2_kernel_launches())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return ctypes.c_void_p(t.data_ptr())
+    return t.ctypes.data_as(ctypes.c_void_p)
+
+
+def make_config(family, dx, dy, T, N, M, D, y, H=None, prior_mean=None, prior_std=None,
+                proposal=LANGEVIN, gamma=0.1, K_iters=10, pf_resample=SYSTEMATIC, ess_frac=0.5,
+                seed=777, ckpt_every=0, particles_per_thread=0, stream=None, y_on_device=False):
+    """Build a Config; numpy arrays referenced by it are kept alive on the returned object."""
+    import numpy as np
+    lib = load()
+    c = Config()
+    lib.smc2_config_init(ctypes.byref(c))
+    keep = []
+    c.model_family, c.d_x, c.d_y = int(family), int(dx), int(dy)
+    c.T, c.N, c.M, c.D = int(T), int(N), int(M), int(D)
+    if y_on_device:
+        c.y = ctypes.c_void_p(y.data_ptr()).value
+        c.y_on_device = 1
+        keep.append(y)
+    else:
+        ya = np.ascontiguousarray(np.asarray(y, dtype=np.float32))
+        keep.append(ya)
+        c.y = ya.ctypes.data
+    if H is not None:
+        Ha = np.ascontiguousarray(np.asarray(H, dtype=np.float32))
+        keep.append(Ha)
+        c.H = Ha.ctypes.data
+    for name, arr in (("prior_mean", prior_mean), ("prior_std", prior_std)):
+        if arr is not None:
+            a = np.ascontiguousarray(np.asarray(arr, dtype=np.float64))
+            keep.append(a)
+            setattr(c, name, a.ctypes.data)
+    c.proposal = int(proposal)
+    c.gamma = float(gamma)
+    c.K_iters = int(K_iters)
+    c.pf_resample = int(pf_resample)
+    c.ess_frac = float(ess_frac)
+    c.seed = int(seed)
+    c.ckpt_every = int(ckpt_every)
+    c.particles_per_thread = int(particles_per_thread)
+    c.stream = stream
+    c._keep = keep
+    return c
+
+
+class Handle:
+    """One device-resident SMC^2 job (smc2_create ... smc2_destroy)."""
+
+    def __init__(self, cfg: Config):
+        self.lib = load()
+        self.cfg = cfg
+        self.D, self.N, self.T, self.M = cfg.D, cfg.N, cfg.T, cfg.M
+        h = ctypes.c_void_p()
+        check(self.lib.smc2_create(ctypes.byref(cfg), ctypes.byref(h)), "smc2_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            check(self.lib.smc2_destroy(self.h), "smc2_destroy")
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- hot path ------------------------------------------------------------
+    def pf_loglik_grad(self, theta, iteration, loglik, grad=None, row0=0):
+        """theta: (n, D) float64 CUDA tensor; loglik: (n,) float64; grad: (n, D) float64 or None."""
+        n = int(theta.shape[0])
+        check(self.lib.pf_loglik_grad_rows(self.h, _ptr(theta), n, int(iteration), int(row0),
+                                           _ptr(loglik), _ptr(grad)), "pf_loglik_grad")
+
+    def pf_loglik_grad_host(self, theta, iteration, loglik, grad=None):
+        """numpy float64 host arrays in and out (copies inside the call)."""
+        n = int(theta.shape[0])
+        check(self.lib.pf_loglik_grad_host(self.h, _ptr(theta), n, int(iteration), _ptr(loglik),
+                                           _ptr(grad)), "pf_loglik_grad_host")
+
+    def step(self, want_means=True):
+        import numpy as np
+        st = Stats()
+        mean = np.zeros(self.D)
+        rec = np.zeros(self.D)
+        if want_means:
+            st.mean = mean.ctypes.data
+            st.recycled_mean = rec.ctypes.data
+        check(self.lib.smc2_step(self.h, ctypes.byref(st)), "smc2_step")
+        return {"k": st.k, "resampled": bool(st.resampled), "ess": st.ess, "l_k": st.l_k,
+                "max_logw": st.max_logw, "mean": mean, "recycled_mean": rec}
+
+    def samples(self):
+        import numpy as np
+        th = np.zeros((self.N, self.D))
+        lw = np.zeros(self.N)
+        check(self.lib.smc2_get_samples(self.h, _ptr(th), _ptr(lw)), "smc2_get_samples")
+        return th, lw
+
+    def state(self):
+        import numpy as np
+        ll = np.zeros(self.N)
+        g = np.zeros((self.N, self.D))
+        check(self.lib.smc2_get_state(self.h, _ptr(ll), _ptr(g)), "smc2_get_state")
+        return ll, g
+
+    def trace(self):
+        import numpy as np
+        anc = np.zeros((self.N, self.T, self.M), dtype=np.uint16)
+        flag = np.zeros((self.N, self.T), dtype=np.uint8)
+        oanc = np.zeros(self.N, dtype=np.int32)
+        ores = ctypes.c_int32(0)
+        check(self.lib.smc2_get_trace(self.h, _ptr(anc), _ptr(flag), _ptr(oanc), ctypes.byref(ores)),
+              "smc2_get_trace")
+        return anc, flag, oanc, bool(ores.value)
+
+    def set_observations(self, y):
+        import numpy as np
+        ya = np.ascontiguousarray(np.asarray(y, dtype=np.float32))
+        check(self.lib.smc2_set_observations(self.h, _ptr(ya)), "smc2_set_observations")
+
+
+def footprint(cfg: Config) -> int:
+    b = ctypes.c_size_t(0)
+    check(load().smc2_footprint(ctypes.byref(cfg), ctypes.byref(b)), "smc2_footprint")
+    return int(b.value)
+
+
+def config_for(workload, **kw):
+    """Config for a workloads.Workload (sizes, data and step size taken from it)."""
+    prop = LANGEVIN if workload.proposal == "langevin" else RW
+    args = dict(proposal=prop, gamma=workload.gamma, K_iters=workload.K, seed=workload.seed)
+    args.update(kw)
+    return make_config(workload.family, workload.dx, workload.dy, workload.T, workload.N, workload.M,
+                       workload.D, workload.y, workload.H, **args)

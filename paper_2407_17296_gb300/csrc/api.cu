@@ -1,0 +1,495 @@
+// api.cu -- host runtime behind the C ABI of include/smc2.h.
+//
+// One handle = one SMC^2 inference job resident on the current device: its
+// samples theta [N][D], outer log-weights, log pi-hat, gradients, and the
+// particle filter's trajectory storage (checkpoints, ancestor tape) live in
+// device memory for the life of the handle.  Every call is stream-ordered on
+// the handle's stream; smc2_step replays a captured CUDA graph of
+// (propose -> filter forward -> adjoint -> outer update) after its first
+// eager iteration.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "../../include/smc2.h"
+#include "outer.cuh"
+#include "pf_args.h"
+#include "runtime.h"
+
+namespace smc2 {
+pf_launch_fn lookup_pf_lg1(int P);
+pf_launch_fn lookup_pf_lg4(int P);
+pf_launch_fn lookup_pf_sv(int P);
+}  // namespace smc2
+
+using namespace smc2;
+
+namespace {
+thread_local std::string g_err;
+std::atomic<uint64_t> g_launches{0};
+}  // namespace
+
+int smc2::fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+void smc2::count_launches(int n) { g_launches += (uint64_t)n; }
+
+#define CUDA_TRY(x)                                                                          \
+    do {                                                                                     \
+        cudaError_t e_ = (x);                                                                \
+        if (e_ != cudaSuccess) return fail(SMC2_E_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+extern "C" const char* smc2_last_error(void) { return g_err.c_str(); }
+extern "C" uint64_t smc2_kernel_launches(void) { return g_launches.load(); }
+
+extern "C" void smc2_config_init(smc2_config* c) {
+    if (!c) return;
+    std::memset(c, 0, sizeof(*c));
+    c->struct_size = sizeof(smc2_config);
+    c->model_family = SMC2_LG_DIAG;
+    c->d_x = 1;
+    c->d_y = 1;
+    c->proposal = SMC2_LANGEVIN;
+    c->gamma = 0.1;
+    c->K_iters = 10;
+    c->pf_resample = SMC2_SYSTEMATIC;
+    c->ess_frac = 0.5f;
+    c->seed = 777;
+}
+
+// ------------------------------------------------------------------ validation / sizing
+
+int smc2::family_dims(const smc2_config* c, int* D) {
+    if (c->model_family == SMC2_SV) {
+        if (c->d_x != 1 || c->d_y != 1) return fail(SMC2_E_INVAL, "SV needs d_x = d_y = 1");
+        *D = 3;
+        return SMC2_OK;
+    }
+    if (c->model_family != SMC2_LG_DIAG) return fail(SMC2_E_INVAL, "unknown model_family");
+    const bool ok = (c->d_x == 1 && c->d_y == 1) || (c->d_x == 4 && c->d_y == 2);
+    if (!ok) return fail(SMC2_E_INVAL, "LG_DIAG supports (d_x, d_y) = (1,1) or (4,2)");
+    *D = 2 * c->d_x + c->d_y;
+    return SMC2_OK;
+}
+
+pf_launch_fn smc2::select_kernel(const smc2_config* c, int P) {
+    if (c->model_family == SMC2_SV) return lookup_pf_sv(P);
+    if (c->d_x == 1) return lookup_pf_lg1(P);
+    if (c->d_x == 4) return lookup_pf_lg4(P);
+    return nullptr;
+}
+
+int smc2::choose_ppt(const smc2_config* c) {
+    if (c->particles_per_thread) return c->particles_per_thread;
+    int P = 4;
+    while (pf_threads(c->M, P) > 512 && P < 8) P *= 2;
+    return P;
+}
+
+int smc2::choose_kc(const smc2_config* c) {
+    if (c->ckpt_every > 0) return c->ckpt_every;
+    // store every step while the trajectory stays modest; otherwise checkpoint
+    const double per_step = (double)c->N * c->M * (4.0 * c->d_x + 4.0);
+    const double budget = 16.0e9;
+    int kc = 1;
+    while (kc < c->T && per_step * ((double)c->T / kc + 1.0 + (kc > 1 ? kc : 0)) > budget) kc *= 2;
+    return kc;
+}
+
+int smc2::validate(const smc2_config* c, int* D) {
+    if (!c) return fail(SMC2_E_INVAL, "config is NULL");
+    if (c->struct_size != sizeof(smc2_config)) return fail(SMC2_E_INVAL, "config struct_size mismatch");
+    int rc = family_dims(c, D);
+    if (rc) return rc;
+    if (c->D != *D) return fail(SMC2_E_INVAL, "D does not match the model family");
+    if (c->T < 1 || c->N < 1 || c->M < 1) return fail(SMC2_E_INVAL, "T, N and M must be positive");
+    if (c->M > 4096) return fail(SMC2_E_INVAL, "M must be <= 4096");
+    if (c->N > 4096) return fail(SMC2_E_INVAL, "N must be <= 4096");
+    if (!c->y) return fail(SMC2_E_INVAL, "y is NULL");
+    if (!(c->ess_frac >= 0.f && c->ess_frac <= 1.f)) return fail(SMC2_E_INVAL, "ess_frac must be in [0, 1]");
+    if (c->pf_resample != SMC2_SYSTEMATIC && c->pf_resample != SMC2_MULTINOMIAL)
+        return fail(SMC2_E_INVAL, "unknown pf_resample");
+    if (c->proposal != SMC2_RW && c->proposal != SMC2_LANGEVIN) return fail(SMC2_E_INVAL, "unknown proposal");
+    if (!(c->gamma > 0.0)) return fail(SMC2_E_INVAL, "gamma must be positive");
+    if (c->ckpt_every < 0) return fail(SMC2_E_INVAL, "ckpt_every must be >= 0");
+    const int P = c->particles_per_thread;
+    if (P != 0 && P != 1 && P != 2 && P != 4 && P != 8) return fail(SMC2_E_INVAL, "particles_per_thread must be 0, 1, 2, 4 or 8");
+    if (pf_threads(c->M, choose_ppt(c)) > 512) return fail(SMC2_E_INVAL, "M too large for particles_per_thread");
+    if (c->prior_std)
+        for (int d = 0; d < *D; ++d)
+            if (!(c->prior_std[d] > 0.0)) return fail(SMC2_E_INVAL, "prior_std must be positive");
+    return SMC2_OK;
+}
+
+void smc2::plan_sizes(const smc2_config* c, int D, int kc, Sizes* s) {
+    const size_t N = c->N, M = c->M, T = c->T, DX = c->d_x;
+    s->n_slots = (kc == 1) ? (int)(T + 1) : (int)((T + kc - 1) / kc);
+    s->xck = N * s->n_slots * M * DX * sizeof(float);
+    s->lwck = N * s->n_slots * M * sizeof(float);
+    s->xseg = (kc > 1) ? N * kc * M * DX * sizeof(float) : 0;
+    s->lwseg = (kc > 1) ? N * kc * M * sizeof(float) : 0;
+    s->anc = N * T * M * sizeof(uint16_t);
+    s->flag = N * T;
+    s->steps = 2 * N * (T + 1) * sizeof(float);
+    s->state = sizeof(double) * (N * D * 5 + N * 6 + 2 * D + kStatsHead + 2 * D) + sizeof(int) * N + 64;
+    s->obs = sizeof(float) * (T * c->d_y + c->d_y * DX);
+    s->total = s->xck + s->lwck + s->xseg + s->lwseg + s->anc + s->flag + s->steps + s->state + s->obs;
+}
+
+extern "C" int smc2_footprint(const smc2_config* cfg, size_t* bytes) {
+    int D = 0;
+    int rc = validate(cfg, &D);
+    if (rc) return rc;
+    Sizes s;
+    plan_sizes(cfg, D, choose_kc(cfg), &s);
+    if (bytes) *bytes = s.total;
+    return SMC2_OK;
+}
+
+// ------------------------------------------------------------------ handle lifecycle
+
+static void free_handle_memory(smc2_handle* h) {
+    void* ptrs[] = {h->y, h->H, h->prior_m, h->prior_s, h->theta, h->theta_new, h->logw, h->logpi,
+                    h->gradpi, h->loglik, h->ll_new, h->grad_new, h->tmp, h->stats, h->outer_anc,
+                    h->k_dev, h->xck, h->lwck, h->xseg, h->lwseg, h->anc, h->flag, h->mstep, h->lstep};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (h->h_stats) cudaFreeHost(h->h_stats);
+    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+}
+
+extern "C" int smc2_create(const smc2_config* cfg, smc2_handle** out) {
+    if (!out) return fail(SMC2_E_INVAL, "out is NULL");
+    *out = nullptr;
+    int D = 0;
+    int rc = validate(cfg, &D);
+    if (rc) return rc;
+    smc2_handle* h = new smc2_handle();
+    h->cfg = *cfg;
+    h->cfg.y = nullptr;
+    h->cfg.H = nullptr;
+    h->cfg.prior_mean = nullptr;
+    h->cfg.prior_std = nullptr;
+    h->D = D;
+    h->P = choose_ppt(cfg);
+    h->threads = pf_threads(cfg->M, h->P);
+    h->kc = choose_kc(cfg);
+    h->pf = select_kernel(cfg, h->P);
+    if (!h->pf) {
+        delete h;
+        return fail(SMC2_E_INVAL, "no kernel for this model shape");
+    }
+    plan_sizes(cfg, D, h->kc, &h->sizes);
+    const Sizes& s = h->sizes;
+    h->footprint = s.total;
+    auto cleanup = [&](int code, const std::string& msg) {
+        free_handle_memory(h);
+        delete h;
+        return fail(code, msg);
+    };
+    if (cfg->stream) {
+        h->stream = static_cast<cudaStream_t>(cfg->stream);
+        h->own_stream = false;
+    } else {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return cleanup(SMC2_E_CUDA, "cudaStreamCreate failed");
+        h->own_stream = true;
+    }
+    const size_t N = cfg->N, T = cfg->T;
+    struct Alloc { void** p; size_t bytes; };
+    Alloc allocs[] = {
+        {(void**)&h->y, sizeof(float) * T * cfg->d_y},
+        {(void**)&h->H, sizeof(float) * cfg->d_y * cfg->d_x},
+        {(void**)&h->prior_m, sizeof(double) * D},
+        {(void**)&h->prior_s, sizeof(double) * D},
+        {(void**)&h->theta, sizeof(double) * N * D},
+        {(void**)&h->theta_new, sizeof(double) * N * D},
+        {(void**)&h->logw, sizeof(double) * N},
+        {(void**)&h->logpi, sizeof(double) * N},
+        {(void**)&h->gradpi, sizeof(double) * N * D},
+        {(void**)&h->loglik, sizeof(double) * N},
+        {(void**)&h->ll_new, sizeof(double) * N},
+        {(void**)&h->grad_new, sizeof(double) * N * D},
+        {(void**)&h->tmp, sizeof(double) * N * D},
+        {(void**)&h->stats, sizeof(double) * (kStatsHead + 2 * D)},
+        {(void**)&h->outer_anc, sizeof(int) * N},
+        {(void**)&h->k_dev, sizeof(uint32_t)},
+        {(void**)&h->xck, s.xck},
+        {(void**)&h->lwck, s.lwck},
+        {(void**)&h->xseg, s.xseg},
+        {(void**)&h->lwseg, s.lwseg},
+        {(void**)&h->anc, s.anc},
+        {(void**)&h->flag, s.flag},
+        {(void**)&h->mstep, s.steps / 2},
+        {(void**)&h->lstep, s.steps / 2},
+    };
+    for (auto& a : allocs) {
+        if (a.bytes == 0) continue;
+        cudaError_t e = cudaMalloc(a.p, a.bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return cleanup(e == cudaErrorMemoryAllocation ? SMC2_E_NOMEM : SMC2_E_CUDA,
+                           std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        }
+    }
+    if (cudaMallocHost((void**)&h->h_stats, sizeof(double) * (kStatsHead + 2 * D)) != cudaSuccess)
+        return cleanup(SMC2_E_NOMEM, "cudaMallocHost failed");
+    // inputs
+    const cudaMemcpyKind ykind = cfg->y_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    bool ok = cudaMemcpyAsync(h->y, cfg->y, sizeof(float) * T * cfg->d_y, ykind, h->stream) == cudaSuccess;
+    {
+        float Hh[16 * 16];
+        for (int r = 0; r < cfg->d_y; ++r)
+            for (int c = 0; c < cfg->d_x; ++c)
+                Hh[r * cfg->d_x + c] = cfg->H ? cfg->H[r * cfg->d_x + c] : (r == c ? 1.f : 0.f);
+        ok = ok && cudaMemcpy(h->H, Hh, sizeof(float) * cfg->d_y * cfg->d_x, cudaMemcpyHostToDevice) == cudaSuccess;
+        double pm[64], ps[64];
+        for (int d = 0; d < D; ++d) {
+            pm[d] = cfg->prior_mean ? cfg->prior_mean[d] : 0.0;
+            ps[d] = cfg->prior_std ? cfg->prior_std[d] : 1.0;
+        }
+        ok = ok && cudaMemcpy(h->prior_m, pm, sizeof(double) * D, cudaMemcpyHostToDevice) == cudaSuccess;
+        ok = ok && cudaMemcpy(h->prior_s, ps, sizeof(double) * D, cudaMemcpyHostToDevice) == cudaSuccess;
+    }
+    ok = ok && cudaMemsetAsync(h->k_dev, 0, sizeof(uint32_t), h->stream) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(h->stats, 0, sizeof(double) * (kStatsHead + 2 * D), h->stream) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(h->gradpi, 0, sizeof(double) * N * D, h->stream) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(h->flag, 0, s.flag, h->stream) == cudaSuccess;
+    ok = ok && cudaStreamSynchronize(h->stream) == cudaSuccess;
+    if (!ok) return cleanup(SMC2_E_CUDA, std::string("initial copies failed: ") + cudaGetErrorString(cudaGetLastError()));
+    *out = h;
+    return SMC2_OK;
+}
+
+extern "C" int smc2_destroy(smc2_handle* h) {
+    if (!h) return fail(SMC2_E_INVAL, "handle is NULL");
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    free_handle_memory(h);
+    delete h;
+    return SMC2_OK;
+}
+
+// ------------------------------------------------------------------ the hot path
+
+PFArgs smc2::make_pf_args(smc2_handle* h, const double* theta, int n, uint32_t iter, uint32_t row0,
+                          const uint32_t* iter_dev, double* loglik, double* grad) {
+    PFArgs a{};
+    a.theta = theta;
+    a.y = h->y;
+    a.H = h->H;
+    a.n = n;
+    a.D = h->D;
+    a.T = h->cfg.T;
+    a.M = h->cfg.M;
+    a.seed_lo = (uint32_t)(h->cfg.seed & 0xFFFFFFFFull);
+    a.seed_hi = (uint32_t)(h->cfg.seed >> 32);
+    a.iter = iter;
+    a.row0 = row0;
+    a.iter_dev = iter_dev;
+    a.ess_frac = h->cfg.ess_frac;
+    a.scheme = h->cfg.pf_resample;
+    a.want_grad = grad != nullptr;
+    a.kc = h->kc;
+    a.n_slots = h->sizes.n_slots;
+    a.xck = h->xck;
+    a.lwck = h->lwck;
+    a.xseg = h->xseg;
+    a.lwseg = h->lwseg;
+    a.anc = h->anc;
+    a.flag = h->flag;
+    a.mstep = h->mstep;
+    a.lstep = h->lstep;
+    a.loglik = loglik;
+    a.grad = grad;
+    return a;
+}
+
+int smc2::launch_filters(smc2_handle* h, const PFArgs& a) {
+    const SmemLayout lf(a.M, h->cfg.d_x, h->D, true), lb(a.M, h->cfg.d_x, h->D, false);
+    const int rc = h->pf(a, h->threads, lf.total, lb.total, h->stream, a.n, a.n);
+    if (rc) return fail(SMC2_E_CUDA, std::string("filter launch failed: ") + cudaGetErrorString(cudaGetLastError()));
+    count_launches(a.want_grad ? 2 : 1);
+    return SMC2_OK;
+}
+
+extern "C" int pf_loglik_grad_rows(smc2_handle* h, const double* theta_dev, int n, uint32_t iter,
+                                   uint32_t row0, double* loglik_dev, double* grad_dev) {
+    if (!h) return fail(SMC2_E_INVAL, "handle is NULL");
+    if (n < 0 || n > h->cfg.N) return fail(SMC2_E_INVAL, "n must be in [0, N]");
+    if (n == 0) return SMC2_OK;
+    if (!theta_dev || !loglik_dev) return fail(SMC2_E_INVAL, "theta and loglik must not be NULL");
+    const PFArgs a = make_pf_args(h, theta_dev, n, iter, row0, nullptr, loglik_dev, grad_dev);
+    return launch_filters(h, a);
+}
+
+extern "C" int pf_loglik_grad(smc2_handle* h, const double* theta_dev, int n, uint32_t iter,
+                              double* loglik_dev, double* grad_dev) {
+    return pf_loglik_grad_rows(h, theta_dev, n, iter, 0u, loglik_dev, grad_dev);
+}
+
+extern "C" int pf_loglik_grad_host(smc2_handle* h, const double* theta_host, int n, uint32_t iter,
+                                   double* loglik_host, double* grad_host) {
+    if (!h) return fail(SMC2_E_INVAL, "handle is NULL");
+    if (n < 0 || n > h->cfg.N) return fail(SMC2_E_INVAL, "n must be in [0, N]");
+    if (n == 0) return SMC2_OK;
+    if (!theta_host || !loglik_host) return fail(SMC2_E_INVAL, "theta and loglik must not be NULL");
+    const size_t D = h->D;
+    CUDA_TRY(cudaMemcpyAsync(h->theta_new, theta_host, sizeof(double) * n * D, cudaMemcpyHostToDevice, h->stream));
+    const PFArgs a = make_pf_args(h, h->theta_new, n, iter, 0u, nullptr, h->ll_new, grad_host ? h->grad_new : nullptr);
+    int rc = launch_filters(h, a);
+    if (rc) return rc;
+    CUDA_TRY(cudaMemcpyAsync(loglik_host, h->ll_new, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+    if (grad_host)
+        CUDA_TRY(cudaMemcpyAsync(grad_host, h->grad_new, sizeof(double) * n * D, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return SMC2_OK;
+}
+
+// ------------------------------------------------------------------ SMC^2 step
+
+OuterArgs smc2::make_outer_args(smc2_handle* h) {
+    OuterArgs o{};
+    o.N = h->cfg.N;
+    o.D = h->D;
+    o.gamma = h->cfg.gamma;
+    o.langevin = h->cfg.proposal == SMC2_LANGEVIN;
+    o.seed_lo = (uint32_t)(h->cfg.seed & 0xFFFFFFFFull);
+    o.seed_hi = (uint32_t)(h->cfg.seed >> 32);
+    o.prior_mean = h->prior_m;
+    o.prior_std = h->prior_s;
+    o.k_dev = h->k_dev;
+    o.theta = h->theta;
+    o.theta_new = h->theta_new;
+    o.logw = h->logw;
+    o.logpi = h->logpi;
+    o.gradpi = h->gradpi;
+    o.loglik = h->loglik;
+    o.ll_new = h->ll_new;
+    o.grad_new = h->grad_new;
+    o.tmp = h->tmp;
+    o.stats = h->stats;
+    o.outer_anc = h->outer_anc;
+    return o;
+}
+
+int smc2::enqueue_step(smc2_handle* h) {
+    const OuterArgs o = make_outer_args(h);
+    if (launch_outer_propose(o, h->stream)) return fail(SMC2_E_CUDA, "outer propose launch failed");
+    const PFArgs a = make_pf_args(h, h->theta_new, h->cfg.N, 0u, 0u, h->k_dev, h->ll_new, h->grad_new);
+    int rc = launch_filters(h, a);
+    if (rc) return rc;
+    if (launch_outer_update(o, h->stream)) return fail(SMC2_E_CUDA, "outer update launch failed");
+    count_launches(2);
+    return SMC2_OK;
+}
+
+int smc2::step_async(smc2_handle* h) {
+    // first iteration eagerly (sets kernel attributes); later ones replay a captured graph
+    if (h->k >= 1 && !h->graph_exec && !h->no_graph) {
+        cudaGraph_t g = nullptr;
+        CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        const uint64_t before = g_launches.load();
+        int rc = enqueue_step(h);
+        cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+        g_launches = before;  // captured, not launched
+        h->launches_per_step = 0;
+        if (rc || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            h->no_graph = true;
+        } else {
+            e = cudaGraphInstantiate(&h->graph_exec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                h->graph_exec = nullptr;
+                h->no_graph = true;
+            }
+        }
+    }
+    if (h->graph_exec) {
+        CUDA_TRY(cudaGraphLaunch(h->graph_exec, h->stream));
+        count_launches(4);
+    } else {
+        int rc = enqueue_step(h);
+        if (rc) return rc;
+    }
+    h->k += 1;
+    return SMC2_OK;
+}
+
+int smc2::read_stats(smc2_handle* h, smc2_stats* out) {
+    const int D = h->D;
+    CUDA_TRY(cudaMemcpyAsync(h->h_stats, h->stats, sizeof(double) * (kStatsHead + 2 * D), cudaMemcpyDeviceToHost,
+                             h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (!out) return SMC2_OK;
+    const double* s = h->h_stats;
+    out->k = (int32_t)s[kStK];
+    out->resampled = s[kStResampled] != 0.0;
+    out->ess = s[kStEss];
+    out->l_k = s[kStLk];
+    out->max_logw = s[kStMaxLogw];
+    if (out->mean)
+        for (int d = 0; d < D; ++d) out->mean[d] = s[kStatsHead + d];
+    if (out->recycled_mean)
+        for (int d = 0; d < D; ++d) out->recycled_mean[d] = s[kStSumL] > 0 ? s[kStatsHead + D + d] / s[kStSumL] : 0.0;
+    return SMC2_OK;
+}
+
+extern "C" int smc2_step(smc2_handle* h, smc2_stats* out) {
+    if (!h) return fail(SMC2_E_INVAL, "handle is NULL");
+    int rc = step_async(h);
+    if (rc) return rc;
+    return read_stats(h, out);
+}
+
+extern "C" int smc2_get_samples(smc2_handle* h, double* theta_host, double* logw_host) {
+    if (!h) return fail(SMC2_E_INVAL, "handle is NULL");
+    const size_t N = h->cfg.N, D = h->D;
+    if (theta_host) CUDA_TRY(cudaMemcpyAsync(theta_host, h->theta, sizeof(double) * N * D, cudaMemcpyDeviceToHost, h->stream));
+    if (logw_host) CUDA_TRY(cudaMemcpyAsync(logw_host, h->logw, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return SMC2_OK;
+}
+
+extern "C" int smc2_get_state(smc2_handle* h, double* loglik_host, double* gradpi_host) {
+    if (!h) return fail(SMC2_E_INVAL, "handle is NULL");
+    const size_t N = h->cfg.N, D = h->D;
+    if (loglik_host) CUDA_TRY(cudaMemcpyAsync(loglik_host, h->loglik, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream));
+    if (gradpi_host) CUDA_TRY(cudaMemcpyAsync(gradpi_host, h->gradpi, sizeof(double) * N * D, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return SMC2_OK;
+}
+
+extern "C" int smc2_get_trace(smc2_handle* h, uint16_t* pf_anc, uint8_t* pf_flag, int32_t* outer_anc,
+                              int32_t* outer_resampled) {
+    if (!h) return fail(SMC2_E_INVAL, "handle is NULL");
+    const size_t N = h->cfg.N, T = h->cfg.T, M = h->cfg.M;
+    if (pf_anc) CUDA_TRY(cudaMemcpyAsync(pf_anc, h->anc, sizeof(uint16_t) * N * T * M, cudaMemcpyDeviceToHost, h->stream));
+    if (pf_flag) CUDA_TRY(cudaMemcpyAsync(pf_flag, h->flag, N * T, cudaMemcpyDeviceToHost, h->stream));
+    if (outer_anc) CUDA_TRY(cudaMemcpyAsync(outer_anc, h->outer_anc, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, h->stream));
+    if (outer_resampled) {
+        double r = 0.0;
+        CUDA_TRY(cudaMemcpyAsync(&r, h->stats + kStResampled, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        CUDA_TRY(cudaStreamSynchronize(h->stream));
+        *outer_resampled = r != 0.0;
+    }
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return SMC2_OK;
+}
+
+extern "C" int smc2_set_observations(smc2_handle* h, const float* y_host) {
+    if (!h || !y_host) return fail(SMC2_E_INVAL, "NULL argument");
+    CUDA_TRY(cudaMemcpyAsync(h->y, y_host, sizeof(float) * h->cfg.T * h->cfg.d_y, cudaMemcpyHostToDevice, h->stream));
+    return SMC2_OK;
+}

@@ -1,0 +1,181 @@
+// models.cuh -- state-space model families for the CRN particle filter.
+//
+// Each family supplies, in FP32 on the device:
+//   init        x_0 from its noise (the reparameterised initial law)
+//   transition  x_t = f(x_{t-1}, theta, eps_t)  (Eq. reparam_epsilon: mean + sqrt(C) eps)
+//   loglik      log g(y_t | x_t, theta)          (Eq. L)
+// and the reverse-mode pieces of the same maps (the adjoints of Eqs. dxk and
+// deriv_loglike), used by the adjoint kernel:
+//   bwd_obs     xbar += lwbar dlog g/dx,  thb += lwbar dlog g/dtheta
+//   bwd_trans   thb += xbar df/dtheta,    xbar <- (df/dx)^T xbar
+//   bwd_init    thb += xbar0 dx_0/dtheta
+// Parameters are derived once per filter from theta in FP64 and rounded to FP32.
+#pragma once
+#include <cmath>
+
+namespace smc2 {
+
+constexpr float kLog2Pi = 1.8378770664093454836f;
+
+// Linear-Gaussian model with diagonal transition (Sec. II, Eqs. xt and yt with
+// f = N(diag(a) x, diag(q)^2), g = N(H x, diag(r)^2)), theta = (a, log q, log r).
+template <int DX_, int DY_, bool HIDENT_>
+struct LGDiag {
+    static constexpr int DX = DX_, DY = DY_, D = 2 * DX_ + DY_;
+    static constexpr bool HIDENT = HIDENT_;
+    static constexpr int kFamily = 0;
+    struct Params {
+        float a[DX], q[DX], rinv[DY];
+        float H[HIDENT ? 1 : DY][DX];
+        float cst;  // -sum log r - DY/2 log 2 pi
+    };
+
+    __device__ static void make_params(const double* th, const float* Hg, Params& p) {
+        double c = 0.0;
+        for (int k = 0; k < DX; ++k) {
+            p.a[k] = (float)th[k];
+            p.q[k] = (float)exp(th[DX + k]);
+        }
+        for (int m = 0; m < DY; ++m) {
+            p.rinv[m] = (float)exp(-th[2 * DX + m]);
+            c -= th[2 * DX + m];
+        }
+        p.cst = (float)(c - 0.5 * DY * 1.8378770664093454836);
+        if constexpr (!HIDENT) {
+            for (int m = 0; m < DY; ++m)
+                for (int k = 0; k < DX; ++k) p.H[m][k] = Hg ? Hg[m * DX + k] : (m == k ? 1.f : 0.f);
+        }
+    }
+
+    __device__ __forceinline__ static void init(const Params&, const float (&eps)[DX], float (&x)[DX]) {
+#pragma unroll
+        for (int k = 0; k < DX; ++k) x[k] = eps[k];
+    }
+
+    __device__ __forceinline__ static void transition(const Params& p, float (&x)[DX],
+                                                      const float (&eps)[DX]) {
+#pragma unroll
+        for (int k = 0; k < DX; ++k) x[k] = p.a[k] * x[k] + p.q[k] * eps[k];
+    }
+
+    __device__ __forceinline__ static void residual(const Params& p, const float (&x)[DX],
+                                                    const float* __restrict__ yt, float (&z)[DY]) {
+#pragma unroll
+        for (int m = 0; m < DY; ++m) {
+            float h;
+            if constexpr (HIDENT) {
+                h = x[m];
+            } else {
+                h = 0.f;
+#pragma unroll
+                for (int k = 0; k < DX; ++k) h += p.H[m][k] * x[k];
+            }
+            z[m] = (__ldg(yt + m) - h) * p.rinv[m];
+        }
+    }
+
+    __device__ __forceinline__ static float loglik(const Params& p, const float (&x)[DX],
+                                                   const float* __restrict__ yt) {
+        float z[DY];
+        residual(p, x, yt, z);
+        float s = 0.f;
+#pragma unroll
+        for (int m = 0; m < DY; ++m) s += z[m] * z[m];
+        return p.cst - 0.5f * s;
+    }
+
+    __device__ __forceinline__ static void bwd_obs(const Params& p, const float (&x)[DX],
+                                                   const float* __restrict__ yt, float lwbar,
+                                                   float (&xbar)[DX], float (&thb)[D]) {
+        float z[DY];
+        residual(p, x, yt, z);
+#pragma unroll
+        for (int m = 0; m < DY; ++m) {
+            thb[2 * DX + m] += lwbar * (z[m] * z[m] - 1.f);
+            const float g = lwbar * z[m] * p.rinv[m];   // lwbar * e_m / r_m^2
+            if constexpr (HIDENT) {
+                xbar[m] += g;
+            } else {
+#pragma unroll
+                for (int k = 0; k < DX; ++k) xbar[k] += g * p.H[m][k];
+            }
+        }
+    }
+
+    // xt = x_t, xp = x'_{t-1} (after resampling); xbar in: adjoint of x_t, out: adjoint of x'.
+    __device__ __forceinline__ static void bwd_trans(const Params& p, const float (&xt)[DX],
+                                                     const float (&xp)[DX], float (&xbar)[DX],
+                                                     float (&thb)[D]) {
+#pragma unroll
+        for (int k = 0; k < DX; ++k) {
+            thb[k] += xbar[k] * xp[k];                          // d/da_k
+            thb[DX + k] += xbar[k] * (xt[k] - p.a[k] * xp[k]);  // d/dlog q_k = q_k eps_k
+            xbar[k] *= p.a[k];
+        }
+    }
+
+    __device__ __forceinline__ static void bwd_init(const Params&, const float (&)[DX], const float (&)[DX],
+                                                    float (&)[D]) {}
+};
+
+// Stochastic volatility: x_t = mu + phi (x_{t-1} - mu) + sigma eta_t, y_t = exp(x_t/2) eps_t,
+// x_0 from the stationary law; theta = (mu, atanh phi, log sigma).
+struct SV {
+    static constexpr int DX = 1, DY = 1, D = 3;
+    static constexpr bool HIDENT = true;
+    static constexpr int kFamily = 1;
+    struct Params {
+        float mu, phi, sig, sd0, omp2;  // omp2 = 1 - phi^2
+    };
+
+    __device__ static void make_params(const double* th, const float*, Params& p) {
+        const double phi = tanh(th[1]);
+        const double sig = exp(th[2]);
+        p.mu = (float)th[0];
+        p.phi = (float)phi;
+        p.sig = (float)sig;
+        p.sd0 = (float)(sig / sqrt(1.0 - phi * phi));
+        p.omp2 = (float)(1.0 - phi * phi);
+    }
+
+    __device__ __forceinline__ static void init(const Params& p, const float (&eps)[1], float (&x)[1]) {
+        x[0] = p.mu + p.sd0 * eps[0];
+    }
+
+    __device__ __forceinline__ static void transition(const Params& p, float (&x)[1], const float (&eps)[1]) {
+        x[0] = p.mu + p.phi * (x[0] - p.mu) + p.sig * eps[0];
+    }
+
+    __device__ __forceinline__ static float loglik(const Params&, const float (&x)[1],
+                                                   const float* __restrict__ yt) {
+        const float y = __ldg(yt);
+        return -0.5f * (kLog2Pi + x[0] + y * y * expf(-x[0]));
+    }
+
+    __device__ __forceinline__ static void bwd_obs(const Params&, const float (&x)[1],
+                                                   const float* __restrict__ yt, float lwbar,
+                                                   float (&xbar)[1], float (&)[3]) {
+        const float y = __ldg(yt);
+        xbar[0] += lwbar * (0.5f * y * y * expf(-x[0]) - 0.5f);
+    }
+
+    __device__ __forceinline__ static void bwd_trans(const Params& p, const float (&xt)[1],
+                                                     const float (&xp)[1], float (&xbar)[1],
+                                                     float (&thb)[3]) {
+        const float dev = xp[0] - p.mu;
+        thb[0] += xbar[0] * (1.f - p.phi);
+        thb[1] += xbar[0] * p.omp2 * dev;
+        thb[2] += xbar[0] * (xt[0] - p.mu - p.phi * dev);  // sigma * eta
+        xbar[0] *= p.phi;
+    }
+
+    __device__ __forceinline__ static void bwd_init(const Params& p, const float (&x0)[1],
+                                                    const float (&xbar)[1], float (&thb)[3]) {
+        const float dev = x0[0] - p.mu;  // sd0 * eps_0
+        thb[0] += xbar[0];
+        thb[1] += xbar[0] * p.phi * dev;
+        thb[2] += xbar[0] * dev;
+    }
+};
+
+}  // namespace smc2

@@ -1,0 +1,308 @@
+// outer.cu -- outer SMC^2 step (Sec. III): proposal, L-kernel weight, normalisation,
+// estimate, recycling statistic, ESS and systematic resampling, all in FP64.
+//
+// Proposal (Sec. III-D): theta' = theta + F(theta) + gamma xi with F = 0.5 gamma^2 grad log pi
+// (SMC1) or F = 0 (SMC0), xi from Philox stream 3 keyed by (iteration, sample).
+// Weight (Eq. l_weights) with the Langevin L-kernel read as the reversed one-step
+// leapfrog (Sec. III-E): L(theta|theta') = N(theta; theta' + F(theta'), gamma^2 I), so
+//   log w += log pi(theta') - log pi(theta) + log L(theta|theta') - log q(theta'|theta).
+// Iteration 1 draws theta from the prior (Eq. init_sample) and weights by
+// pi/q_1 = p-hat(y|theta) (Eq. init_weights).
+// Then: normalise (Eq. normalise_smc2), estimate f~_k = sum w~ theta (Eq. realised_estimates),
+// l_k = (sum w)^2 / sum w^2 (Eq. recycling_I), ESS (Eq. ess_smc2) and, if ESS < N/2,
+// systematic resampling with one uniform per iteration (Philox stream 4), ancestors
+// a_i = min{j : c_j >= (i + nu)/N}, log w <- LSE(log w) - log N (the sum is kept).
+#include <cuda_runtime.h>
+
+#include "outer.cuh"
+#include "philox.cuh"
+
+namespace smc2 {
+
+namespace {
+
+constexpr int kOuterThreads = 1024;
+constexpr unsigned kFullMask = 0xffffffffu;
+
+__device__ __forceinline__ double u01_open_d(uint32_t u) { return ((double)(u >> 8) + 1.0) * 5.9604644775390625e-08; }
+__device__ __forceinline__ double u01_half_d(uint32_t u) { return (double)(u >> 8) * 5.9604644775390625e-08; }
+
+// FP64 Box-Muller on (ua, ub).
+__device__ __forceinline__ void box_muller_d(uint32_t ua, uint32_t ub, double& z0, double& z1) {
+    const double r = sqrt(-2.0 * log(u01_open_d(ua)));
+    double s, c;
+    sincospi(2.0 * u01_half_d(ub), &s, &c);
+    z0 = r * c;
+    z1 = r * s;
+}
+
+__device__ double outer_normal(PhiloxKey key, int d) {
+    const uint4 w = philox4x32_10(make_uint4(0u, (uint32_t)d >> 2, kStreamOuterXi, 0u), key);
+    double z0, z1;
+    if ((d & 3) < 2) box_muller_d(w.x, w.y, z0, z1);
+    else box_muller_d(w.z, w.w, z0, z1);
+    return (d & 1) ? z1 : z0;
+}
+
+__global__ void outer_propose_kernel(OuterArgs a) {
+    const uint32_t k = *a.k_dev + 1u;  // iteration being proposed
+    const int D = a.D;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < a.N * D; idx += gridDim.x * blockDim.x) {
+        const int i = idx / D, d = idx - i * D;
+        const PhiloxKey key = philox_key(a.seed_lo, a.seed_hi, k, (uint32_t)i);
+        const double xi = outer_normal(key, d);
+        double v;
+        if (k == 1u) {
+            v = a.prior_mean[d] + a.prior_std[d] * xi;
+        } else {
+            const double drift = a.langevin ? 0.5 * a.gamma * a.gamma * a.gradpi[idx] : 0.0;
+            v = a.theta[idx] + drift + a.gamma * xi;
+        }
+        a.theta_new[idx] = v;
+    }
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFullMask, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFullMask, v, o));
+    return v;
+}
+
+// block-wide sum / max (all threads get the result); red needs 32 doubles; two syncs
+__device__ double block_sum_d(double v, double* red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum_d(v);
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += red[w];
+    __syncthreads();
+    return s;
+}
+__device__ double block_max_d(double v, double* red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_max_d(v);
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double s = -INFINITY;
+    for (int w = 0; w < nw; ++w) s = fmax(s, red[w]);
+    __syncthreads();
+    return s;
+}
+
+__device__ double log_prior(const double* th, const double* m, const double* s, int D) {
+    double acc = 0.0;
+    for (int d = 0; d < D; ++d) {
+        const double z = (th[d] - m[d]) / s[d];
+        acc += -0.5 * z * z - log(s[d]) - 0.9189385332046727418;
+    }
+    return acc;
+}
+
+__global__ void __launch_bounds__(kOuterThreads) outer_update_kernel(OuterArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    double* red = reinterpret_cast<double*>(smem);               // 32
+    double* csum = red + 32;                                      // N
+    int* anc = reinterpret_cast<int*>(csum + a.N);                // N
+    const int N = a.N, D = a.D, tid = threadIdx.x, nt = blockDim.x;
+    const uint32_t k = *a.k_dev + 1u;
+    const double g2 = a.gamma * a.gamma;
+
+    // 1. pseudo-marginal update of every sample with its particle-filter result
+    for (int i = tid; i < N; i += nt) {
+        const double* thn = a.theta_new + (size_t)i * D;
+        const double lln = a.ll_new[i];
+        const double lpn = (lln > -INFINITY) ? log_prior(thn, a.prior_mean, a.prior_std, D) + lln : -INFINITY;
+        double lw;
+        if (k == 1u) {
+            lw = lln;  // pi / q_1 with q_1 the prior
+        } else {
+            lw = a.logw[i];
+            if (lw > -INFINITY && lpn > -INFINITY && a.logpi[i] > -INFINITY) {
+                double corr = 0.0;
+                if (a.langevin) {
+                    // log L(theta | theta') - log q(theta' | theta)
+                    const double* th = a.theta + (size_t)i * D;
+                    const double* gp = a.gradpi + (size_t)i * D;
+                    const double* gn = a.grad_new + (size_t)i * D;
+                    double qf = 0.0, lf = 0.0;
+                    for (int d = 0; d < D; ++d) {
+                        const double gpn = -(thn[d] - a.prior_mean[d]) / (a.prior_std[d] * a.prior_std[d]) + gn[d];
+                        const double fwd = thn[d] - th[d] - 0.5 * g2 * gp[d];
+                        const double bwd = th[d] - thn[d] - 0.5 * g2 * gpn;
+                        qf += fwd * fwd;
+                        lf += bwd * bwd;
+                    }
+                    corr = -0.5 * (lf - qf) / g2;
+                }
+                lw = lw + (lpn - a.logpi[i]) + corr;
+            } else {
+                lw = -INFINITY;
+            }
+        }
+        a.logw[i] = lw;
+        a.logpi[i] = lpn;
+        a.loglik[i] = lln;
+        for (int d = 0; d < D; ++d) {
+            const double th = thn[d];
+            a.theta[(size_t)i * D + d] = th;
+            a.gradpi[(size_t)i * D + d] =
+                -(th - a.prior_mean[d]) / (a.prior_std[d] * a.prior_std[d]) + a.grad_new[(size_t)i * D + d];
+        }
+    }
+    __syncthreads();
+
+    // 2. normalise, ESS, estimate, recycling statistic
+    double lmax = -INFINITY;
+    for (int i = tid; i < N; i += nt) lmax = fmax(lmax, a.logw[i]);
+    lmax = block_max_d(lmax, red);
+    double s1 = 0.0, s2 = 0.0;
+    if (lmax > -INFINITY) {
+        for (int i = tid; i < N; i += nt) {
+            const double e = exp(a.logw[i] - lmax);
+            s1 += e;
+            s2 += e * e;
+        }
+    }
+    s1 = block_sum_d(s1, red);
+    s2 = block_sum_d(s2, red);
+    const double ess = (s2 > 0.0) ? s1 * s1 / s2 : 0.0;
+    double* mean = a.stats + kStatsHead;
+    double* recnum = a.stats + kStatsHead + D;
+    {
+        // warp w accumulates dimensions d = w, w + nw, ...
+        const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+        for (int d = wid; d < D; d += nw) {
+            double acc = 0.0;
+            if (lmax > -INFINITY)
+                for (int i = lane; i < N; i += 32) acc += exp(a.logw[i] - lmax) * a.theta[(size_t)i * D + d];
+            acc = warp_sum_d(acc);
+            if (lane == 0) {
+                const double md = (s1 > 0.0) ? acc / s1 : 0.0;
+                mean[d] = md;
+                const double prev = (k == 1u) ? 0.0 : recnum[d];
+                recnum[d] = prev + ess * md;
+            }
+        }
+    }
+    const bool resample = ess < 0.5 * (double)N && lmax > -INFINITY;
+    if (tid == 0) {
+        a.stats[kStEss] = ess;
+        a.stats[kStLk] = ess;  // (sum w)^2 / sum w^2
+        a.stats[kStResampled] = resample ? 1.0 : 0.0;
+        a.stats[kStMaxLogw] = lmax;
+        a.stats[kStSumL] = ((k == 1u) ? 0.0 : a.stats[kStSumL]) + ess;
+        a.stats[kStK] = (double)k;
+    }
+    if (!resample) {
+        if (tid == 0) *a.k_dev = k;
+        return;
+    }
+
+    // 3. systematic resampling: FP64 prefix sums (per-thread chunk, warp shuffle, warps)
+    {
+        const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+        const int chunk = (N + nt - 1) / nt;
+        const int i0 = tid * chunk;
+        double run = 0.0;
+        for (int c = 0; c < chunk; ++c) {
+            const int i = i0 + c;
+            if (i < N) {
+                run += exp(a.logw[i] - lmax);
+                csum[i] = run;
+            }
+        }
+        double inc = run;
+        for (int o = 1; o < 32; o <<= 1) {
+            const double v = __shfl_up_sync(kFullMask, inc, o);
+            if (lane >= o) inc += v;
+        }
+        if (lane == 31) red[wid] = inc;
+        __syncthreads();
+        double pre = 0.0, tot = 0.0;
+        for (int w = 0; w < nw; ++w) {
+            if (w < wid) pre += red[w];
+            tot += red[w];
+        }
+        const double base = pre + (inc - run);
+        for (int c = 0; c < chunk; ++c) {
+            const int i = i0 + c;
+            if (i < N) csum[i] = (i == N - 1) ? 1.0 : (base + csum[i]) / tot;
+        }
+        __syncthreads();
+    }
+    const PhiloxKey key = philox_key(a.seed_lo, a.seed_hi, k, 0u);
+    const uint4 w = philox4x32_10(make_uint4(0u, 0u, kStreamOuterNu, 0u), key);
+    const double nu = u01_open_d(w.x);
+    for (int i = tid; i < N; i += nt) {
+        const double tau = ((double)i + nu) / (double)N;
+        int lo = 0, hi = N - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (csum[mid] >= tau) hi = mid;
+            else lo = mid + 1;
+        }
+        anc[i] = lo;
+        a.outer_anc[i] = lo;
+    }
+    __syncthreads();
+    // gather rows through the scratch buffer
+    for (int idx = tid; idx < N * D; idx += nt) {
+        const int i = idx / D, d = idx - i * D;
+        a.tmp[idx] = a.theta[(size_t)anc[i] * D + d];
+    }
+    __syncthreads();
+    for (int idx = tid; idx < N * D; idx += nt) a.theta[idx] = a.tmp[idx];
+    __syncthreads();
+    for (int idx = tid; idx < N * D; idx += nt) {
+        const int i = idx / D, d = idx - i * D;
+        a.tmp[idx] = a.gradpi[(size_t)anc[i] * D + d];
+    }
+    __syncthreads();
+    for (int idx = tid; idx < N * D; idx += nt) a.gradpi[idx] = a.tmp[idx];
+    __syncthreads();
+    // scalars: logpi and loglik through csum (free now) as scratch
+    for (int i = tid; i < N; i += nt) csum[i] = a.logpi[anc[i]];
+    __syncthreads();
+    for (int i = tid; i < N; i += nt) a.logpi[i] = csum[i];
+    __syncthreads();
+    for (int i = tid; i < N; i += nt) csum[i] = a.loglik[anc[i]];
+    __syncthreads();
+    const double lw_new = lmax + log(s1) - log((double)N);
+    for (int i = tid; i < N; i += nt) {
+        a.loglik[i] = csum[i];
+        a.logw[i] = lw_new;
+    }
+    if (tid == 0) *a.k_dev = k;
+}
+
+}  // namespace
+
+size_t outer_update_smem(int N, int D) {
+    (void)D;
+    return sizeof(double) * (32 + (size_t)N) + sizeof(int) * (size_t)N;
+}
+
+int launch_outer_propose(const OuterArgs& a, void* stream) {
+    const int total = a.N * a.D;
+    const int threads = 256;
+    const int blocks = (total + threads - 1) / threads;
+    outer_propose_kernel<<<blocks, threads, 0, static_cast<cudaStream_t>(stream)>>>(a);
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+int launch_outer_update(const OuterArgs& a, void* stream) {
+    const size_t smem = outer_update_smem(a.N, a.D);
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(outer_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return -3;
+    outer_update_kernel<<<1, kOuterThreads, smem, static_cast<cudaStream_t>(stream)>>>(a);
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+}  // namespace smc2

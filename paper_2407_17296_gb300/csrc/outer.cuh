@@ -1,0 +1,36 @@
+// outer.cuh -- the outer SMC^2 sampler step in FP64 (Sec. III).
+#pragma once
+#include <cstdint>
+
+namespace smc2 {
+
+struct OuterArgs {
+    int N, D;
+    double gamma;
+    int langevin;                 // 1: SMC1 Langevin proposal, 0: SMC0 random walk
+    uint32_t seed_lo, seed_hi;
+    const double* prior_mean;     // [D]
+    const double* prior_std;      // [D]
+    uint32_t* k_dev;              // iteration counter (1-based), advanced by outer_update
+    double* theta;                // [N][D] current samples
+    double* theta_new;            // [N][D] proposals (input of the particle filters)
+    double* logw;                 // [N]
+    double* logpi;                // [N] log prior + log p-hat
+    double* gradpi;               // [N][D] grad log prior + grad log p-hat
+    double* loglik;               // [N]
+    const double* ll_new;         // [N]  particle-filter outputs at theta_new
+    const double* grad_new;       // [N][D]
+    double* tmp;                  // [N][D] gather scratch
+    double* stats;                // [kStatsHead + 2D]
+    int* outer_anc;               // [N]
+};
+
+// stats layout (FP64 slots)
+enum { kStEss = 0, kStLk = 1, kStResampled = 2, kStMaxLogw = 3, kStSumL = 4, kStK = 5, kStatsHead = 6 };
+// then mean [D] at kStatsHead, recycled numerator sum_k l_k f~_k [D] at kStatsHead + D
+
+int launch_outer_propose(const OuterArgs& a, void* stream);
+int launch_outer_update(const OuterArgs& a, void* stream);
+size_t outer_update_smem(int N, int D);
+
+}  // namespace smc2

@@ -1,0 +1,74 @@
+// pf_args.h -- launch arguments shared by the host runtime and the particle-filter kernels.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+#ifdef __CUDACC__
+#define SMC2_HD __host__ __device__
+#else
+#define SMC2_HD
+#endif
+
+namespace smc2 {
+
+struct PFArgs {
+    // inputs
+    const double* theta;    // [n][D] row-major, FP64
+    const float* y;         // [T][dy]
+    const float* H;         // [dy][dx] or nullptr (identity)
+    int n;                  // filters in this launch
+    int D, T, M;
+    uint32_t seed_lo, seed_hi, iter, row0;
+    const uint32_t* iter_dev;  // if set, the Philox iteration is *iter_dev + 1 (graph replays)
+    float ess_frac;         // resample when ESS < ess_frac * M
+    int scheme;             // 0 systematic, 1 multinomial
+    int want_grad;          // run the adjoint / keep checkpoints
+    // adjoint storage (see the trajectory layout in pf_kernels.cuh)
+    int kc;                 // checkpoint interval; 1 = every step is stored
+    int n_slots;            // checkpoint slots per filter
+    float* xck;             // [n][n_slots][M][DX]
+    float* lwck;            // [n][n_slots][M]
+    float* xseg;            // [n][kc][M][DX]   (kc > 1)
+    float* lwseg;           // [n][kc][M]       (kc > 1)
+    uint16_t* anc;          // [n][T][M] ancestor tape (row t-1: before step t)
+    uint8_t* flag;          // [n][T]   1 if the filter resampled before step t
+    float* mstep;           // [n][T+1] recentring maximum of step t
+    float* lstep;           // [n][T+1] log sum exp of the recentred log-weights after step t
+    // outputs
+    double* loglik;         // [n]
+    double* grad;           // [n][D]
+};
+
+// Dynamic shared-memory plan (mirrored on the host to size the launch).
+struct SmemLayout {
+    size_t xstage, xbstage, cs, marks, starts, red, scanw, scanwi, dred, total;
+    SMC2_HD SmemLayout(int M, int DX, int D, bool fwd) {
+        size_t o = 0;
+        auto take = [&](size_t bytes) {
+            const size_t r = o;
+            o += (bytes + 15) & ~size_t(15);
+            return r;
+        };
+        xstage = take(sizeof(float) * (size_t)M * DX);
+        xbstage = fwd ? o : take(sizeof(float) * (size_t)M * DX);
+        cs = fwd ? take(sizeof(float) * (size_t)M) : o;
+        marks = take(sizeof(uint16_t) * (size_t)M);      // fwd: range marks; bwd: tape row
+        starts = fwd ? o : take(sizeof(uint16_t) * (size_t)M);
+        red = take(sizeof(float4) * 2 * 32);
+        scanw = take(sizeof(unsigned long long) * 32);
+        scanwi = take(sizeof(int) * 32);
+        dred = fwd ? o : take(sizeof(double) * (size_t)D * 32);
+        total = o;
+    }
+};
+
+SMC2_HD inline int pf_threads(int M, int P) {
+    const int chunks = (M + P - 1) / P;
+    return ((chunks + 31) / 32) * 32;
+}
+
+// Host-side launchers, one per (model, particles-per-thread) instantiation.
+typedef int (*pf_launch_fn)(const PFArgs& a, int threads, size_t smem_fwd, size_t smem_bwd,
+                            void* stream, int grid_fwd, int grid_bwd);
+
+}  // namespace smc2

@@ -1,0 +1,64 @@
+// runtime.h -- internal host-side state of the C ABI (not part of the public header).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include "../../include/smc2.h"
+#include "outer.cuh"
+#include "pf_args.h"
+
+namespace smc2 {
+
+struct Sizes {
+    int n_slots = 0;
+    size_t xck = 0, lwck = 0, xseg = 0, lwseg = 0, anc = 0, flag = 0, steps = 0, state = 0, obs = 0, total = 0;
+};
+
+int fail(int code, const std::string& msg);
+void count_launches(int n);
+int family_dims(const smc2_config* c, int* D);
+int validate(const smc2_config* c, int* D);
+pf_launch_fn select_kernel(const smc2_config* c, int P);
+int choose_ppt(const smc2_config* c);
+int choose_kc(const smc2_config* c);
+void plan_sizes(const smc2_config* c, int D, int kc, Sizes* s);
+
+}  // namespace smc2
+
+struct smc2_handle {
+    smc2_config cfg{};        // copy; pointer members cleared
+    int D = 0, P = 4, threads = 32, kc = 1;
+    smc2::Sizes sizes;
+    size_t footprint = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    smc2::pf_launch_fn pf = nullptr;
+    // device state
+    float *y = nullptr, *H = nullptr;
+    double *prior_m = nullptr, *prior_s = nullptr;
+    double *theta = nullptr, *theta_new = nullptr, *logw = nullptr, *logpi = nullptr, *gradpi = nullptr;
+    double *loglik = nullptr, *ll_new = nullptr, *grad_new = nullptr, *tmp = nullptr, *stats = nullptr;
+    int* outer_anc = nullptr;
+    uint32_t* k_dev = nullptr;
+    float *xck = nullptr, *lwck = nullptr, *xseg = nullptr, *lwseg = nullptr, *mstep = nullptr, *lstep = nullptr;
+    uint16_t* anc = nullptr;
+    uint8_t* flag = nullptr;
+    double* h_stats = nullptr;  // pinned
+    uint32_t k = 0;             // iterations enqueued
+    cudaGraphExec_t graph_exec = nullptr;
+    bool no_graph = false;
+    int launches_per_step = 0;
+};
+
+namespace smc2 {
+PFArgs make_pf_args(smc2_handle* h, const double* theta, int n, uint32_t iter, uint32_t row0,
+                    const uint32_t* iter_dev, double* loglik, double* grad);
+int launch_filters(smc2_handle* h, const PFArgs& a);
+OuterArgs make_outer_args(smc2_handle* h);
+int enqueue_step(smc2_handle* h);
+int step_async(smc2_handle* h);
+int read_stats(smc2_handle* h, smc2_stats* out);
+}  // namespace smc2

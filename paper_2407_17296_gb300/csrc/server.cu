@@ -1,0 +1,385 @@
+// server.cu -- continuous-batching request loop and the launch-configuration autotuner.
+//
+// Serving: jobs (each an SMC^2 inference problem with its own model, sizes and
+// data) are queued by smc2_submit.  A worker thread admits queued jobs in
+// arrival order while their device footprint fits the HBM budget and fewer than
+// max_active run; an admitted job keeps all of its state on the device and
+// advances one SMC^2 iteration at a time on its own stream, so iterations of
+// different jobs overlap on the GPU and a finished job frees its slot and memory
+// for the next arrival at once.  smc2_poll reports completion and hands back the
+// final samples, weights and the recycled posterior-mean estimate.
+//
+// Autotuner: for a model shape it times every supported particles-per-thread
+// value and a few checkpoint intervals on the current device with CUDA events
+// and caches the fastest choice in-process.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <tuple>
+#include <vector>
+
+#include "../../include/smc2.h"
+#include "runtime.h"
+
+using namespace smc2;
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Job {
+    uint64_t id = 0;
+    smc2_config cfg{};
+    std::vector<float> y, H;
+    std::vector<double> pm, ps;
+    int D = 0;
+    size_t bytes = 0;
+    enum State { kQueued, kActive, kDone, kCancelled } state = kQueued;
+    smc2_handle* h = nullptr;
+    cudaEvent_t ev = nullptr;
+    bool in_flight = false;
+    int k_done = 0;
+    int status = SMC2_OK;
+    Clock::time_point t_submit, t_admit, t_done;
+    std::vector<double> theta, logw, recycled;
+};
+
+}  // namespace
+
+struct smc2_server {
+    size_t budget = 0, used = 0;
+    int max_active = 1;
+    int device = 0;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::map<uint64_t, std::unique_ptr<Job>> jobs;
+    std::deque<uint64_t> pending;
+    std::vector<Job*> active;
+    uint64_t next_id = 1;
+    bool stop = false;
+    std::thread worker;
+};
+
+namespace {
+
+void finish_job(smc2_server* s, Job* j, int status) {
+    if (j->h) {
+        if (status == SMC2_OK) {
+            j->theta.assign((size_t)j->cfg.N * j->D, 0.0);
+            j->logw.assign(j->cfg.N, 0.0);
+            j->recycled.assign(j->D, 0.0);
+            int rc = smc2_get_samples(j->h, j->theta.data(), j->logw.data());
+            smc2_stats st{};
+            st.recycled_mean = j->recycled.data();
+            if (!rc) rc = read_stats(j->h, &st);
+            if (rc) status = rc;
+        }
+        smc2_destroy(j->h);
+        j->h = nullptr;
+    }
+    if (j->ev) {
+        cudaEventDestroy(j->ev);
+        j->ev = nullptr;
+    }
+    s->used -= j->bytes;
+    j->status = status;
+    j->t_done = Clock::now();
+    if (j->state != Job::kCancelled) j->state = Job::kDone;
+}
+
+void worker_loop(smc2_server* s) {
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (!s->stop) {
+        bool progressed = false;
+        // admission in arrival order, by footprint and slot count
+        while (!s->pending.empty() && (int)s->active.size() < s->max_active) {
+            auto it = s->jobs.find(s->pending.front());
+            if (it == s->jobs.end() || it->second->state != Job::kQueued) {
+                s->pending.pop_front();
+                continue;
+            }
+            Job* j = it->second.get();
+            if (s->used + j->bytes > s->budget) break;
+            s->pending.pop_front();
+            smc2_config c = j->cfg;
+            c.y = j->y.data();
+            c.y_on_device = 0;
+            c.H = j->H.empty() ? nullptr : j->H.data();
+            c.prior_mean = j->pm.empty() ? nullptr : j->pm.data();
+            c.prior_std = j->ps.empty() ? nullptr : j->ps.data();
+            c.stream = nullptr;
+            s->used += j->bytes;
+            j->t_admit = Clock::now();
+            int rc = smc2_create(&c, &j->h);
+            if (rc == SMC2_OK && cudaEventCreateWithFlags(&j->ev, cudaEventDisableTiming) != cudaSuccess)
+                rc = SMC2_E_CUDA;
+            if (rc != SMC2_OK) {
+                finish_job(s, j, rc);
+                continue;
+            }
+            j->state = Job::kActive;
+            s->active.push_back(j);
+            progressed = true;
+        }
+        // advance every active job by one iteration when its previous one has finished
+        for (size_t a = 0; a < s->active.size();) {
+            Job* j = s->active[a];
+            if (j->state == Job::kCancelled) {
+                if (j->h) cudaStreamSynchronize(j->h->stream);
+                finish_job(s, j, SMC2_E_NOTFOUND);
+                s->active.erase(s->active.begin() + a);
+                progressed = true;
+                continue;
+            }
+            if (j->in_flight) {
+                const cudaError_t q = cudaEventQuery(j->ev);
+                if (q == cudaErrorNotReady) {
+                    ++a;
+                    continue;
+                }
+                j->in_flight = false;
+                progressed = true;
+                if (q != cudaSuccess) {
+                    finish_job(s, j, SMC2_E_CUDA);
+                    s->active.erase(s->active.begin() + a);
+                    continue;
+                }
+                ++j->k_done;
+            }
+            if (j->k_done >= j->cfg.K_iters) {
+                finish_job(s, j, SMC2_OK);
+                s->active.erase(s->active.begin() + a);
+                progressed = true;
+                continue;
+            }
+            int rc = step_async(j->h);
+            if (rc == SMC2_OK && cudaEventRecord(j->ev, j->h->stream) != cudaSuccess) rc = SMC2_E_CUDA;
+            if (rc != SMC2_OK) {
+                finish_job(s, j, rc);
+                s->active.erase(s->active.begin() + a);
+                continue;
+            }
+            j->in_flight = true;
+            progressed = true;
+            ++a;
+        }
+        if (!progressed) {
+            if (s->active.empty() && s->pending.empty())
+                s->cv.wait(lk);
+            else
+                s->cv.wait_for(lk, std::chrono::microseconds(50));
+        }
+    }
+    for (Job* j : s->active) {
+        if (j->h) cudaStreamSynchronize(j->h->stream);
+        j->state = Job::kCancelled;
+        finish_job(s, j, SMC2_E_NOTFOUND);
+    }
+    s->active.clear();
+}
+
+}  // namespace
+
+extern "C" int smc2_server_create(size_t hbm_budget, int max_active, smc2_server** out) {
+    if (!out || hbm_budget == 0 || max_active < 1) return fail(SMC2_E_INVAL, "bad server arguments");
+    auto* s = new smc2_server();
+    s->budget = hbm_budget;
+    s->max_active = max_active;
+    if (cudaGetDevice(&s->device) != cudaSuccess) {
+        delete s;
+        return fail(SMC2_E_CUDA, "cudaGetDevice failed");
+    }
+    s->worker = std::thread(worker_loop, s);
+    *out = s;
+    return SMC2_OK;
+}
+
+extern "C" int smc2_submit(smc2_server* s, const smc2_config* cfg, uint64_t* job_id) {
+    if (!s || !job_id) return fail(SMC2_E_INVAL, "NULL argument");
+    int D = 0;
+    int rc = validate(cfg, &D);
+    if (rc) return rc;
+    if (cfg->y_on_device) return fail(SMC2_E_INVAL, "served jobs take host observations");
+    size_t bytes = 0;
+    rc = smc2_footprint(cfg, &bytes);
+    if (rc) return rc;
+    if (bytes > s->budget) return fail(SMC2_E_NOMEM, "job footprint exceeds the server's HBM budget");
+    if (cfg->K_iters < 1) return fail(SMC2_E_INVAL, "K_iters must be >= 1");
+    auto j = std::make_unique<Job>();
+    j->cfg = *cfg;
+    j->D = D;
+    j->bytes = bytes;
+    j->y.assign(cfg->y, cfg->y + (size_t)cfg->T * cfg->d_y);
+    if (cfg->H) j->H.assign(cfg->H, cfg->H + (size_t)cfg->d_y * cfg->d_x);
+    if (cfg->prior_mean) j->pm.assign(cfg->prior_mean, cfg->prior_mean + D);
+    if (cfg->prior_std) j->ps.assign(cfg->prior_std, cfg->prior_std + D);
+    j->t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        j->id = s->next_id++;
+        *job_id = j->id;
+        s->pending.push_back(j->id);
+        s->jobs[j->id] = std::move(j);
+    }
+    s->cv.notify_all();
+    return SMC2_OK;
+}
+
+extern "C" int smc2_poll(smc2_server* s, uint64_t job_id, smc2_result* out) {
+    if (!s) return fail(SMC2_E_INVAL, "NULL server");
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->jobs.find(job_id);
+    if (it == s->jobs.end()) return fail(SMC2_E_NOTFOUND, "unknown job id");
+    Job* j = it->second.get();
+    if (j->state == Job::kQueued || j->state == Job::kActive) return SMC2_PENDING;
+    if (j->state == Job::kCancelled) {
+        s->jobs.erase(it);
+        return fail(SMC2_E_NOTFOUND, "job was cancelled");
+    }
+    if (out) {
+        out->status = j->status;
+        out->K = j->k_done;
+        out->latency_s = std::chrono::duration<double>(j->t_done - j->t_submit).count();
+        out->queue_s = std::chrono::duration<double>(j->t_admit - j->t_submit).count();
+        if (out->theta && !j->theta.empty()) std::memcpy(out->theta, j->theta.data(), sizeof(double) * j->theta.size());
+        if (out->logw && !j->logw.empty()) std::memcpy(out->logw, j->logw.data(), sizeof(double) * j->logw.size());
+        if (out->recycled_mean && !j->recycled.empty())
+            std::memcpy(out->recycled_mean, j->recycled.data(), sizeof(double) * j->recycled.size());
+    }
+    s->jobs.erase(it);
+    return SMC2_OK;
+}
+
+extern "C" int smc2_cancel(smc2_server* s, uint64_t job_id) {
+    if (!s) return fail(SMC2_E_INVAL, "NULL server");
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = s->jobs.find(job_id);
+        if (it == s->jobs.end() || it->second->state == Job::kDone) return fail(SMC2_E_NOTFOUND, "unknown or finished job");
+        Job* j = it->second.get();
+        if (j->state == Job::kQueued) {
+            j->state = Job::kCancelled;
+        } else {
+            j->state = Job::kCancelled;  // the worker releases it
+        }
+    }
+    s->cv.notify_all();
+    return SMC2_OK;
+}
+
+extern "C" int smc2_server_destroy(smc2_server* s) {
+    if (!s) return fail(SMC2_E_INVAL, "NULL server");
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    delete s;
+    return SMC2_OK;
+}
+
+// ------------------------------------------------------------------ autotuner
+
+namespace {
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int, int, int>, std::pair<int, int>> g_tune_cache;
+}  // namespace
+
+extern "C" int smc2_autotune(const smc2_config* cfg, int* ppt, int* ckpt) {
+    int D = 0;
+    int rc = validate(cfg, &D);
+    if (rc) return rc;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const auto key = std::make_tuple(dev, cfg->model_family, cfg->d_x, cfg->M, cfg->N, cfg->T, cfg->pf_resample);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            if (ppt) *ppt = it->second.first;
+            if (ckpt) *ckpt = it->second.second;
+            return SMC2_OK;
+        }
+    }
+    const int Tt = cfg->T < 64 ? cfg->T : 64;  // time a prefix of the series; cost is linear in T
+    const int kcs[] = {1, 4, 8, 16};
+    const int ps[] = {1, 2, 4, 8};
+    double* th = nullptr;
+    double* ll = nullptr;
+    double* g = nullptr;
+    const size_t N = cfg->N;
+    if (cudaMalloc(&th, sizeof(double) * N * D) != cudaSuccess) return fail(SMC2_E_NOMEM, "autotune alloc");
+    cudaMalloc(&ll, sizeof(double) * N);
+    cudaMalloc(&g, sizeof(double) * N * D);
+    std::vector<double> th0(N * D, 0.0);
+    for (size_t i = 0; i < N; ++i)
+        for (int d = 0; d < D; ++d) th0[i * D + d] = cfg->prior_mean ? cfg->prior_mean[d] : 0.0;
+    cudaMemcpy(th, th0.data(), sizeof(double) * N * D, cudaMemcpyHostToDevice);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int bp = choose_ppt(cfg), bk = choose_kc(cfg);
+    for (int P : ps) {
+        if (pf_threads(cfg->M, P) > 512) continue;
+        for (int kc : kcs) {
+            if (kc > Tt) continue;
+            smc2_config c = *cfg;
+            c.T = Tt;
+            c.particles_per_thread = P;
+            c.ckpt_every = kc;
+            c.stream = nullptr;
+            smc2_handle* h = nullptr;
+            if (smc2_create(&c, &h) != SMC2_OK) {
+                cudaGetLastError();
+                continue;
+            }
+            float ms = 1e30f;
+            bool okrun = pf_loglik_grad(h, th, (int)N, 1, ll, g) == SMC2_OK;  // warm-up
+            for (int rep = 0; rep < 3 && okrun; ++rep) {
+                cudaEventRecord(e0, h->stream);
+                okrun = pf_loglik_grad(h, th, (int)N, 1, ll, g) == SMC2_OK;
+                cudaEventRecord(e1, h->stream);
+                cudaEventSynchronize(e1);
+                float t = 0.f;
+                cudaEventElapsedTime(&t, e0, e1);
+                if (t < ms) ms = t;
+            }
+            // checkpointing trades memory for recomputation: prefer storing every step only
+            // while it fits the same trajectory budget the heuristic uses
+            smc2_config full = *cfg;
+            full.ckpt_every = kc;
+            Sizes sz;
+            plan_sizes(&full, D, kc, &sz);
+            const bool fits = (double)(sz.xck + sz.lwck + sz.xseg + sz.lwseg) <= 16.0e9;
+            if (okrun && fits && ms < best) {
+                best = ms;
+                bp = P;
+                bk = kc;
+            }
+            smc2_destroy(h);
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(th);
+    cudaFree(ll);
+    cudaFree(g);
+    cudaGetLastError();
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = {bp, bk};
+    }
+    if (ppt) *ppt = bp;
+    if (ckpt) *ckpt = bk;
+    return SMC2_OK;
+}

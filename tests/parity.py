@@ -1,0 +1,63 @@
+"""Shared helpers of the GPU parity tests: run the CUDA path, compare with the oracle.
+
+Tolerances (stated once, used everywhere):
+  * ancestor indices and resample decisions: bit-exact, except where a
+    cumulative weight lies within BAND = 1e-6 of a threshold (near-ties); the
+    oracle then follows the GPU's choice and counts the case;
+  * log-likelihood: |ll_gpu - ll_cpu| <= 1e-4 * max(1, |ll_cpu|);
+  * gradient: max_d |g_gpu - g_cpu| <= 1e-3 * max(1, max_d |g_cpu|);
+  * posterior means: |m_gpu - m_cpu| <= 1e-3 * max(1, |m_cpu|).
+"""
+from collections import Counter
+
+import numpy as np
+
+import oracle
+
+BAND = 1e-6
+LL_RTOL = 1e-4
+GRAD_RTOL = 1e-3
+MEAN_RTOL = 1e-3
+
+
+def gpu_pf(w, theta, iteration=1, row0=0, want_grad=True, **cfgkw):
+    """Run pf_loglik_grad through the C ABI; returns (ll, grad, anc, flag) as numpy."""
+    import torch
+    from paper_2407_17296_gb300 import binding
+    cfg = binding.config_for(w, **cfgkw)
+    n = theta.shape[0]
+    with binding.Handle(cfg) as h:
+        th = torch.tensor(theta, dtype=torch.float64, device="cuda")
+        ll = torch.empty(n, dtype=torch.float64, device="cuda")
+        g = torch.empty(n, w.D, dtype=torch.float64, device="cuda") if want_grad else None
+        h.pf_loglik_grad(th, iteration, ll, g, row0=row0)
+        torch.cuda.synchronize()
+        anc, flag, _, _ = h.trace()
+    return (ll.cpu().numpy(), None if g is None else g.cpu().numpy(), anc[:n], flag[:n])
+
+
+def check_rows(w, theta, ll, g, anc, flag, rows, iteration=1, row0=0, scheme=0, ess_frac=0.5,
+               band=BAND):
+    """Oracle in follow mode for each sampled row; asserts the tolerances; returns counters."""
+    agg = Counter()
+    for i in rows:
+        r = oracle.pf(w.family, w.dx, w.dy, w.H, theta[i], w.y, w.M, w.seed, iteration, row0 + i,
+                      scheme=scheme, ess_frac=ess_frac, want_grad=g is not None,
+                      hint_anc=anc[i], hint_flag=flag[i], band=band, flag_band=band)
+        st = r["stats"]
+        agg.update(st)
+        assert st["nontie_mismatch"] == 0, (i, st, r["worst"])
+        assert st["flag_mismatch"] == 0, (i, st)
+        assert st["bad_hint"] == 0, (i, st)
+        np.testing.assert_array_equal(r["flag"], flag[i])
+        fl = flag[i] == 1
+        np.testing.assert_array_equal(r["anc"][fl], anc[i][fl])
+        ref = r["loglik"]
+        assert abs(ll[i] - ref) <= LL_RTOL * max(1.0, abs(ref)), (i, ll[i], ref)
+        if g is not None:
+            gmax = max(1.0, float(np.abs(r["grad"]).max()))
+            err = float(np.abs(g[i] - r["grad"]).max())
+            assert err <= GRAD_RTOL * gmax, (i, g[i], r["grad"], err / gmax)
+            agg["grad_rel_err_max_e9"] = max(agg["grad_rel_err_max_e9"], int(1e9 * err / gmax))
+        agg["ll_abs_err_max_e9"] = max(agg["ll_abs_err_max_e9"], int(1e9 * abs(ll[i] - ref)))
+    return agg

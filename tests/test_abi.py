@@ -1,0 +1,95 @@
+"""The C-ABI library loads and exports every symbol include/smc2.h declares, and its
+host-side validation works without a GPU (no device calls are made here)."""
+import ctypes
+import os
+import re
+import shutil
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "smc2.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2407_17296_gb300 import binding, build
+    if not os.path.exists(binding.LIB_PATH):
+        if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+            pytest.skip("no nvcc to build the library")
+        build.build_library()
+    return binding.load()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^[A-Za-z_][\w\s\*]*?\b([a-z_0-9]+)\s*\([^;{]*\)\s*;", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("smc2_create", "pf_loglik_grad", "smc2_step", "smc2_submit", "smc2_poll",
+                     "smc2_destroy", "smc2_last_error"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2407_17296_gb300 import binding
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert name in binding.EXPORTS, name
+
+
+def test_config_layout_matches(lib):
+    from paper_2407_17296_gb300 import binding
+    c = binding.Config()
+    lib.smc2_config_init(ctypes.byref(c))
+    assert c.struct_size == ctypes.sizeof(binding.Config)
+    assert c.ess_frac == pytest.approx(0.5) and c.pf_resample == binding.SYSTEMATIC
+
+
+def _cfg(**kw):
+    from paper_2407_17296_gb300 import binding, workloads
+    w = workloads.lg4(T=50, N=16, M=64)
+    return binding.config_for(w, **kw)
+
+
+def test_footprint_scales_with_sizes(lib):
+    from paper_2407_17296_gb300 import binding
+    b1 = binding.footprint(_cfg(ckpt_every=1))
+    b4 = binding.footprint(_cfg(ckpt_every=4))
+    assert b1 > b4 > 0
+    # trajectory of (x, log w) for every step dominates at ckpt_every = 1
+    N, M, T, dx = 16, 64, 50, 4
+    assert b1 >= N * (T + 1) * M * (4 * dx + 4) + N * T * M * 2
+
+
+@pytest.mark.parametrize("field,value,code", [
+    ("D", 7, -1), ("M", 5000, -1), ("N", 0, -1), ("T", 0, -1), ("ess_frac", 1.5, -1),
+    ("pf_resample", 3, -1), ("proposal", 9, -1), ("gamma", 0.0, -1), ("particles_per_thread", 3, -1),
+    ("d_x", 3, -1), ("struct_size", 12, -1), ("model_family", 7, -1)])
+def test_invalid_configs_are_rejected(lib, field, value, code):
+    from paper_2407_17296_gb300 import binding
+    c = _cfg()
+    setattr(c, field, value)
+    b = ctypes.c_size_t(0)
+    assert lib.smc2_footprint(ctypes.byref(c), ctypes.byref(b)) == code
+    assert len(binding.last_error()) > 0
+
+
+def test_null_arguments_are_rejected(lib):
+    assert lib.smc2_destroy(None) == -1
+    assert lib.smc2_step(None, None) == -1
+    assert lib.pf_loglik_grad(None, None, 1, 1, None, None) == -1
+    assert lib.smc2_poll(None, 1, None) == -1
+    h = ctypes.c_void_p()
+    assert lib.smc2_create(None, ctypes.byref(h)) == -1
+
+
+def test_server_rejects_bad_arguments_without_device(lib):
+    s = ctypes.c_void_p()
+    assert lib.smc2_server_create(0, 1, ctypes.byref(s)) == -1
+    assert lib.smc2_server_create(1 << 30, 0, ctypes.byref(s)) == -1

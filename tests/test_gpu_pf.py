@@ -1,0 +1,165 @@
+"""GPU parity of the CRN particle filter (forward + adjoint) against the FP64 oracle.
+
+All calls go through the C ABI (libsmc2.so).  Small cases span several warps
+and a ragged particle tail; the full-size cases run the whole launch of the
+benchmark's configuration and check sampled filters one by one.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2407_17296_gb300 import workloads as W
+
+from .parity import BAND, check_rows, gpu_pf
+
+pytestmark = pytest.mark.gpu
+
+
+def _report(name, agg):
+    print(f"\n[{name}] " + ", ".join(f"{k}={v}" for k, v in sorted(agg.items())))
+
+
+@pytest.mark.parametrize("make,T,M,n", [(W.lg1, 80, 300, 9), (W.lg4, 60, 1000, 7), (W.sv, 90, 517, 6)])
+@pytest.mark.parametrize("scheme", [0, 1])
+@pytest.mark.parametrize("kc", [1, 7])
+def test_parity_small(make, T, M, n, scheme, kc):
+    w = make(T=T, N=n, M=M)
+    theta = W.thetas_near(w, n, 0.05, seed=11)
+    ll, g, anc, flag = gpu_pf(w, theta, iteration=3, pf_resample=scheme, ckpt_every=kc)
+    agg = check_rows(w, theta, ll, g, anc, flag, range(n), iteration=3, scheme=scheme)
+    assert agg["resample_steps"] > 0
+    _report(f"{w.name} T={T} M={M} scheme={scheme} kc={kc}", agg)
+
+
+@pytest.mark.parametrize("ppt", [1, 2, 4, 8])
+def test_parity_particles_per_thread(ppt):
+    w = W.lg4(T=40, N=3, M=333)
+    theta = W.thetas_near(w, 3, 0.05, seed=5)
+    ll, g, anc, flag = gpu_pf(w, theta, particles_per_thread=ppt, ckpt_every=3)
+    check_rows(w, theta, ll, g, anc, flag, range(3))
+
+
+def test_parity_full_size_lg4():
+    """Full linear-Gaussian workload (N=1024, M=1024, T=250) in the benchmark's launch
+    configuration; sampled filters checked one by one."""
+    w = W.lg4()
+    theta = W.thetas_near(w, w.N, 0.05, seed=21)
+    ll, g, anc, flag = gpu_pf(w, theta, iteration=2)
+    assert np.all(np.isfinite(ll)) and np.all(np.isfinite(g))
+    agg = check_rows(w, theta, ll, g, anc, flag, [0, 1, 513, 1022, 1023], iteration=2)
+    _report("lg4 full", agg)
+
+
+def test_parity_full_size_sv():
+    w = W.sv()
+    theta = W.thetas_near(w, w.N, 0.05, seed=22)
+    ll, g, anc, flag = gpu_pf(w, theta, iteration=2)
+    assert np.all(np.isfinite(ll)) and np.all(np.isfinite(g))
+    agg = check_rows(w, theta, ll, g, anc, flag, [0, 2047, 4095], iteration=2)
+    _report("sv full", agg)
+
+
+def test_checkpoint_interval_does_not_change_results():
+    w = W.lg4(T=45, N=5, M=200)
+    theta = W.thetas_near(w, 5, 0.05)
+    ref = gpu_pf(w, theta, ckpt_every=1)
+    for kc in (2, 4, 16, 45, 64):
+        out = gpu_pf(w, theta, ckpt_every=kc)
+        np.testing.assert_array_equal(out[0], ref[0])
+        np.testing.assert_allclose(out[1], ref[1], rtol=1e-6, atol=1e-9)
+
+
+def test_deterministic_and_row_offset():
+    w = W.lg4(T=30, N=8, M=128)
+    theta = W.thetas_near(w, 8, 0.05)
+    a = gpu_pf(w, theta)
+    b = gpu_pf(w, theta)
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
+    # rows 3.. launched on their own with the Philox row offset give the same filters
+    c = gpu_pf(w, theta[3:], row0=3)
+    np.testing.assert_array_equal(c[0], a[0][3:])
+    np.testing.assert_array_equal(c[1], a[1][3:])
+
+
+def test_single_particle_closed_form():
+    """M = 1: resampling is the identity and log p-hat is the path density."""
+    w = W.lg4(T=50, N=2, M=1)
+    theta = W.thetas_near(w, 2, 0.1)
+    ll, g, anc, flag = gpu_pf(w, theta)
+    for i in range(2):
+        r = oracle.pf(0, 4, 2, w.H, theta[i], w.y, 1, w.seed, 1, i)
+        assert abs(ll[i] - r["loglik"]) <= 1e-4 * abs(r["loglik"])
+        np.testing.assert_allclose(g[i], r["grad"], rtol=1e-3, atol=1e-3)
+
+
+def test_single_step_and_forward_only():
+    w = W.lg1(T=1, N=3, M=64)
+    theta = W.thetas_near(w, 3, 0.1)
+    ll, g, anc, flag = gpu_pf(w, theta)
+    check_rows(w, theta, ll, g, anc, flag, range(3))
+    ll2, g2, _, _ = gpu_pf(w, theta, want_grad=False)
+    np.testing.assert_array_equal(ll, ll2)
+    assert g2 is None
+
+
+@pytest.mark.parametrize("ess_frac", [0.0, 1.0])
+def test_never_and_always_resample(ess_frac):
+    w = W.lg4(T=30, N=3, M=256)
+    theta = W.thetas_near(w, 3, 0.05)
+    ll, g, anc, flag = gpu_pf(w, theta, ess_frac=ess_frac)
+    if ess_frac == 0.0:
+        assert flag.sum() == 0
+    else:
+        assert np.all(flag[:, 1:] == 1)
+    check_rows(w, theta, ll, g, anc, flag, range(3), ess_frac=ess_frac)
+
+
+def test_degenerate_filter_reports_minus_inf():
+    """Exploding dynamics overflow FP32 for every particle: log p-hat = -inf, gradient 0,
+    and the neighbouring filters of the launch are unaffected."""
+    w = W.lg1(T=100, N=3, M=64)
+    theta = W.thetas_near(w, 3, 0.05)
+    theta[1, 0] = 40.0
+    ll, g, anc, flag = gpu_pf(w, theta)
+    assert ll[1] == -np.inf and np.all(g[1] == 0.0)
+    check_rows(w, theta, ll, g, anc, flag, [0, 2])
+
+
+def test_zero_rows_is_a_noop():
+    import torch
+    from paper_2407_17296_gb300 import binding
+    w = W.lg1(T=10, N=4, M=32)
+    with binding.Handle(binding.config_for(w)) as h:
+        th = torch.zeros(0, 3, dtype=torch.float64, device="cuda")
+        ll = torch.zeros(0, dtype=torch.float64, device="cuda")
+        h.pf_loglik_grad(th, 1, ll, None)
+        torch.cuda.synchronize()
+
+
+def test_host_buffer_entry_point_matches_device():
+    from paper_2407_17296_gb300 import binding
+    w = W.lg4(T=25, N=6, M=100)
+    theta = W.thetas_near(w, 6, 0.05)
+    ll_d, g_d, _, _ = gpu_pf(w, theta)
+    with binding.Handle(binding.config_for(w)) as h:
+        ll = np.zeros(6)
+        g = np.zeros((6, w.D))
+        h.pf_loglik_grad_host(np.ascontiguousarray(theta), 1, ll, g)
+    np.testing.assert_array_equal(ll, ll_d)
+    np.testing.assert_array_equal(g, g_d)
+
+
+def test_autograd_function():
+    import torch
+    from paper_2407_17296_gb300 import autograd, binding
+    w = W.lg4(T=20, N=4, M=128)
+    theta = W.thetas_near(w, 4, 0.05)
+    ll_ref, g_ref, _, _ = gpu_pf(w, theta)
+    with binding.Handle(binding.config_for(w)) as h:
+        th = torch.tensor(theta, dtype=torch.float64, device="cuda", requires_grad=True)
+        ll = autograd.loglik(th, h, 1)
+        wts = torch.arange(1, 5, dtype=torch.float64, device="cuda")
+        (ll * wts).sum().backward()
+        np.testing.assert_array_equal(ll.detach().cpu().numpy(), ll_ref)
+        np.testing.assert_allclose(th.grad.cpu().numpy(), g_ref * np.arange(1, 5)[:, None], rtol=1e-12)

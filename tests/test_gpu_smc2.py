@@ -1,0 +1,85 @@
+"""GPU parity of the full SMC^2 iteration (proposal, filters, L-kernel weights, normalise,
+ESS, estimate, recycling, resampling) against the FP64 oracle sampler."""
+import numpy as np
+import pytest
+
+import oracle.smc2 as osmc2
+from paper_2407_17296_gb300 import workloads as W
+
+from .parity import BAND, MEAN_RTOL
+
+pytestmark = pytest.mark.gpu
+
+
+def _run_gpu(w, K, **kw):
+    from paper_2407_17296_gb300 import binding
+    recs, hints = [], []
+    with binding.Handle(binding.config_for(w, **kw)) as h:
+        for _ in range(K):
+            st = h.step()
+            anc, flag, oanc, ores = h.trace()
+            th, lw = h.samples()
+            recs.append(dict(st, theta=th, logw=lw))
+            hints.append({"pf_anc": anc, "pf_flag": flag, "outer_anc": oanc, "outer_flag": ores})
+    return recs, hints
+
+
+def _compare(recs, ref, rec_ref=None, weight_floor=1e-12):
+    """Per iteration: decisions of every filter that carries weight match the oracle's
+    (near-ties excepted); means, ESS and the resampling decision agree.  Samples of
+    negligible weight (e.g. prior draws with explosive dynamics, whose FP32 states overflow
+    to a -inf log-likelihood while FP64 stays finite) are excluded from the decision check:
+    they contribute nothing to any estimate on either side."""
+    ties = 0
+    for g, r in zip(recs, ref):
+        lw = r["logw"]
+        wn = np.exp(lw - lw.max())
+        alive = np.nonzero(wn > weight_floor)[0]
+        for i in alive:
+            st = r["pf_stats_rows"][i]
+            assert st["nontie_mismatch"] == 0 and st["flag_mismatch"] == 0, (r["k"], i, st)
+            ties += st["tie_followed"]
+        assert r["outer_stats"].get("nontie_mismatch", 0) == 0, r["outer_stats"]
+        assert "flag_disagree" not in r["outer_stats"]
+        assert g["k"] == r["k"] and g["resampled"] == r["resampled"]
+        np.testing.assert_allclose(g["mean"], r["mean"], rtol=0,
+                                   atol=MEAN_RTOL * max(1.0, float(np.abs(r["mean"]).max())))
+        assert abs(g["ess"] - r["ess"]) <= 1e-3 * r["ess"], (g["ess"], r["ess"])
+        th_ref = r["theta"][r["ancestors"]] if r["resampled"] else r["theta"]
+        rows = np.arange(len(th_ref))
+        src = r["ancestors"] if r["resampled"] else rows
+        keep = np.isin(src, alive)
+        np.testing.assert_allclose(g["theta"][keep], th_ref[keep], rtol=1e-5, atol=1e-5)
+    if rec_ref is not None:
+        np.testing.assert_allclose(recs[-1]["recycled_mean"], rec_ref, rtol=0,
+                                   atol=MEAN_RTOL * max(1.0, float(np.abs(rec_ref).max())))
+    return ties
+
+
+@pytest.mark.parametrize("proposal", ["langevin", "rw"])
+def test_smc2_matches_oracle_lg1(proposal):
+    """The small linear-Gaussian workload end to end: N=64, M=128, T=100, 10 iterations,
+    N(0, I) prior."""
+    w = W.lg1(proposal=proposal)
+    recs, hints = _run_gpu(w, w.K)
+    ref, rec_ref = osmc2.run(w.family, 1, 1, None, w.y, w.N, w.M, w.K, w.gamma, proposal, w.seed,
+                             hints=hints, band=BAND, flag_band=BAND)
+    ties = _compare(recs, ref, rec_ref)
+    print(f"\n[smc2 lg1 {proposal}] PF near-ties followed: {ties}; final mean {recs[-1]['mean']}")
+
+
+def test_smc2_sv_small_matches_oracle():
+    w = W.sv(T=60, N=32, M=128, K=5)
+    recs, hints = _run_gpu(w, w.K)
+    ref, _ = osmc2.run(w.family, 1, 1, None, w.y, w.N, w.M, w.K, w.gamma, "langevin", w.seed,
+                       hints=hints, band=BAND, flag_band=BAND)
+    _compare(recs, ref)
+
+
+def test_smc2_invariants_full_lg4():
+    """Full-size linear-Gaussian job: three iterations stay finite with ESS in [1, N]."""
+    w = W.lg4(K=3)
+    recs, _ = _run_gpu(w, 3)
+    for r in recs:
+        assert 1.0 <= r["ess"] <= w.N + 1e-6
+        assert np.all(np.isfinite(r["mean"]))
