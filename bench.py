@@ -39,12 +39,14 @@ ALG_OPS = {"lg1": 60 + 24, "lg4": 94 + 47, "sv": 64 + 30, "lg16": 4 * 84 + 16 * 
 def _args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
-    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="lg4")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--N", type=int, default=0, help="override the number of samples (profiling runs)")
+    p.add_argument("--no-autotune", action="store_true", help="use the default launch configuration")
     return p.parse_args()
 
 
@@ -163,14 +165,17 @@ def run_gpu(a, rank, world, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     w = workloads.ALL[a.workload]()
+    if a.N:
+        w = w.with_sizes(N=a.N)
     # weak scaling: every rank runs its own independent job (own seed), no data-path collective
     w.seed = w.seed + 1000 * rank
     binding.load()
     stream = torch.cuda.Stream(device=dev)
     cfg = binding.config_for(w, stream=stream.cuda_stream)
     ppt, kc = binding.ctypes.c_int(0), binding.ctypes.c_int(0)
-    binding.check(binding.load().smc2_autotune(binding.ctypes.byref(cfg), binding.ctypes.byref(ppt),
-                                               binding.ctypes.byref(kc)), "smc2_autotune")
+    if not a.no_autotune:
+        binding.check(binding.load().smc2_autotune(binding.ctypes.byref(cfg), binding.ctypes.byref(ppt),
+                                                   binding.ctypes.byref(kc)), "smc2_autotune")
     cfg = binding.config_for(w, stream=stream.cuda_stream, particles_per_thread=ppt.value,
                              ckpt_every=kc.value)
     h = binding.Handle(cfg)

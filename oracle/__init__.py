@@ -33,7 +33,7 @@ STREAM_OUTER_XI = 3
 STREAM_OUTER_NU = 4
 
 STAT_NAMES = ("near_ties", "tie_followed", "nontie_mismatch", "flag_ties",
-              "flag_mismatch", "resample_steps", "bad_hint")
+              "flag_mismatch", "resample_steps", "bad_hint", "tie_conditioned")
 
 _lib = None
 
@@ -65,6 +65,7 @@ def _load():
         ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,            # seed iter row
         ctypes.c_int, ctypes.c_double, ctypes.c_int,                  # scheme ess_frac want_grad
         vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_double,       # hints replay band flag_band
+        ctypes.c_double,                                              # band_rel
         vp, vp, vp, vp, vp, vp]                                       # outputs
     lib.oracle_pf.restype = ctypes.c_int
     _lib = lib
@@ -117,13 +118,15 @@ def ancestors(w, tau):
 
 def pf(family, dx, dy, H, theta, y, M, seed, it, row, scheme=SYSTEMATIC, ess_frac=0.5,
        want_grad=True, hint_anc=None, hint_flag=None, replay=False, band=1e-6,
-       flag_band=1e-6, want_tape=True):
+       flag_band=1e-6, want_tape=True, band_rel=0.0):
     """One CRN particle-filter run in FP64 (see oracle.c for the algorithm).
 
     family: LG_DIAG or SV; H: (dy, dx) float array or None for identity;
     theta: (D,) float64; y: (T, dy) observations (used as float32).
     Returns a dict with loglik, grad (D,), anc (T, M) uint16, flag (T,) uint8,
     stats (dict of counters) and worst (largest non-tie mismatch distance).
+    band_rel widens the tie band to max(band, band_rel * L) with L the accumulated largest
+    |log g| since the last resampling (see oracle.c); 0 keeps the fixed band.
     """
     lib = _load()
     theta = np.ascontiguousarray(theta, dtype=np.float64)
@@ -143,7 +146,7 @@ def pf(family, dx, dy, H, theta, y, M, seed, it, row, scheme=SYSTEMATIC, ess_fra
                        T, int(M), int(seed), int(it) & 0xFFFFFFFF, int(row) & 0xFFFFFFFF,
                        int(scheme), float(ess_frac), int(bool(want_grad)),
                        _ptr(ha), _ptr(hf), int(bool(replay)), float(band), float(flag_band),
-                       _ptr(ll), _ptr(grad), _ptr(anc), _ptr(flag), _ptr(stats), _ptr(worst))
+                       float(band_rel), _ptr(ll), _ptr(grad), _ptr(anc), _ptr(flag), _ptr(stats), _ptr(worst))
     if rc != 0:
         raise ValueError("oracle_pf rejected its arguments")
     return {"loglik": float(ll[0]), "grad": grad if want_grad else None, "anc": anc,

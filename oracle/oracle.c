@@ -255,6 +255,7 @@ enum {
     ST_FLAG_MISMATCH,      /* resample decisions that differed from the hint outside the band */
     ST_RESAMPLE_STEPS,     /* number of steps that resampled */
     ST_BAD_HINT,           /* hint ancestor out of range */
+    ST_TIE_COND,           /* followed differences outside band but inside the conditioned band */
     ST_COUNT
 };
 
@@ -288,6 +289,11 @@ static int first_at_least(const double* c, int M, double tau)
  *     the hint; differences are classified against the band (|c - tau| < band for
  *     ancestors, |ESS/(ess_frac*M) - 1| < band for the resample flag) and counted,
  *     and the hint is then followed so that later steps stay comparable.
+ *     band_rel >= 0 widens both bands to max(band, band_rel * L) where L is the sum, over
+ *     the steps since the last resampling, of the largest |log g| of the step: an FP32
+ *     evaluation of log w then carries an absolute error of order 2^-24 L, which moves
+ *     the cumulative weights by about as much.  Differences inside the widened band but
+ *     outside the base band are counted separately (ST_TIE_COND).
  *   outputs: loglik, grad[D] (if want_grad), anc_out[T*M], flag_out[T] (may be NULL),
  *     stats[ST_COUNT], worst[1] = largest |c - tau| distance of a non-tie mismatch.
  * Row t-1 of the tapes describes resampling before step t (row 0 is never used).
@@ -298,7 +304,7 @@ int oracle_pf(int family, int dx, int dy, int D, const double* H,
               uint64_t seed, uint32_t iter, uint32_t row,
               int scheme, double ess_frac, int want_grad,
               const uint16_t* hint_anc, const uint8_t* hint_flag, int replay, double band, double flag_band,
-              double* loglik, double* grad, uint16_t* anc_out, uint8_t* flag_out,
+              double band_rel, double* loglik, double* grad, uint16_t* anc_out, uint8_t* flag_out,
               long long* stats, double* worst)
 {
     or_model m = {family, dx, dy, D, H};
@@ -350,11 +356,13 @@ int oracle_pf(int family, int dx, int dy, int D, const double* H,
 
     int resample_next = 0;
     double ess_prev = (double)M;
+    double lacc = 0.0; /* sum of max |log g| per step since the last resampling */
     for (int t = 1; t <= T; ++t) {
         /* ---- resampling decision and CRN resampling before step t (App. B) ---- */
         if (t >= 2) {
             int own = resample_next;
             int use = own;
+            const double wide = band_rel * lacc;
             if (hint_flag) {
                 int h = hint_flag[t - 1] ? 1 : 0;
                 if (replay) {
@@ -362,6 +370,7 @@ int oracle_pf(int family, int dx, int dy, int D, const double* H,
                 } else if (h != own) {
                     double rel = fabs(ess_prev / (ess_frac * M) - 1.0);
                     if (rel < flag_band) st[ST_FLAG_TIES]++;
+                    else if (rel < wide) st[ST_TIE_COND]++;
                     else st[ST_FLAG_MISMATCH]++;
                     use = h;
                 }
@@ -411,6 +420,7 @@ int oracle_pf(int family, int dx, int dy, int D, const double* H,
                             double d2 = lo - nu[i];       /* >= 0 if c_{h-1} >= tau */
                             double dist = d1 > d2 ? d1 : d2;
                             if (dist < band) st[ST_TIE_FOLLOWED]++;
+                            else if (dist < wide) st[ST_TIE_COND]++;
                             else {
                                 st[ST_NONTIE_MISMATCH]++;
                                 if (dist > worst_dist) worst_dist = dist;
@@ -438,18 +448,21 @@ int oracle_pf(int family, int dx, int dy, int D, const double* H,
                     double* s = g; g = gn; gn = s;
                 }
                 for (int i = 0; i < M; ++i) lw[i] = lw_new;
+                lacc = 0.0;
             }
         }
 
         /* ---- propagate with the prior proposal and reweight (Eq. priorproposalweight) ---- */
         normals(key, (uint32_t)t, OR_STREAM_PROP, (long)M * dx, eps);
         for (int r = 0; r < dy; ++r) yt[r] = (double)y[(size_t)(t - 1) * dy + r];
+        double step_max_abs = 0.0;
         for (int j = 0; j < M; ++j) {
             double* xj = x + (size_t)j * dx;
             double* xnj = xn + (size_t)j * dx;
             model_transition(&m, theta, xj, eps + (size_t)j * dx, xnj, Fx, Ft);
             double Lj = model_loglik(&m, theta, xnj, yt, Lx, Lt);
             lw[j] += Lj;
+            if (fabs(Lj) > step_max_abs) step_max_abs = fabs(Lj);
             if (want_grad) {
                 double* Jj = J + (size_t)j * nJ;
                 double* Jnj = Jn + (size_t)j * nJ;
@@ -470,6 +483,7 @@ int oracle_pf(int family, int dx, int dy, int D, const double* H,
         }
         { double* s = x; x = xn; xn = s; }
         if (want_grad) { double* s = J; J = Jn; Jn = s; }
+        lacc += step_max_abs;
 
         /* ---- ESS of the new weights (Eq. ess) for the next decision ---- */
         if (t < T) {

@@ -77,7 +77,7 @@ def systematic_ancestors(logw, nu, hint=None, band=1e-6):
 
 def run(family, dx, dy, H, y, N, M, K, gamma, proposal, seed, prior_mean=None, prior_std=None,
         scheme=SYSTEMATIC, ess_frac=0.5, hints=None, band=1e-6, flag_band=1e-6,
-        outer_band=1e-4, D=None, loglik_grad_fn=None):
+        outer_band=1e-4, D=None, loglik_grad_fn=None, band_rel=0.0):
     """Run K iterations; returns (list of per-iteration records, recycled mean).
 
     proposal: "rw" (SMC0) or "langevin" (SMC1).
@@ -110,7 +110,7 @@ def run(family, dx, dy, H, y, N, M, K, gamma, proposal, seed, prior_mean=None, p
                 hf = hint["pf_flag"][i]
             r = _pf(family, dx, dy, H, theta[i], y, M, seed, k, i, scheme=scheme,
                     ess_frac=ess_frac, want_grad=True, hint_anc=ha, hint_flag=hf,
-                    band=band, flag_band=flag_band, want_tape=False)
+                    band=band, flag_band=flag_band, want_tape=False, band_rel=band_rel)
             ll[i] = r["loglik"]
             g[i] = r["grad"]
             rows.append(r["stats"])

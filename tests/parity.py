@@ -15,6 +15,11 @@ import numpy as np
 import oracle
 
 BAND = 1e-6
+# FP32 conditioning of the weights: where the log-weight increments accumulated since the
+# last resampling reach L in magnitude, FP32 log-weights carry an absolute error of order
+# 2^-24 L; the widened band max(BAND, 2^-21 L) is used for prior draws and other extreme
+# parameters (counted separately as "tie_conditioned").
+BAND_REL = 2.0 ** -21
 LL_RTOL = 1e-4
 GRAD_RTOL = 1e-3
 MEAN_RTOL = 1e-3

@@ -284,6 +284,9 @@ def test_follow_mode_classifies_planted_mismatches():
     assert s["stats"]["nontie_mismatch"] == 1 and s["worst"] > 1e-6
     assert s["loglik"] != r["loglik"]
     assert np.array_equal(s["anc"][t0], bad[t0])
+    # inside the conditioned band (band_rel * accumulated |log g|) it is counted as such
+    s = oracle.pf(0, 4, 2, w.H, th, w.y, M, 3, 1, 0, hint_anc=bad, hint_flag=r["flag"], band_rel=1.0)
+    assert s["stats"]["nontie_mismatch"] == 0 and s["stats"]["tie_conditioned"] == 1
     # the same plant inside a huge band counts as a followed tie instead
     s = oracle.pf(0, 4, 2, w.H, th, w.y, M, 3, 1, 0, hint_anc=bad, hint_flag=r["flag"], band=2.0)
     assert s["stats"]["nontie_mismatch"] == 0 and s["stats"]["tie_followed"] == 1
