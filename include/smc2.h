@@ -148,6 +148,36 @@ int smc2_get_state(smc2_handle* h, double* loglik_host, double* gradpi_host);
 int smc2_get_trace(smc2_handle* h, uint16_t* pf_anc, uint8_t* pf_flag, int32_t* outer_anc,
                    int32_t* outer_resampled);
 
+/*
+ * pf_loglik_grad_static: pf_loglik_grad for callers that cannot allocate device memory
+ * (for example code inside a framework that owns all device memory through its own
+ * pool, latency-critical loops where cudaMalloc/cudaFree would synchronise the device,
+ * or plug-ins that must not grow the device footprint after start-up).  The paper has
+ * no counterpart; this is a deployment variant of the same computation.
+ *
+ * No handle and no allocation: cfg describes the model and sizes (model_family, d_x,
+ * d_y, H (host, copied), y (DEVICE pointer, y_on_device must be 1), T, M, D,
+ * pf_resample, ess_frac, seed, ckpt_every, particles_per_thread, stream); cfg->N is
+ * ignored and n rows of theta_dev ([n][D] FP64, device) are filtered with Philox rows
+ * row0..row0+n-1 and iteration iter.  Outputs as for pf_loglik_grad (loglik_dev [n],
+ * grad_dev [n][D] or NULL), caller-owned device buffers.  Work is enqueued on
+ * cfg->stream (NULL: the legacy default stream).
+ *
+ * Working memory (checkpoints, ancestor tape, per-step scalars, a copy of H) comes from
+ * one static device array of 64 MiB that every GPU loading this library holds until the
+ * process exits.  With ckpt_every = 0 the checkpoint interval is the smallest power of
+ * two whose working set fits; a problem that does not fit even then is rejected with
+ * SMC2_E_INVAL and a message giving the bytes it needs.  The first call on each device
+ * looks up the array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  All calls share the one array and it keeps the last
+ * call's contents (nothing in it needs to start at zero): calls whose work overlaps on
+ * the GPU race with each other, so serialise them (one stream, or events).
+ * This entry point calls no cudaMalloc, cudaFree or other allocating routine.
+ * Errors: SMC2_E_INVAL, SMC2_E_CUDA.
+ */
+int pf_loglik_grad_static(const smc2_config* cfg, const double* theta_dev, int n, uint32_t iter,
+                          uint32_t row0, double* loglik_dev, double* grad_dev);
+
 /* Replace the observations (T x d_y FP32, host) of an existing handle; the copy is
  * stream-ordered on the handle's stream. */
 int smc2_set_observations(smc2_handle* h, const float* y_host);

@@ -24,7 +24,8 @@ EXPORTS = ("smc2_config_init", "smc2_create", "pf_loglik_grad", "pf_loglik_grad_
            "pf_loglik_grad_host", "smc2_step", "smc2_get_samples", "smc2_get_state",
            "smc2_get_trace", "smc2_set_observations", "smc2_footprint", "smc2_destroy",
            "smc2_autotune", "smc2_kernel_launches", "smc2_last_error", "smc2_server_create",
-           "smc2_submit", "smc2_poll", "smc2_cancel", "smc2_server_destroy")
+           "smc2_submit", "smc2_poll", "smc2_cancel", "smc2_server_destroy",
+           "pf_loglik_grad_static")
 
 
 class Config(ctypes.Structure):
@@ -116,6 +117,8 @@ def load(path: str = LIB_PATH):
         "smc2_poll": (ctypes.c_int, [vp, u64, ctypes.POINTER(Result)]),
         "smc2_cancel": (ctypes.c_int, [vp, u64]),
         "smc2_server_destroy": (ctypes.c_int, [vp]),
+        "pf_loglik_grad_static": (ctypes.c_int, [ctypes.POINTER(Config), dp, ctypes.c_int, u32, u32,
+                                                 dp, dp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
