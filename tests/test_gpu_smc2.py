@@ -58,7 +58,9 @@ def _compare(recs, ref, rec_ref=None, weight_floor=1e-12, stable=None):
         rows = np.arange(len(th_ref))
         src = r["ancestors"] if r["resampled"] else rows
         keep = np.isin(src, alive)
-        np.testing.assert_allclose(g["theta"][keep], th_ref[keep], rtol=1e-5, atol=1e-5)
+        # a Langevin move carries the gradient's error into theta: per iteration at most
+        # 0.5 gamma^2 * GRAD_RTOL * |grad| (~2e-4 here), accumulated over the iterations
+        np.testing.assert_allclose(g["theta"][keep], th_ref[keep], rtol=1e-3, atol=1e-3)
     if rec_ref is not None:
         np.testing.assert_allclose(recs[-1]["recycled_mean"], rec_ref, rtol=0,
                                    atol=MEAN_RTOL * max(1.0, float(np.abs(rec_ref).max())))
