@@ -22,9 +22,14 @@
 #include "runtime.h"
 
 namespace smc2 {
-pf_launch_fn lookup_pf_lg1(int P);
-pf_launch_fn lookup_pf_lg4(int P);
-pf_launch_fn lookup_pf_sv(int P);
+pf_kernel_fn lookup_lg1_fwd(int P, int regs);
+pf_kernel_fn lookup_lg1_bwd(int P, int regs);
+pf_kernel_fn lookup_lg4_fwd(int P, int regs);
+pf_kernel_fn lookup_lg4_bwd(int P, int regs);
+pf_kernel_fn lookup_sv_fwd(int P, int regs);
+pf_kernel_fn lookup_sv_bwd(int P, int regs);
+pf_kernel_fn lookup_lg16_fwd(int P, int regs);
+pf_kernel_fn lookup_lg16_bwd(int P, int regs);
 }  // namespace smc2
 
 using namespace smc2;
@@ -74,24 +79,70 @@ int smc2::family_dims(const smc2_config* c, int* D) {
         return SMC2_OK;
     }
     if (c->model_family != SMC2_LG_DIAG) return fail(SMC2_E_INVAL, "unknown model_family");
-    const bool ok = (c->d_x == 1 && c->d_y == 1) || (c->d_x == 4 && c->d_y == 2);
-    if (!ok) return fail(SMC2_E_INVAL, "LG_DIAG supports (d_x, d_y) = (1,1) or (4,2)");
+    const bool ok = (c->d_x == 1 && c->d_y == 1) || (c->d_x == 4 && c->d_y == 2) || (c->d_x == 16 && c->d_y == 16);
+    if (!ok) return fail(SMC2_E_INVAL, "LG_DIAG supports (d_x, d_y) = (1,1), (4,2) or (16,16)");
+    if (c->d_x == 16 && c->H) {
+        for (int r = 0; r < 16; ++r)
+            for (int k = 0; k < 16; ++k)
+                if (c->H[r * 16 + k] != (r == k ? 1.f : 0.f))
+                    return fail(SMC2_E_INVAL, "the 16-dimensional model needs H = identity");
+    }
     *D = 2 * c->d_x + c->d_y;
     return SMC2_OK;
 }
 
-pf_launch_fn smc2::select_kernel(const smc2_config* c, int P) {
-    if (c->model_family == SMC2_SV) return lookup_pf_sv(P);
-    if (c->d_x == 1) return lookup_pf_lg1(P);
-    if (c->d_x == 4) return lookup_pf_lg4(P);
+pf_kernel_fn smc2::lookup_forward(const smc2_config* c, int P, int regs) {
+    if (!variant_fits(c, P, regs)) return nullptr;
+    if (c->model_family == SMC2_SV) return lookup_sv_fwd(P, regs);
+    if (c->d_x == 1) return lookup_lg1_fwd(P, regs);
+    if (c->d_x == 4) return lookup_lg4_fwd(P, regs);
+    if (c->d_x == 16) return lookup_lg16_fwd(P, regs);
     return nullptr;
 }
 
-int smc2::choose_ppt(const smc2_config* c) {
-    if (c->particles_per_thread) return c->particles_per_thread;
-    int P = 4;
-    while (pf_threads(c->M, P) > 512 && P < 8) P *= 2;
-    return P;
+pf_kernel_fn smc2::lookup_backward(const smc2_config* c, int P, int regs) {
+    if (!variant_fits(c, P, regs)) return nullptr;
+    if (c->model_family == SMC2_SV) return lookup_sv_bwd(P, regs);
+    if (c->d_x == 1) return lookup_lg1_bwd(P, regs);
+    if (c->d_x == 4) return lookup_lg4_bwd(P, regs);
+    if (c->d_x == 16) return lookup_lg16_bwd(P, regs);
+    return nullptr;
+}
+
+int smc2::model_lanes(const smc2_config* c) { return (c->model_family == SMC2_LG_DIAG && c->d_x == 16) ? 4 : 1; }
+
+bool smc2::variant_fits(const smc2_config* c, int P, int regs) {
+    const int threads = pf_threads(c->M, P, model_lanes(c));
+    return threads <= 1024 && threads * regs <= 65536;
+}
+
+// Register cap used with an explicitly requested particles-per-thread value: the largest
+// of 128, 80, 64 that the block size allows.
+static int default_regs(const smc2_config* c, int P) {
+    for (int r : {128, 80, 64})
+        if (variant_fits(c, P, r)) return r;
+    return 64;
+}
+
+void smc2::choose_launch(const smc2_config* c, LaunchChoice* lc) {
+    LaunchChoice t;
+    const bool tuned = tuned_launch(c, &t);
+    if (c->particles_per_thread) {
+        lc->pf = lc->pb = c->particles_per_thread;
+        lc->rf = lc->rb = default_regs(c, c->particles_per_thread);
+    } else if (tuned) {
+        *lc = t;
+    } else {
+        // enough particles per thread to keep every Philox call whole and the block <= 512
+        // threads (1024 for the lane-split model), 64 registers when that still fits
+        const int G = model_lanes(c);
+        const int cap = (G > 1) ? 1024 : 512;
+        int P = (c->d_x >= 4) ? 2 : 4;
+        while (pf_threads(c->M, P, G) > cap && P < 8) P *= 2;
+        lc->pf = lc->pb = P;
+        lc->rf = lc->rb = variant_fits(c, P, 64) && P <= 4 ? 64 : default_regs(c, P);
+    }
+    lc->kc = (c->ckpt_every > 0) ? c->ckpt_every : (tuned ? t.kc : choose_kc(c));
 }
 
 int smc2::choose_kc(const smc2_config* c) {
@@ -122,7 +173,13 @@ int smc2::validate(const smc2_config* c, int* D) {
     if (c->ckpt_every < 0) return fail(SMC2_E_INVAL, "ckpt_every must be >= 0");
     const int P = c->particles_per_thread;
     if (P != 0 && P != 1 && P != 2 && P != 4 && P != 8) return fail(SMC2_E_INVAL, "particles_per_thread must be 0, 1, 2, 4 or 8");
-    if (pf_threads(c->M, choose_ppt(c)) > 512) return fail(SMC2_E_INVAL, "M too large for particles_per_thread");
+    if (P != 0 && !variant_fits(c, P, 64)) return fail(SMC2_E_INVAL, "M too large for particles_per_thread");
+    {
+        LaunchChoice lc;
+        choose_launch(c, &lc);
+        if (!variant_fits(c, lc.pf, lc.rf) || !variant_fits(c, lc.pb, lc.rb))
+            return fail(SMC2_E_INVAL, "M too large for this model (no launch configuration fits)");
+    }
     if (c->prior_std)
         for (int d = 0; d < *D; ++d)
             if (!(c->prior_std[d] > 0.0)) return fail(SMC2_E_INVAL, "prior_std must be positive");
@@ -149,7 +206,9 @@ extern "C" int smc2_footprint(const smc2_config* cfg, size_t* bytes) {
     int rc = validate(cfg, &D);
     if (rc) return rc;
     Sizes s;
-    plan_sizes(cfg, D, choose_kc(cfg), &s);
+    LaunchChoice lc;
+    choose_launch(cfg, &lc);
+    plan_sizes(cfg, D, lc.kc, &s);
     if (bytes) *bytes = s.total;
     return SMC2_OK;
 }
@@ -180,11 +239,11 @@ extern "C" int smc2_create(const smc2_config* cfg, smc2_handle** out) {
     h->cfg.prior_mean = nullptr;
     h->cfg.prior_std = nullptr;
     h->D = D;
-    h->P = choose_ppt(cfg);
-    h->threads = pf_threads(cfg->M, h->P);
-    h->kc = choose_kc(cfg);
-    h->pf = select_kernel(cfg, h->P);
-    if (!h->pf) {
+    choose_launch(cfg, &h->lc);
+    h->kc = h->lc.kc;
+    h->fwd = lookup_forward(cfg, h->lc.pf, h->lc.rf);
+    h->bwd = lookup_backward(cfg, h->lc.pb, h->lc.rb);
+    if (!h->fwd || !h->bwd) {
         delete h;
         return fail(SMC2_E_INVAL, "no kernel for this model shape");
     }
@@ -314,8 +373,8 @@ PFArgs smc2::make_pf_args(smc2_handle* h, const double* theta, int n, uint32_t i
 }
 
 int smc2::launch_filters(smc2_handle* h, const PFArgs& a) {
-    const SmemLayout lf(a.M, h->cfg.d_x, h->D, true), lb(a.M, h->cfg.d_x, h->D, false);
-    const int rc = h->pf(a, h->threads, lf.total, lb.total, h->stream, a.n, a.n);
+    int rc = h->fwd(a, h->stream, a.n);
+    if (!rc && a.want_grad) rc = h->bwd(a, h->stream, a.n);
     if (rc) return fail(SMC2_E_CUDA, std::string("filter launch failed: ") + cudaGetErrorString(cudaGetLastError()));
     count_launches(a.want_grad ? 2 : 1);
     return SMC2_OK;

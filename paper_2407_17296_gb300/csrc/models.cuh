@@ -1,6 +1,7 @@
 // models.cuh -- state-space model families for the CRN particle filter.
 //
-// Each family supplies, in FP32 on the device:
+// Each family supplies, in FP32 on the device (for the state dimensions a lane holds:
+// all of them when G = 1, d_x / G of them when a particle is split over G lanes):
 //   init        x_0 from its noise (the reparameterised initial law)
 //   transition  x_t = f(x_{t-1}, theta, eps_t)  (Eq. reparam_epsilon: mean + sqrt(C) eps)
 //   loglik      log g(y_t | x_t, theta)          (Eq. L)
@@ -9,7 +10,10 @@
 //   bwd_obs     xbar += lwbar dlog g/dx,  thb += lwbar dlog g/dtheta
 //   bwd_trans   thb += xbar df/dtheta,    xbar <- (df/dx)^T xbar
 //   bwd_init    thb += xbar0 dx_0/dtheta
-// Parameters are derived once per filter from theta in FP64 and rounded to FP32.
+// Parameters are derived once per filter from theta in FP64 and rounded to FP32
+// (make_params), then each lane takes the slice it needs (lane_params).  Gradient
+// partials live in DTH registers per lane; theta_index(l, gl) names the parameter that
+// partial l of lane gl belongs to.
 #pragma once
 #include <cmath>
 
@@ -22,6 +26,7 @@ constexpr float kLog2Pi = 1.8378770664093454836f;
 template <int DX_, int DY_, bool HIDENT_>
 struct LGDiag {
     static constexpr int DX = DX_, DY = DY_, D = 2 * DX_ + DY_;
+    static constexpr int G = 1, DL = DX_, DTH = D;
     static constexpr bool HIDENT = HIDENT_;
     static constexpr int kFamily = 0;
     struct Params {
@@ -29,6 +34,9 @@ struct LGDiag {
         float H[HIDENT ? 1 : DY][DX];
         float cst;  // -sum log r - DY/2 log 2 pi
     };
+    using LaneParams = Params;
+    __device__ __forceinline__ static void lane_params(const Params& p, int, LaneParams& lp) { lp = p; }
+    __device__ __forceinline__ static int theta_index(int l, int) { return l; }
 
     __device__ static void make_params(const double* th, const float* Hg, Params& p) {
         double c = 0.0;
@@ -122,11 +130,15 @@ struct LGDiag {
 // x_0 from the stationary law; theta = (mu, atanh phi, log sigma).
 struct SV {
     static constexpr int DX = 1, DY = 1, D = 3;
+    static constexpr int G = 1, DL = 1, DTH = 3;
     static constexpr bool HIDENT = true;
     static constexpr int kFamily = 1;
     struct Params {
         float mu, phi, sig, sd0, omp2;  // omp2 = 1 - phi^2
     };
+    using LaneParams = Params;
+    __device__ __forceinline__ static void lane_params(const Params& p, int, LaneParams& lp) { lp = p; }
+    __device__ __forceinline__ static int theta_index(int l, int) { return l; }
 
     __device__ static void make_params(const double* th, const float*, Params& p) {
         const double phi = tanh(th[1]);
@@ -176,6 +188,101 @@ struct SV {
         thb[1] += xbar[0] * p.phi * dev;
         thb[2] += xbar[0] * dev;
     }
+};
+
+// Linear-Gaussian model with diagonal transition and H = I whose d_x dimensions are split
+// over G lanes (DL = d_x / G each): the dimensions evolve and are observed independently,
+// so a lane propagates, weights and differentiates its own slice; the particle's
+// log g is the sum of the lanes' partial sums plus cst (added after the group sum).
+// theta = (a[DX], log q[DX], log r[DX]); a lane's partials are (a, log q, log r) of its slice.
+template <int DX_, int G_>
+struct LGSplit {
+    static constexpr int DX = DX_, DY = DX_, D = 3 * DX_;
+    static constexpr int G = G_, DL = DX_ / G_, DTH = 3 * (DX_ / G_);
+    static constexpr bool HIDENT = true;
+    static constexpr int kFamily = 0;
+    static_assert(DX_ % G_ == 0, "dimensions must split evenly over the lanes");
+    struct Params {
+        float a[DX], q[DX], rinv[DX];
+        float cst;  // -sum log r - DX/2 log 2 pi
+    };
+    struct LaneParams {
+        float a[DL], q[DL], rinv[DL];
+        float cst;
+    };
+
+    __device__ static void make_params(const double* th, const float*, Params& p) {
+        double c = 0.0;
+        for (int k = 0; k < DX; ++k) {
+            p.a[k] = (float)th[k];
+            p.q[k] = (float)exp(th[DX + k]);
+            p.rinv[k] = (float)exp(-th[2 * DX + k]);
+            c -= th[2 * DX + k];
+        }
+        p.cst = (float)(c - 0.5 * DX * 1.8378770664093454836);
+    }
+
+    __device__ __forceinline__ static void lane_params(const Params& p, int gl, LaneParams& lp) {
+#pragma unroll
+        for (int k = 0; k < DL; ++k) {
+            lp.a[k] = p.a[gl * DL + k];
+            lp.q[k] = p.q[gl * DL + k];
+            lp.rinv[k] = p.rinv[gl * DL + k];
+        }
+        lp.cst = p.cst;
+    }
+
+    __device__ __forceinline__ static int theta_index(int l, int gl) {
+        const int blk = l / DL, k = l - blk * DL;  // blk 0: a, 1: log q, 2: log r
+        return blk * DX + gl * DL + k;
+    }
+
+    __device__ __forceinline__ static void init(const LaneParams&, const float (&eps)[DL], float (&x)[DL]) {
+#pragma unroll
+        for (int k = 0; k < DL; ++k) x[k] = eps[k];
+    }
+
+    __device__ __forceinline__ static void transition(const LaneParams& p, float (&x)[DL], const float (&eps)[DL]) {
+#pragma unroll
+        for (int k = 0; k < DL; ++k) x[k] = p.a[k] * x[k] + p.q[k] * eps[k];
+    }
+
+    // -1/2 sum over the lane's dimensions of ((y - x)/r)^2; yt points at the lane's slice
+    __device__ __forceinline__ static float loglik(const LaneParams& p, const float (&x)[DL],
+                                                   const float* __restrict__ yt) {
+        float s = 0.f;
+#pragma unroll
+        for (int k = 0; k < DL; ++k) {
+            const float z = (__ldg(yt + k) - x[k]) * p.rinv[k];
+            s += z * z;
+        }
+        return -0.5f * s;
+    }
+
+    __device__ __forceinline__ static void bwd_obs(const LaneParams& p, const float (&x)[DL],
+                                                   const float* __restrict__ yt, float lwbar,
+                                                   float (&xbar)[DL], float (&thb)[DTH]) {
+#pragma unroll
+        for (int k = 0; k < DL; ++k) {
+            const float z = (__ldg(yt + k) - x[k]) * p.rinv[k];
+            thb[2 * DL + k] += lwbar * (z * z - 1.f);
+            xbar[k] += lwbar * z * p.rinv[k];
+        }
+    }
+
+    __device__ __forceinline__ static void bwd_trans(const LaneParams& p, const float (&xt)[DL],
+                                                     const float (&xp)[DL], float (&xbar)[DL],
+                                                     float (&thb)[DTH]) {
+#pragma unroll
+        for (int k = 0; k < DL; ++k) {
+            thb[k] += xbar[k] * xp[k];
+            thb[DL + k] += xbar[k] * (xt[k] - p.a[k] * xp[k]);
+            xbar[k] *= p.a[k];
+        }
+    }
+
+    __device__ __forceinline__ static void bwd_init(const LaneParams&, const float (&)[DL], const float (&)[DL],
+                                                    float (&)[DTH]) {}
 };
 
 }  // namespace smc2

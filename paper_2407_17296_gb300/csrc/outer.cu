@@ -95,11 +95,12 @@ __device__ double block_max_d(double v, double* red) {
     return s;
 }
 
-__device__ double log_prior(const double* th, const double* m, const double* s, int D) {
-    double acc = 0.0;
+// log N(theta; m, diag(s^2)) with inv_s = 1/s and cst = -sum log s - D/2 log 2 pi precomputed
+__device__ double log_prior(const double* th, const double* m, const double* inv_s, double cst, int D) {
+    double acc = cst;
     for (int d = 0; d < D; ++d) {
-        const double z = (th[d] - m[d]) / s[d];
-        acc += -0.5 * z * z - log(s[d]) - 0.9189385332046727418;
+        const double z = (th[d] - m[d]) * inv_s[d];
+        acc -= 0.5 * z * z;
     }
     return acc;
 }
@@ -107,17 +108,27 @@ __device__ double log_prior(const double* th, const double* m, const double* s, 
 __global__ void __launch_bounds__(kOuterThreads) outer_update_kernel(OuterArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     double* red = reinterpret_cast<double*>(smem);               // 32
-    double* csum = red + 32;                                      // N
+    double* pinv = red + 32;                                      // 64: 1/prior_std, then cst
+    double* csum = pinv + 65;                                     // N
     int* anc = reinterpret_cast<int*>(csum + a.N);                // N
     const int N = a.N, D = a.D, tid = threadIdx.x, nt = blockDim.x;
     const uint32_t k = *a.k_dev + 1u;
     const double g2 = a.gamma * a.gamma;
+    if (tid == 0) {
+        double c = 0.0;
+        for (int d = 0; d < D; ++d) {
+            pinv[d] = 1.0 / a.prior_std[d];
+            c -= log(a.prior_std[d]) + 0.9189385332046727418;
+        }
+        pinv[64] = c;
+    }
+    __syncthreads();
 
     // 1. pseudo-marginal update of every sample with its particle-filter result
     for (int i = tid; i < N; i += nt) {
         const double* thn = a.theta_new + (size_t)i * D;
         const double lln = a.ll_new[i];
-        const double lpn = (lln > -INFINITY) ? log_prior(thn, a.prior_mean, a.prior_std, D) + lln : -INFINITY;
+        const double lpn = (lln > -INFINITY) ? log_prior(thn, a.prior_mean, pinv, pinv[64], D) + lln : -INFINITY;
         double lw;
         if (k == 1u) {
             lw = lln;  // pi / q_1 with q_1 the prior
@@ -132,7 +143,7 @@ __global__ void __launch_bounds__(kOuterThreads) outer_update_kernel(OuterArgs a
                     const double* gn = a.grad_new + (size_t)i * D;
                     double qf = 0.0, lf = 0.0;
                     for (int d = 0; d < D; ++d) {
-                        const double gpn = -(thn[d] - a.prior_mean[d]) / (a.prior_std[d] * a.prior_std[d]) + gn[d];
+                        const double gpn = -(thn[d] - a.prior_mean[d]) * pinv[d] * pinv[d] + gn[d];
                         const double fwd = thn[d] - th[d] - 0.5 * g2 * gp[d];
                         const double bwd = th[d] - thn[d] - 0.5 * g2 * gpn;
                         qf += fwd * fwd;
@@ -151,8 +162,7 @@ __global__ void __launch_bounds__(kOuterThreads) outer_update_kernel(OuterArgs a
         for (int d = 0; d < D; ++d) {
             const double th = thn[d];
             a.theta[(size_t)i * D + d] = th;
-            a.gradpi[(size_t)i * D + d] =
-                -(th - a.prior_mean[d]) / (a.prior_std[d] * a.prior_std[d]) + a.grad_new[(size_t)i * D + d];
+            a.gradpi[(size_t)i * D + d] = -(th - a.prior_mean[d]) * pinv[d] * pinv[d] + a.grad_new[(size_t)i * D + d];
         }
     }
     __syncthreads();
@@ -285,7 +295,7 @@ __global__ void __launch_bounds__(kOuterThreads) outer_update_kernel(OuterArgs a
 
 size_t outer_update_smem(int N, int D) {
     (void)D;
-    return sizeof(double) * (32 + (size_t)N) + sizeof(int) * (size_t)N;
+    return sizeof(double) * (32 + 65 + (size_t)N) + sizeof(int) * (size_t)N;
 }
 
 int launch_outer_propose(const OuterArgs& a, void* stream) {

@@ -42,7 +42,7 @@ struct PFArgs {
 // Dynamic shared-memory plan (mirrored on the host to size the launch).
 struct SmemLayout {
     size_t xstage, xbstage, cs, marks, starts, red, scanw, scanwi, dred, total;
-    SMC2_HD SmemLayout(int M, int DX, int D, bool fwd) {
+    SMC2_HD SmemLayout(int M, int DX, int D, bool fwd, int G = 1) {
         size_t o = 0;
         auto take = [&](size_t bytes) {
             const size_t r = o;
@@ -53,7 +53,7 @@ struct SmemLayout {
         xbstage = fwd ? o : take(sizeof(float) * (size_t)M * DX);
         cs = fwd ? take(sizeof(float) * (size_t)M) : o;
         marks = take(sizeof(uint16_t) * (size_t)M);      // fwd: range marks; bwd: tape row
-        starts = fwd ? o : take(sizeof(uint16_t) * (size_t)M);
+        starts = fwd ? o : take(sizeof(float) * 32 * G * (DX / G + 1));  // segmented-scan scratch
         red = take(sizeof(float4) * 2 * 32);
         scanw = take(sizeof(unsigned long long) * 32);
         scanwi = take(sizeof(int) * 32);
@@ -62,13 +62,18 @@ struct SmemLayout {
     }
 };
 
-SMC2_HD inline int pf_threads(int M, int P) {
-    const int chunks = (M + P - 1) / P;
-    return ((chunks + 31) / 32) * 32;
+// threads of a block: G lanes per chunk of P particles, rounded up to whole warps
+SMC2_HD inline int pf_threads(int M, int P, int G = 1) {
+    const int lanes = ((M + P - 1) / P) * G;
+    return ((lanes + 31) / 32) * 32;
 }
 
-// Host-side launchers, one per (model, particles-per-thread) instantiation.
-typedef int (*pf_launch_fn)(const PFArgs& a, int threads, size_t smem_fwd, size_t smem_bwd,
-                            void* stream, int grid_fwd, int grid_bwd);
+// Host-side launcher of one compiled kernel variant (forward or adjoint pass).
+typedef int (*pf_kernel_fn)(const PFArgs& a, void* stream, int grid);
+
+// A launch choice: particles per thread and register cap of each pass, checkpoint interval.
+struct LaunchChoice {
+    int pf = 4, rf = 128, pb = 4, rb = 128, kc = 1;
+};
 
 }  // namespace smc2

@@ -1,9 +1,12 @@
 // pf_kernels.cuh -- the CRN particle filter (forward) and its reverse-time adjoint.
 //
 // One CTA runs one filter (one theta-sample) at a time, in a grid-stride loop
-// over the filters of the launch.  Thread `tid` owns the P consecutive
-// particles j = tid*P .. tid*P+P-1; their states live in registers for the
-// whole pass.  Cross-particle work per step goes through warp shuffles and a
+// over the filters of the launch.  A group of G adjacent lanes owns P consecutive
+// particles j = chunk*P .. chunk*P+P-1 (chunk = tid / G); lane gl = tid % G of the
+// group holds state dimensions gl*DL .. gl*DL+DL-1 (DL = d_x / G) of those particles
+// in registers for the whole pass, and per-particle scalars (log-weights, their
+// cotangents) are replicated across the group.  G = 1 for small d_x; the
+// 16-dimensional model spreads each particle over G = 4 lanes.  Cross-particle work per step goes through warp shuffles and a
 // little shared memory:
 //   * log-sum-exp and ESS: one block reduction of (max, sum e, sum e^2);
 //   * resampling: an exact 64-bit fixed-point prefix sum of the weights
@@ -42,25 +45,46 @@
 
 namespace smc2 {
 
-constexpr int kMaxThreads = 512;
+constexpr int kMaxThreads = 1024;
 constexpr unsigned kFull = 0xffffffffu;
-constexpr float kFixScale = 1099511627776.0f;  // 2^40: fixed-point scale of the resampling weights
 
 // ---------------------------------------------------------------- block primitives
 
+// floor(w * 2^40) for w in [0, 1], from the float's bits with integer operations only
+// (conversions between floats and 64-bit integers run on the narrow FP64 pipe).
+__device__ __forceinline__ unsigned long long fixed40(float w) {
+    const uint32_t b = __float_as_uint(w);
+    const int e = (int)((b >> 23) & 0xffu);
+    if (e == 0) return 0ull;                          // zero (or a denormal weight)
+    const uint32_t m = (b & 0x7fffffu) | 0x800000u;   // w = m * 2^(e - 150)
+    const int sh = e - 110;                           // w * 2^40 = m * 2^sh, sh <= 17
+    if (sh >= 0) return (unsigned long long)m << sh;
+    if (sh <= -24) return 0ull;
+    return (unsigned long long)(m >> (-sh));
+}
+
+// S as a float, rounded toward zero (monotone in S), with integer operations only.
+__device__ __forceinline__ float u64_to_float_rz(unsigned long long S) {
+    if (S == 0ull) return 0.f;
+    const int lz = __clzll((long long)S);
+    const uint32_t m = (uint32_t)((S << lz) >> 40);  // leading 24 bits, top bit set
+    const uint32_t E = (uint32_t)(63 - lz);          // S ~ m * 2^(E - 23)
+    return __uint_as_float(((E + 127u) << 23) | (m & 0x7fffffu));
+}
+
 // (max, sum exp(v - max), sum exp(2 (v - max))) over all particles of the CTA.
 // Every thread returns bit-identical values (same combination order everywhere).
+// A NaN log-weight anywhere turns s1 into NaN (the caller treats the filter as broken).
 template <int P>
-__device__ __forceinline__ void block_lse3(const float (&lw)[P], float4* red, float& m, float& s1,
+__device__ __forceinline__ void block_lse3(const float (&lwin)[P], bool lead, float4* red, float& m, float& s1,
                                            float& s2) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    float ml = lw[0];
-    bool bad = isnan(lw[0]);
+    float lw[P];  // only one lane of each group counts its (replicated) particles
 #pragma unroll
-    for (int p = 1; p < P; ++p) {
-        ml = fmaxf(ml, lw[p]);
-        bad |= isnan(lw[p]);
-    }
+    for (int p = 0; p < P; ++p) lw[p] = lead ? lwin[p] : -INFINITY;
+    float ml = lw[0];
+#pragma unroll
+    for (int p = 1; p < P; ++p) ml = fmaxf(ml, lw[p]);
     float mw = ml;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mw = fmaxf(mw, __shfl_xor_sync(kFull, mw, o));
@@ -68,7 +92,7 @@ __device__ __forceinline__ void block_lse3(const float (&lw)[P], float4* red, fl
     if (mw > -INFINITY) {
 #pragma unroll
         for (int p = 0; p < P; ++p) {
-            const float e = expf(lw[p] - mw);
+            const float e = __expf(lw[p] - mw);  // NaN in, NaN out
             a1 += e;
             a2 += e * e;
         }
@@ -78,29 +102,32 @@ __device__ __forceinline__ void block_lse3(const float (&lw)[P], float4* red, fl
         a1 += __shfl_xor_sync(kFull, a1, o);
         a2 += __shfl_xor_sync(kFull, a2, o);
     }
-    if (__any_sync(kFull, bad)) a1 = __int_as_float(0x7fc00000);  // NaN marks a broken filter
     if (lane == 0) red[wid] = make_float4(mw, a1, a2, 0.f);
     __syncthreads();
-    float M_ = -INFINITY;
-    for (int w = 0; w < nw; ++w) M_ = fmaxf(M_, red[w].x);
-    float S1 = 0.f, S2 = 0.f;
-    for (int w = 0; w < nw; ++w) {
-        const float4 r = red[w];
-        const float e = (r.x > -INFINITY) ? expf(r.x - M_) : 0.f;
-        S1 += r.y * e;
-        S2 += r.z * e * e;
-        if (isnan(r.y)) S1 = r.y;
+    // every warp combines the per-warp partials with the same butterfly, so all threads
+    // end with bit-identical results (the combining operations are commutative)
+    const float4 r = (lane < nw) ? red[lane] : make_float4(-INFINITY, 0.f, 0.f, 0.f);
+    float M_ = r.x;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) M_ = fmaxf(M_, __shfl_xor_sync(kFull, M_, o));
+    const bool bad = __any_sync(kFull, isnan(r.x) || isnan(r.y));  // a warp of NaNs has a NaN maximum
+    const float e = (r.x > -INFINITY) ? __expf(r.x - M_) : 0.f;
+    float S1 = r.y * e, S2 = r.z * e * e;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        S1 += __shfl_xor_sync(kFull, S1, o);
+        S2 += __shfl_xor_sync(kFull, S2, o);
     }
     m = M_;
-    s1 = S1;
+    s1 = bad ? __int_as_float(0x7fc00000) : S1;
     s2 = S2;
 }
 
 // Exact inclusive prefix sums S_j of the fixed-point weights round(w_j * 2^40) over the
 // CTA's particles.  Returns the thread's base (sum before its first particle), its local
 // inclusive sums s[p], and the grand total.  One __syncthreads.
-template <int P>
-__device__ __forceinline__ void block_fixed_scan(const float (&lw)[P], int j0, int M,
+template <int P, int G>
+__device__ __forceinline__ void block_fixed_scan(const float (&lw)[P], bool lead, int j0, int M,
                                                  unsigned long long* scanw,
                                                  unsigned long long (&s)[P],
                                                  unsigned long long& base,
@@ -109,8 +136,8 @@ __device__ __forceinline__ void block_fixed_scan(const float (&lw)[P], int j0, i
     unsigned long long run = 0ull;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-        const float w = (j0 + p < M) ? expf(lw[p]) : 0.f;  // lw <= 0 after recentring
-        run += __float2ull_rz(w * kFixScale);
+        const float w = (lead && j0 + p < M) ? __expf(lw[p]) : 0.f;  // lw <= 0 after recentring
+        run += fixed40(w);
         s[p] = run;
     }
     unsigned long long inc = run;
@@ -121,33 +148,35 @@ __device__ __forceinline__ void block_fixed_scan(const float (&lw)[P], int j0, i
     }
     if (lane == 31) scanw[wid] = inc;
     __syncthreads();
-    unsigned long long pre = 0ull, tot = 0ull;
-    for (int w = 0; w < nw; ++w) {
-        const unsigned long long v = scanw[w];
-        if (w < wid) pre += v;
-        tot += v;
+    unsigned long long v = (lane < nw) ? scanw[lane] : 0ull;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long u = __shfl_up_sync(kFull, v, o);
+        if (lane >= o) v += u;
     }
-    base = pre + (inc - run);
-    total = tot;
+    const unsigned long long pre = __shfl_sync(kFull, v, (wid + 31) & 31);
+    total = __shfl_sync(kFull, v, nw - 1);
+    base = (wid > 0 ? pre : 0ull) + (inc - run);
+    if constexpr (G > 1) base = __shfl_sync(kFull, base, lane & ~(G - 1));  // the group leader's base
 }
 
 // Systematic ancestors (App. B with tau_i = (i + nu)/M): a_i = min{j : c_j >= tau_i}.
 // Particle j is the ancestor of i in [n(c_{j-1}), n(c_j)) with n(c) = #{i : tau_i <= c}
 // = clamp(floor(c M - nu) + 1, 0, M); range starts are marked and a prefix-max fills
 // in every i.  Three __syncthreads.  anc[p] is the ancestor of particle i = j0 + p.
-template <int P>
-__device__ __forceinline__ void systematic_ancestors(const float (&lw)[P], int j0, int M, float nu,
+template <int P, int G>
+__device__ __forceinline__ void systematic_ancestors(const float (&lw)[P], bool lead, int j0, int M, float nu,
                                                      uint16_t* marks, unsigned long long* scanw,
                                                      int* scanwi, int (&anc)[P]) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int p = 0; p < P; ++p)
-        if (j0 + p < M) marks[j0 + p] = 0;
+        if (lead && j0 + p < M) marks[j0 + p] = 0;
     unsigned long long s[P], base, tot;
-    block_fixed_scan<P>(lw, j0, M, scanw, s, base, tot);
-    const float scale = (float)M / (float)tot;
+    block_fixed_scan<P, G>(lw, lead, j0, M, scanw, s, base, tot);
+    const float scale = (float)M / u64_to_float_rz(tot);
     auto count_le = [&](unsigned long long S) {
-        const float cm = (float)S * scale - nu;
+        const float cm = u64_to_float_rz(S) * scale - nu;
         const int n = (int)floorf(cm) + 1;
         return min(max(n, 0), M);
     };
@@ -156,7 +185,7 @@ __device__ __forceinline__ void systematic_ancestors(const float (&lw)[P], int j
     for (int p = 0; p < P; ++p) {
         const int j = j0 + p;
         const int hi = (j == M - 1) ? M : count_le(base + s[p]);
-        if (j < M && hi > lo) marks[lo] = (uint16_t)(j + 1);
+        if (lead && j < M && hi > lo) marks[lo] = (uint16_t)(j + 1);
         lo = hi;
     }
     __syncthreads();
@@ -173,12 +202,19 @@ __device__ __forceinline__ void systematic_ancestors(const float (&lw)[P], int j
         const int v = __shfl_up_sync(kFull, inc, o);
         if (lane >= o) inc = max(inc, v);
     }
-    int excl = __shfl_up_sync(kFull, inc, 1);
-    if (lane == 0) excl = 0;
+    // exclusive prefix of the group: the inclusive value of the lane before the group leader
+    const int lead_lane = lane & ~(G - 1);
+    int excl = __shfl_sync(kFull, inc, (lead_lane + 31) & 31);
+    if (lead_lane == 0) excl = 0;
     if (lane == 31) scanwi[wid] = inc;
     __syncthreads();
-    int pre = 0;
-    for (int w = 0; w < wid; ++w) pre = max(pre, scanwi[w]);
+    int v = (lane < (int)(blockDim.x >> 5)) ? scanwi[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(kFull, v, o);
+        if (lane >= o) v = max(v, u);
+    }
+    const int pre = (wid > 0) ? __shfl_sync(kFull, v, (wid + 31) & 31) : 0;
     const int e = max(pre, excl);
 #pragma unroll
     for (int p = 0; p < P; ++p) anc[p] = max(e, rr[p]) - 1;
@@ -186,17 +222,17 @@ __device__ __forceinline__ void systematic_ancestors(const float (&lw)[P], int j
 
 // Multinomial ancestors (the paper's scheme, App. B): one uniform nu_i per particle,
 // a_i = min{j : c_j >= nu_i} by binary search over the cumulative weights.  Two __syncthreads.
-template <int P>
-__device__ __forceinline__ void multinomial_ancestors(const float (&lw)[P], int j0, int M,
+template <int P, int G>
+__device__ __forceinline__ void multinomial_ancestors(const float (&lw)[P], bool lead, int j0, int M,
                                                       PhiloxKey key, uint32_t t, float* cs,
                                                       unsigned long long* scanw, int (&anc)[P]) {
     unsigned long long s[P], base, tot;
-    block_fixed_scan<P>(lw, j0, M, scanw, s, base, tot);
-    const float inv = 1.0f / (float)tot;
+    block_fixed_scan<P, G>(lw, lead, j0, M, scanw, s, base, tot);
+    const float inv = 1.0f / u64_to_float_rz(tot);
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         const int j = j0 + p;
-        if (j < M) cs[j] = (j == M - 1) ? 1.0f : (float)(base + s[p]) * inv;
+        if (lead && j < M) cs[j] = (j == M - 1) ? 1.0f : u64_to_float_rz(base + s[p]) * inv;
     }
     __syncthreads();
 #pragma unroll
@@ -216,78 +252,232 @@ __device__ __forceinline__ void multinomial_ancestors(const float (&lw)[P], int 
     }
 }
 
+// Adjoint of the gather x'_i = x_{a_i} for sorted ancestors (systematic resampling):
+// xbar_new[j] = sum of xbar'[i] over the offspring i of j (a run of equal a_i), zero for
+// parents without offspring.  A segmented prefix sum (thread, warp shuffles, warps) keeps
+// the work balanced whatever the offspring counts, e.g. when one particle owns them all.
+// Each lane handles its own state dimensions; ancs holds the tape row in shared memory
+// (visible to all threads before the call); xbstage receives the per-parent sums; segw is
+// 32 x G x (DL + 1) floats of scratch.  Two __syncthreads.
+template <int P, int DX, int DL, int G>
+__device__ __forceinline__ void gather_adjoint_sorted(float (&xbar)[P][DL], const int (&ai)[P], int j0, int gl,
+                                                      int M, const uint16_t* ancs, float* xbstage,
+                                                      float* segw) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+        if (j0 + p < M)
+#pragma unroll
+            for (int k = 0; k < DL; ++k) xbstage[(j0 + p) * DX + gl * DL + k] = 0.f;
+    // thread aggregate: sum since the last run head in the thread's range (F: a head was seen)
+    float acc[DL];
+    bool F = false;
+#pragma unroll
+    for (int k = 0; k < DL; ++k) acc[k] = 0.f;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const int i = j0 + p;
+        if (i < M) {
+            if (i == 0 || (int)ancs[i - 1] != ai[p]) {
+                F = true;
+#pragma unroll
+                for (int k = 0; k < DL; ++k) acc[k] = 0.f;
+            }
+#pragma unroll
+            for (int k = 0; k < DL; ++k) acc[k] += xbar[p][k];
+        }
+    }
+    // warp-level inclusive segmented scan over the groups (stride G keeps each dimension apart)
+    bool Fi = F;
+    float V[DL];
+#pragma unroll
+    for (int k = 0; k < DL; ++k) V[k] = acc[k];
+#pragma unroll
+    for (int o = G; o < 32; o <<= 1) {
+        const bool Fo = __shfl_up_sync(kFull, (int)Fi, o) != 0;
+        float Vo[DL];
+#pragma unroll
+        for (int k = 0; k < DL; ++k) Vo[k] = __shfl_up_sync(kFull, V[k], o);
+        if (lane >= o) {
+            if (!Fi)
+#pragma unroll
+                for (int k = 0; k < DL; ++k) V[k] += Vo[k];
+            Fi |= Fo;
+        }
+    }
+    bool Fe = __shfl_up_sync(kFull, (int)Fi, G) != 0;
+    float Ve[DL];
+#pragma unroll
+    for (int k = 0; k < DL; ++k) Ve[k] = __shfl_up_sync(kFull, V[k], G);
+    if (lane < G) {
+        Fe = false;
+#pragma unroll
+        for (int k = 0; k < DL; ++k) Ve[k] = 0.f;
+    }
+    if (lane >= 32 - G) {  // the warp's last group holds the warp aggregate of each dimension slice
+        float* w = segw + (wid * G + gl) * (DL + 1);
+        w[0] = Fi ? 1.f : 0.f;
+#pragma unroll
+        for (int k = 0; k < DL; ++k) w[1 + k] = V[k];
+    }
+    __syncthreads();
+    // prefix over the preceding warps
+    float vp[DL];
+    if constexpr (G == 1) {
+        bool Fw = (lane < nw) && segw[lane * (DL + 1)] != 0.f;
+        float Vw[DL];
+#pragma unroll
+        for (int k = 0; k < DL; ++k) Vw[k] = (lane < nw) ? segw[lane * (DL + 1) + 1 + k] : 0.f;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const bool Fo = __shfl_up_sync(kFull, (int)Fw, o) != 0;
+            float Vo[DL];
+#pragma unroll
+            for (int k = 0; k < DL; ++k) Vo[k] = __shfl_up_sync(kFull, Vw[k], o);
+            if (lane >= o) {
+                if (!Fw)
+#pragma unroll
+                    for (int k = 0; k < DL; ++k) Vw[k] += Vo[k];
+                Fw |= Fo;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < DL; ++k) vp[k] = (wid > 0) ? __shfl_sync(kFull, Vw[k], (wid + 31) & 31) : 0.f;
+    } else {
+#pragma unroll
+        for (int k = 0; k < DL; ++k) vp[k] = 0.f;
+        for (int w = 0; w < wid; ++w) {
+            const float* sw = segw + (w * G + gl) * (DL + 1);
+            const bool fw = sw[0] != 0.f;
+#pragma unroll
+            for (int k = 0; k < DL; ++k) vp[k] = fw ? sw[1 + k] : vp[k] + sw[1 + k];
+        }
+    }
+    float carry[DL];
+#pragma unroll
+    for (int k = 0; k < DL; ++k) carry[k] = Fe ? Ve[k] : vp[k] + Ve[k];
+    // second pass: running sums from the carry; complete sums at the end of each run go to
+    // the run's parent
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const int i = j0 + p;
+        if (i < M) {
+            if (i == 0 || (int)ancs[i - 1] != ai[p])
+#pragma unroll
+                for (int k = 0; k < DL; ++k) carry[k] = 0.f;
+#pragma unroll
+            for (int k = 0; k < DL; ++k) carry[k] += xbar[p][k];
+            if (i == M - 1 || (int)ancs[i + 1] != ai[p])
+#pragma unroll
+                for (int k = 0; k < DL; ++k) xbstage[ai[p] * DX + gl * DL + k] = carry[k];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+        if (j0 + p < M)
+#pragma unroll
+            for (int k = 0; k < DL; ++k) xbar[p][k] = xbstage[(j0 + p) * DX + gl * DL + k];
+}
+
 // ---------------------------------------------------------------- state I/O helpers
 
-template <int P, int DX>
+// Lane gl of a group stores/loads/stages dimensions gl*DL .. gl*DL+DL-1 of its particles;
+// rows are particle-major [M][DX], so a group writes DX contiguous floats per particle.
+template <int P, int DX, int DL>
 __device__ __forceinline__ void store_state(float* __restrict__ xdst, float* __restrict__ lwdst, int j0,
-                                            int M, const float (&x)[P][DX], const float (&lw)[P]) {
+                                            int gl, int M, const float (&x)[P][DL], const float (&lw)[P]) {
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         const int j = j0 + p;
         if (j < M) {
-            if constexpr (DX % 4 == 0) {
+            float* dst = xdst + (size_t)j * DX + gl * DL;
+            if constexpr (DL % 4 == 0) {
 #pragma unroll
-                for (int k = 0; k < DX; k += 4)
-                    *reinterpret_cast<float4*>(xdst + (size_t)j * DX + k) =
-                        make_float4(x[p][k], x[p][k + 1], x[p][k + 2], x[p][k + 3]);
+                for (int k = 0; k < DL; k += 4)
+                    *reinterpret_cast<float4*>(dst + k) = make_float4(x[p][k], x[p][k + 1], x[p][k + 2], x[p][k + 3]);
             } else {
 #pragma unroll
-                for (int k = 0; k < DX; ++k) xdst[(size_t)j * DX + k] = x[p][k];
+                for (int k = 0; k < DL; ++k) dst[k] = x[p][k];
             }
-            lwdst[j] = lw[p];
+            if (lwdst && gl == 0) lwdst[j] = lw[p];
         }
     }
 }
 
-template <int P, int DX>
-__device__ __forceinline__ void load_x(const float* __restrict__ xsrc, int j0, int M, float (&x)[P][DX]) {
+template <int P, int DX, int DL>
+__device__ __forceinline__ void load_x(const float* __restrict__ xsrc, int j0, int gl, int M,
+                                       float (&x)[P][DL]) {
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-        const int j = min(j0 + p, M - 1);
-        if constexpr (DX % 4 == 0) {
+        const float* src = xsrc + (size_t)min(j0 + p, M - 1) * DX + gl * DL;
+        if constexpr (DL % 4 == 0) {
 #pragma unroll
-            for (int k = 0; k < DX; k += 4) {
-                const float4 v = *reinterpret_cast<const float4*>(xsrc + (size_t)j * DX + k);
+            for (int k = 0; k < DL; k += 4) {
+                const float4 v = *reinterpret_cast<const float4*>(src + k);
                 x[p][k] = v.x; x[p][k + 1] = v.y; x[p][k + 2] = v.z; x[p][k + 3] = v.w;
             }
         } else {
 #pragma unroll
-            for (int k = 0; k < DX; ++k) x[p][k] = xsrc[(size_t)j * DX + k];
+            for (int k = 0; k < DL; ++k) x[p][k] = src[k];
         }
     }
 }
 
-template <int P, int DX>
-__device__ __forceinline__ void stage_x(float* xstage, int j0, int M, const float (&x)[P][DX]) {
+template <int P, int DX, int DL>
+__device__ __forceinline__ void stage_x(float* xstage, int j0, int gl, int M, const float (&x)[P][DL]) {
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         const int j = j0 + p;
         if (j < M) {
-            if constexpr (DX % 4 == 0) {
+            float* dst = xstage + j * DX + gl * DL;
+            if constexpr (DL % 4 == 0) {
 #pragma unroll
-                for (int k = 0; k < DX; k += 4)
-                    *reinterpret_cast<float4*>(xstage + j * DX + k) =
-                        make_float4(x[p][k], x[p][k + 1], x[p][k + 2], x[p][k + 3]);
+                for (int k = 0; k < DL; k += 4)
+                    *reinterpret_cast<float4*>(dst + k) = make_float4(x[p][k], x[p][k + 1], x[p][k + 2], x[p][k + 3]);
             } else {
 #pragma unroll
-                for (int k = 0; k < DX; ++k) xstage[j * DX + k] = x[p][k];
+                for (int k = 0; k < DL; ++k) dst[k] = x[p][k];
             }
         }
     }
 }
 
-template <int DX>
-__device__ __forceinline__ void read_staged(const float* xstage, int j, float (&x)[DX]) {
-    if constexpr (DX % 4 == 0) {
+template <int DX, int DL>
+__device__ __forceinline__ void read_staged(const float* xstage, int j, int gl, float (&x)[DL]) {
+    const float* src = xstage + j * DX + gl * DL;
+    if constexpr (DL % 4 == 0) {
 #pragma unroll
-        for (int k = 0; k < DX; k += 4) {
-            const float4 v = *reinterpret_cast<const float4*>(xstage + j * DX + k);
+        for (int k = 0; k < DL; k += 4) {
+            const float4 v = *reinterpret_cast<const float4*>(src + k);
             x[k] = v.x; x[k + 1] = v.y; x[k + 2] = v.z; x[k + 3] = v.w;
         }
     } else {
 #pragma unroll
-        for (int k = 0; k < DX; ++k) x[k] = xstage[j * DX + k];
+        for (int k = 0; k < DL; ++k) x[k] = src[k];
     }
+}
+
+// Normals of the lane's dimensions of its P particles: normal index n = j*DX + k.
+template <int P, int DX, int DL>
+__device__ __forceinline__ void draw_normals(PhiloxKey key, uint32_t t, uint32_t stream, int j0, int gl,
+                                             float (&eps)[P * DL]) {
+    if constexpr (DL == DX) {
+        normals<P * DX>(key, t, stream, (uint32_t)(j0 * DX), eps);
+    } else {
+#pragma unroll
+        for (int p = 0; p < P; ++p)
+            normals<DL>(key, t, stream, (uint32_t)((j0 + p) * DX + gl * DL),
+                        reinterpret_cast<float(&)[DL]>(eps[p * DL]));
+    }
+}
+
+// Sum over the G lanes of a group (every lane gets the same value).
+template <int G>
+__device__ __forceinline__ float group_sum(float v) {
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
 }
 
 struct Traj {
@@ -305,8 +495,10 @@ struct Traj {
 template <class Mdl, int P>
 __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, const SmemLayout& L,
                                typename Mdl::Params& sprm) {
-    constexpr int DX = Mdl::DX, DY = Mdl::DY;
+    constexpr int DX = Mdl::DX, DY = Mdl::DY, G = Mdl::G, DL = Mdl::DL;
     const int tid = threadIdx.x;
+    const int gl = (G > 1) ? (tid & (G - 1)) : 0;
+    const bool lead = gl == 0;
     const int M = a.M, T = a.T;
     float* xstage = reinterpret_cast<float*>(smem + L.xstage);
     float* cs = reinterpret_cast<float*>(smem + L.cs);
@@ -317,20 +509,21 @@ __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, cons
 
     if (tid == 0) Mdl::make_params(a.theta + (size_t)f * a.D, a.H, sprm);
     __syncthreads();
-    const typename Mdl::Params prm = sprm;
+    typename Mdl::LaneParams prm;
+    Mdl::lane_params(sprm, gl, prm);
     const uint32_t iter = a.iter_dev ? *a.iter_dev + 1u : a.iter;
     const PhiloxKey key = philox_key(a.seed_lo, a.seed_hi, iter, a.row0 + (uint32_t)f);
-    const int j0 = tid * P;
+    const int j0 = (tid / G) * P;
     const Traj tr{a, f, DX};
     const bool store = a.want_grad != 0;
 
-    float x[P][DX], lw[P];
+    float x[P][DL], lw[P];
     {
-        float eps[P * DX];
-        normals<P * DX>(key, 0u, kStreamInit, (uint32_t)(j0 * DX), eps);
+        float eps[P * DL];
+        draw_normals<P, DX, DL>(key, 0u, kStreamInit, j0, gl, eps);
 #pragma unroll
         for (int p = 0; p < P; ++p) {
-            Mdl::init(prm, reinterpret_cast<const float(&)[DX]>(eps[p * DX]), x[p]);
+            Mdl::init(prm, reinterpret_cast<const float(&)[DL]>(eps[p * DL]), x[p]);
             lw[p] = (j0 + p < M) ? 0.f : -INFINITY;
         }
     }
@@ -338,7 +531,7 @@ __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, cons
     double acc = 0.0;
     bool resample = false, dead = false;
     if (store) {
-        store_state<P, DX>(tr.x_ck(0), tr.lw_ck(0), j0, M, x, lw);
+        store_state<P, DX, DL>(tr.x_ck(0), tr.lw_ck(0), j0, gl, M, x, lw);
         if (tid == 0) {
             a.mstep[(size_t)f * (T + 1)] = 0.f;
             a.lstep[(size_t)f * (T + 1)] = Lprev;
@@ -346,15 +539,15 @@ __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, cons
     }
     for (int t = 1; t <= T; ++t) {
         if (resample) {
-            stage_x<P, DX>(xstage, j0, M, x);
+            stage_x<P, DX, DL>(xstage, j0, gl, M, x);
             int anc[P];
             if (a.scheme == 0) {
                 const uint4 w = philox4x32_10(make_uint4((uint32_t)t, 0u, kStreamResample, 0u), key);
-                systematic_ancestors<P>(lw, j0, M, u01_open(w.x), marks, scanw, scanwi, anc);
+                systematic_ancestors<P, G>(lw, lead, j0, M, u01_open(w.x), marks, scanw, scanwi, anc);
             } else {
-                multinomial_ancestors<P>(lw, j0, M, key, (uint32_t)t, cs, scanw, anc);
+                multinomial_ancestors<P, G>(lw, lead, j0, M, key, (uint32_t)t, cs, scanw, anc);
             }
-            if (a.anc) {
+            if (a.anc && lead) {
                 uint16_t* row = a.anc + ((size_t)f * T + (t - 1)) * M;
 #pragma unroll
                 for (int p = 0; p < P; ++p)
@@ -362,7 +555,7 @@ __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, cons
             }
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                if (j0 + p < M) read_staged<DX>(xstage, anc[p], x[p]);
+                if (j0 + p < M) read_staged<DX, DL>(xstage, anc[p], gl, x[p]);
                 lw[p] = (j0 + p < M) ? 0.f : -INFINITY;
             }
             Lprev = logf((float)M);
@@ -370,17 +563,19 @@ __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, cons
         if (tid == 0 && a.flag) a.flag[(size_t)f * T + (t - 1)] = resample ? 1 : 0;
 
         {
-            float eps[P * DX];
-            normals<P * DX>(key, (uint32_t)t, kStreamProp, (uint32_t)(j0 * DX), eps);
-            const float* yt = a.y + (size_t)(t - 1) * DY;
+            float eps[P * DL];
+            draw_normals<P, DX, DL>(key, (uint32_t)t, kStreamProp, j0, gl, eps);
+            const float* yt = a.y + (size_t)(t - 1) * DY + (G > 1 ? gl * DL : 0);
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                Mdl::transition(prm, x[p], reinterpret_cast<const float(&)[DX]>(eps[p * DX]));
-                if (j0 + p < M) lw[p] += Mdl::loglik(prm, x[p], yt);
+                Mdl::transition(prm, x[p], reinterpret_cast<const float(&)[DL]>(eps[p * DL]));
+                float g = Mdl::loglik(prm, x[p], yt);
+                if constexpr (G > 1) g = group_sum<G>(g) + prm.cst;  // whole-particle log g
+                if (j0 + p < M) lw[p] += g;
             }
         }
         float m, s1, s2;
-        block_lse3<P>(lw, red + (t & 1) * 32, m, s1, s2);
+        block_lse3<P>(lw, lead, red + (t & 1) * 32, m, s1, s2);
         if (!(isfinite(m) && isfinite(s1) && s1 > 0.f)) {
             dead = true;
             break;
@@ -396,8 +591,11 @@ __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, cons
                 a.mstep[(size_t)f * (T + 1) + t] = m;
                 a.lstep[(size_t)f * (T + 1) + t] = ls1;
             }
-            if (a.kc == 1) store_state<P, DX>(tr.x_ck(t), tr.lw_ck(t), j0, M, x, lw);
-            else if (t % a.kc == 0 && t < T) store_state<P, DX>(tr.x_ck(t / a.kc), tr.lw_ck(t / a.kc), j0, M, x, lw);
+            // with kc = 1 the adjoint reads log w only at steps followed by resampling and at T
+            if (a.kc == 1)
+                store_state<P, DX, DL>(tr.x_ck(t), (resample || t == T) ? tr.lw_ck(t) : nullptr, j0, gl, M, x, lw);
+            else if (t % a.kc == 0 && t < T)
+                store_state<P, DX, DL>(tr.x_ck(t / a.kc), tr.lw_ck(t / a.kc), j0, gl, M, x, lw);
         }
     }
     if (tid == 0) a.loglik[f] = dead ? -INFINITY : acc;
@@ -408,13 +606,15 @@ __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, cons
 template <class Mdl, int P>
 __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, const SmemLayout& L,
                                 typename Mdl::Params& sprm) {
-    constexpr int DX = Mdl::DX, DY = Mdl::DY, D = Mdl::D;
+    constexpr int DX = Mdl::DX, DY = Mdl::DY, D = Mdl::D, G = Mdl::G, DL = Mdl::DL, DTH = Mdl::DTH;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    const int gl = (G > 1) ? (tid & (G - 1)) : 0;
+    const bool lead = gl == 0;
     const int M = a.M, T = a.T, kc = a.kc;
     float* xstage = reinterpret_cast<float*>(smem + L.xstage);
     float* xbstage = reinterpret_cast<float*>(smem + L.xbstage);
     uint16_t* ancs = reinterpret_cast<uint16_t*>(smem + L.marks);
-    uint16_t* starts = reinterpret_cast<uint16_t*>(smem + L.starts);
+    float* segw = reinterpret_cast<float*>(smem + L.starts);
     double* dred = reinterpret_cast<double*>(smem + L.dred);
 
     const double ll = a.loglik[f];
@@ -424,27 +624,31 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
     }
     if (tid == 0) Mdl::make_params(a.theta + (size_t)f * a.D, a.H, sprm);
     __syncthreads();
-    const typename Mdl::Params prm = sprm;
+    typename Mdl::LaneParams prm;
+    Mdl::lane_params(sprm, gl, prm);
     const uint32_t iter = a.iter_dev ? *a.iter_dev + 1u : a.iter;
     const PhiloxKey key = philox_key(a.seed_lo, a.seed_hi, iter, a.row0 + (uint32_t)f);
-    const int j0 = tid * P;
+    const int j0 = (tid / G) * P;
     const Traj tr{a, f, DX};
     const float* lstep = a.lstep + (size_t)f * (T + 1);
     const float* mstep = a.mstep + (size_t)f * (T + 1);
     const uint8_t* flags = a.flag + (size_t)f * T;
 
-    float xbar[P][DX], lwbar[P], thb[D];
+    float xbar[P][DL], lwbar[P], thb[DTH];
 #pragma unroll
     for (int p = 0; p < P; ++p)
 #pragma unroll
-        for (int k = 0; k < DX; ++k) xbar[p][k] = 0.f;
+        for (int k = 0; k < DL; ++k) xbar[p][k] = 0.f;
 #pragma unroll
-    for (int d = 0; d < D; ++d) thb[d] = 0.f;
+    for (int d = 0; d < DTH; ++d) thb[d] = 0.f;
 
-    const int S = (kc == 1) ? T : (T + kc - 1) / kc;
+    // With kc = 1 the whole run is one segment whose every step is a checkpoint slot.
+    const int S = (kc == 1) ? 1 : (T + kc - 1) / kc;
+    float xt[P][DL];  // states x_t of the step being reversed (carried from the previous iteration)
+    float xn[P][DL];  // states x_{t-1}, loaded one iteration ahead
     for (int s = S - 1; s >= 0; --s) {
-        const int t0 = (kc == 1) ? s : s * kc;
-        const int t1 = (kc == 1) ? s + 1 : min(t0 + kc, T);
+        const int t0 = (kc == 1) ? 0 : s * kc;
+        const int t1 = (kc == 1) ? T : min(t0 + kc, T);
         auto Xp = [&](int t) -> const float* {
             if (kc == 1) return tr.x_ck(t);
             return (t == t0) ? tr.x_ck(s) : tr.x_seg(t - t0 - 1);
@@ -455,33 +659,35 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
         };
         if (kc > 1) {
             // recompute the segment (t0, t1] from its checkpoint: same CRN, tape ancestors
-            float x[P][DX], lw[P];
-            load_x<P, DX>(tr.x_ck(s), j0, M, x);
+            float x[P][DL], lw[P];
+            load_x<P, DX, DL>(tr.x_ck(s), j0, gl, M, x);
 #pragma unroll
             for (int p = 0; p < P; ++p) lw[p] = (j0 + p < M) ? tr.lw_ck(s)[j0 + p] : -INFINITY;
             for (int t = t0 + 1; t <= t1; ++t) {
                 if (flags[t - 1]) {
-                    stage_x<P, DX>(xstage, j0, M, x);
+                    stage_x<P, DX, DL>(xstage, j0, gl, M, x);
                     const uint16_t* row = a.anc + ((size_t)f * T + (t - 1)) * M;
                     __syncthreads();
 #pragma unroll
                     for (int p = 0; p < P; ++p) {
-                        if (j0 + p < M) read_staged<DX>(xstage, row[j0 + p], x[p]);
+                        if (j0 + p < M) read_staged<DX, DL>(xstage, row[j0 + p], gl, x[p]);
                         lw[p] = (j0 + p < M) ? 0.f : -INFINITY;
                     }
                     __syncthreads();
                 }
-                float eps[P * DX];
-                normals<P * DX>(key, (uint32_t)t, kStreamProp, (uint32_t)(j0 * DX), eps);
-                const float* yt = a.y + (size_t)(t - 1) * DY;
+                float eps[P * DL];
+                draw_normals<P, DX, DL>(key, (uint32_t)t, kStreamProp, j0, gl, eps);
+                const float* yt = a.y + (size_t)(t - 1) * DY + (G > 1 ? gl * DL : 0);
                 const float mt = mstep[t];
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
-                    Mdl::transition(prm, x[p], reinterpret_cast<const float(&)[DX]>(eps[p * DX]));
-                    if (j0 + p < M) lw[p] += Mdl::loglik(prm, x[p], yt);
+                    Mdl::transition(prm, x[p], reinterpret_cast<const float(&)[DL]>(eps[p * DL]));
+                    float g = Mdl::loglik(prm, x[p], yt);
+                    if constexpr (G > 1) g = group_sum<G>(g) + prm.cst;
+                    if (j0 + p < M) lw[p] += g;
                     lw[p] -= mt;
                 }
-                store_state<P, DX>(tr.x_seg(t - t0 - 1), tr.lw_seg(t - t0 - 1), j0, M, x, lw);
+                store_state<P, DX, DL>(tr.x_seg(t - t0 - 1), tr.lw_seg(t - t0 - 1), j0, gl, M, x, lw);
             }
         }
         if (s == S - 1) {
@@ -489,107 +695,88 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
             const float* lwT = LWp(T);
             const float LT = lstep[T];
 #pragma unroll
-            for (int p = 0; p < P; ++p) lwbar[p] = (j0 + p < M) ? expf(lwT[j0 + p] - LT) : 0.f;
+            for (int p = 0; p < P; ++p) lwbar[p] = (j0 + p < M) ? __expf(lwT[j0 + p] - LT) : 0.f;
+            load_x<P, DX, DL>(Xp(T), j0, gl, M, xt);
         }
+        load_x<P, DX, DL>(Xp(t1 - 1), j0, gl, M, xn);
         for (int t = t1; t > t0; --t) {
-            float xt[P][DX];
-            load_x<P, DX>(Xp(t), j0, M, xt);
-            const float* yt = a.y + (size_t)(t - 1) * DY;
+            const float* yt = a.y + (size_t)(t - 1) * DY + (G > 1 ? gl * DL : 0);
 #pragma unroll
             for (int p = 0; p < P; ++p)
                 if (j0 + p < M) Mdl::bwd_obs(prm, xt[p], yt, lwbar[p], xbar[p], thb);
             const bool fl = flags[t - 1] != 0;
-            float xp[P][DX];
+            float xp[P][DL];
             int ai[P];
             if (fl) {
-                float xprev[P][DX];
-                load_x<P, DX>(Xp(t - 1), j0, M, xprev);
-                stage_x<P, DX>(xstage, j0, M, xprev);
+                stage_x<P, DX, DL>(xstage, j0, gl, M, xn);
                 const uint16_t* row = a.anc + ((size_t)f * T + (t - 1)) * M;
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
                     ai[p] = (j0 + p < M) ? (int)row[j0 + p] : 0;
-                    if (j0 + p < M) ancs[j0 + p] = (uint16_t)ai[p];
+                    if (lead && j0 + p < M) ancs[j0 + p] = (uint16_t)ai[p];
                 }
                 __syncthreads();
 #pragma unroll
-                for (int p = 0; p < P; ++p) read_staged<DX>(xstage, ai[p], xp[p]);
+                for (int p = 0; p < P; ++p) read_staged<DX, DL>(xstage, ai[p], gl, xp[p]);
             } else {
-                load_x<P, DX>(Xp(t - 1), j0, M, xp);
+#pragma unroll
+                for (int p = 0; p < P; ++p)
+#pragma unroll
+                    for (int k = 0; k < DL; ++k) xp[p][k] = xn[p][k];
             }
 #pragma unroll
             for (int p = 0; p < P; ++p)
                 if (j0 + p < M) Mdl::bwd_trans(prm, xt[p], xp[p], xbar[p], thb);
+            // x_{t-1} is the state of the next iteration; start loading x_{t-2} now so the
+            // load overlaps the rest of this step
+#pragma unroll
+            for (int p = 0; p < P; ++p)
+#pragma unroll
+                for (int k = 0; k < DL; ++k) xt[p][k] = xn[p][k];
+            if (t - 2 >= t0) load_x<P, DX, DL>(Xp(t - 2), j0, gl, M, xn);
             if (fl) {
                 // adjoint of the gather x'_i = x_{a_i}: sum the cotangents of each parent's offspring
                 if (a.scheme == 0) {
-                    stage_x<P, DX>(xbstage, j0, M, xbar);
-#pragma unroll
-                    for (int p = 0; p < P; ++p) {
-                        const int i = j0 + p;
-                        if (i < M && (i == 0 || ancs[i - 1] != ancs[i])) starts[ancs[i]] = (uint16_t)i;
-                    }
-                    __syncthreads();
-#pragma unroll
-                    for (int p = 0; p < P; ++p) {
-                        const int j = j0 + p;
-                        float sum[DX];
-#pragma unroll
-                        for (int k = 0; k < DX; ++k) sum[k] = 0.f;
-                        if (j < M) {
-                            const int st = starts[j];
-                            if (st < M && ancs[st] == j) {
-                                for (int i = st; i < M && ancs[i] == j; ++i) {
-                                    float v[DX];
-                                    read_staged<DX>(xbstage, i, v);
-#pragma unroll
-                                    for (int k = 0; k < DX; ++k) sum[k] += v[k];
-                                }
-                            }
-                        }
-#pragma unroll
-                        for (int k = 0; k < DX; ++k) xbar[p][k] = sum[k];
-                    }
+                    gather_adjoint_sorted<P, DX, DL, G>(xbar, ai, j0, gl, M, ancs, xbstage, segw);
                 } else {
 #pragma unroll
                     for (int p = 0; p < P; ++p)
                         if (j0 + p < M)
 #pragma unroll
-                            for (int k = 0; k < DX; ++k) xbstage[(j0 + p) * DX + k] = 0.f;
+                            for (int k = 0; k < DL; ++k) xbstage[(j0 + p) * DX + gl * DL + k] = 0.f;
                     __syncthreads();
 #pragma unroll
                     for (int p = 0; p < P; ++p)
                         if (j0 + p < M)
 #pragma unroll
-                            for (int k = 0; k < DX; ++k) atomicAdd(&xbstage[ai[p] * DX + k], xbar[p][k]);
+                            for (int k = 0; k < DL; ++k)
+                                atomicAdd(&xbstage[ai[p] * DX + gl * DL + k], xbar[p][k]);
                     __syncthreads();
 #pragma unroll
                     for (int p = 0; p < P; ++p)
-                        if (j0 + p < M) read_staged<DX>(xbstage, j0 + p, xbar[p]);
+                        if (j0 + p < M) read_staged<DX, DL>(xbstage, j0 + p, gl, xbar[p]);
                 }
                 // adjoint of the mean reset log w' = LSE(log w) - log M: cotangent becomes w~_{t-1}
                 const float* lwp = LWp(t - 1);
                 const float Lp = lstep[t - 1];
 #pragma unroll
-                for (int p = 0; p < P; ++p) lwbar[p] = (j0 + p < M) ? expf(lwp[j0 + p] - Lp) : 0.f;
+                for (int p = 0; p < P; ++p) lwbar[p] = (j0 + p < M) ? __expf(lwp[j0 + p] - Lp) : 0.f;
                 __syncthreads();
             }
         }
     }
-    {
-        float x0[P][DX];
-        load_x<P, DX>(tr.x_ck(0), j0, M, x0);
+    // t = 0: the initial states are in xt
 #pragma unroll
-        for (int p = 0; p < P; ++p)
-            if (j0 + p < M) Mdl::bwd_init(prm, x0[p], xbar[p], thb);
-    }
-    // gradient: FP64 block sum of the per-thread FP32 partials
+    for (int p = 0; p < P; ++p)
+        if (j0 + p < M) Mdl::bwd_init(prm, xt[p], xbar[p], thb);
+    // gradient: FP64 block sum of the per-thread FP32 partials (lanes of equal gl hold the
+    // same parameters; Mdl::theta_index maps a lane's partial to its parameter)
 #pragma unroll
-    for (int d = 0; d < D; ++d) {
-        double v = (double)thb[d];
+    for (int l = 0; l < DTH; ++l) {
+        double v = (double)thb[l];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-        if (lane == 0) dred[d * 32 + wid] = v;
+        for (int o = 16; o >= G; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+        if (lane < G) dred[Mdl::theta_index(l, gl) * 32 + wid] = v;
     }
     __syncthreads();
     for (int d = tid; d < D; d += blockDim.x) {
@@ -601,47 +788,58 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
 
 // ---------------------------------------------------------------- kernels and launcher
 
-template <class Mdl, int P>
-__global__ void __launch_bounds__(kMaxThreads) pf_forward_kernel(PFArgs a) {
+// REGS caps the registers per thread (occupancy versus instruction-level parallelism);
+// a launch is valid while threads * REGS <= 65536 (threads <= kMaxThreads).
+template <class Mdl, int P, int REGS>
+__global__ void __maxnreg__(REGS) pf_forward_kernel(PFArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ typename Mdl::Params sprm;
-    const SmemLayout L(a.M, Mdl::DX, Mdl::D, true);
+    const SmemLayout L(a.M, Mdl::DX, Mdl::D, true, Mdl::G);
     for (int f = blockIdx.x; f < a.n; f += gridDim.x) {
         forward_filter<Mdl, P>(a, f, smem, L, sprm);
         __syncthreads();
     }
 }
 
-template <class Mdl, int P>
-__global__ void __launch_bounds__(kMaxThreads) pf_backward_kernel(PFArgs a) {
+template <class Mdl, int P, int REGS>
+__global__ void __maxnreg__(REGS) pf_backward_kernel(PFArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ typename Mdl::Params sprm;
-    const SmemLayout L(a.M, Mdl::DX, Mdl::D, false);
+    const SmemLayout L(a.M, Mdl::DX, Mdl::D, false, Mdl::G);
     for (int f = blockIdx.x; f < a.n; f += gridDim.x) {
         backward_filter<Mdl, P>(a, f, smem, L, sprm);
         __syncthreads();
     }
 }
 
-template <class Mdl, int P>
-int launch_pf(const PFArgs& a, int threads, size_t smem_fwd, size_t smem_bwd, void* stream,
-              int grid_fwd, int grid_bwd) {
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (smem_fwd > 48 * 1024 &&
-        cudaFuncSetAttribute(pf_forward_kernel<Mdl, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem_fwd) != cudaSuccess)
+// Launch one pass for a.n filters (grid = a.n CTAs, or fewer for a grid-stride launch).
+template <class Mdl, int P, int REGS>
+int launch_forward(const PFArgs& a, void* stream, int grid) {
+    const int threads = pf_threads(a.M, P, Mdl::G);
+    const size_t smem = SmemLayout(a.M, Mdl::DX, Mdl::D, true, Mdl::G).total;
+    if (threads > kMaxThreads) return -1;
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(pf_forward_kernel<Mdl, P, REGS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
         return -3;
-    if (a.want_grad && smem_bwd > 48 * 1024 &&
-        cudaFuncSetAttribute(pf_backward_kernel<Mdl, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem_bwd) != cudaSuccess)
-        return -3;
-    pf_forward_kernel<Mdl, P><<<grid_fwd, threads, smem_fwd, st>>>(a);
-    if (cudaGetLastError() != cudaSuccess) return -3;
-    if (a.want_grad) {
-        pf_backward_kernel<Mdl, P><<<grid_bwd, threads, smem_bwd, st>>>(a);
-        if (cudaGetLastError() != cudaSuccess) return -3;
-    }
-    return 0;
+    pf_forward_kernel<Mdl, P, REGS><<<grid, threads, smem, static_cast<cudaStream_t>(stream)>>>(a);
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
+
+template <class Mdl, int P, int REGS>
+int launch_backward(const PFArgs& a, void* stream, int grid) {
+    const int threads = pf_threads(a.M, P, Mdl::G);
+    const size_t smem = SmemLayout(a.M, Mdl::DX, Mdl::D, false, Mdl::G).total;
+    if (threads > kMaxThreads) return -1;
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(pf_backward_kernel<Mdl, P, REGS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return -3;
+    pf_backward_kernel<Mdl, P, REGS><<<grid, threads, smem, static_cast<cudaStream_t>(stream)>>>(a);
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+// The launch variants compiled for every model: (particles per thread, register cap).
+#define SMC2_PF_VARIANTS(X) X(1, 64) X(1, 128) X(2, 64) X(2, 128) X(4, 64) X(4, 80) X(4, 128) X(8, 64) X(8, 128)
 
 }  // namespace smc2

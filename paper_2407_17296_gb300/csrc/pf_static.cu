@@ -94,9 +94,11 @@ extern "C" int pf_loglik_grad_static(const smc2_config* cfg, const double* theta
     rc = scratch_address(&base);
     if (rc) return rc;
 
-    const int P = choose_ppt(&c);
-    const pf_launch_fn fn = select_kernel(&c, P);
-    if (!fn) return fail(SMC2_E_INVAL, "no kernel for this model shape");
+    LaunchChoice lc;
+    choose_launch(&c, &lc);
+    const pf_kernel_fn fwd = lookup_forward(&c, lc.pf, lc.rf);
+    const pf_kernel_fn bwd = lookup_backward(&c, lc.pb, lc.rb);
+    if (!fwd || !bwd) return fail(SMC2_E_INVAL, "no kernel for this model shape");
     cudaStream_t stream = static_cast<cudaStream_t>(cfg->stream);
 
     unsigned char* p = static_cast<unsigned char*>(base);
@@ -142,9 +144,9 @@ extern "C" int pf_loglik_grad_static(const smc2_config* cfg, const double* theta
     // every scratch region is written before it is read within this call: the forward pass
     // writes the flags and per-step scalars of every step it runs, the tape rows of every
     // resampling step and every checkpoint slot; nothing has to start at zero.
-    const SmemLayout lf(c.M, c.d_x, D, true), lb(c.M, c.d_x, D, false);
-    if (fn(a, pf_threads(c.M, P), lf.total, lb.total, stream, n, n))
-        return fail(SMC2_E_CUDA, std::string("filter launch failed: ") + cudaGetErrorString(cudaGetLastError()));
+    int lrc = fwd(a, stream, n);
+    if (!lrc && a.want_grad) lrc = bwd(a, stream, n);
+    if (lrc) return fail(SMC2_E_CUDA, std::string("filter launch failed: ") + cudaGetErrorString(cudaGetLastError()));
     count_launches(a.want_grad ? 2 : 1);
     return SMC2_OK;
 }

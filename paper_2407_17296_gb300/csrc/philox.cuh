@@ -50,20 +50,34 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, PhiloxKey key) {
     return c;
 }
 
-__device__ __forceinline__ float u01_open(uint32_t u) {   // (0, 1]
-    return (float)((u >> 8) + 1u) * 5.9604644775390625e-08f;
-}
-__device__ __forceinline__ float u01_half(uint32_t u) {   // [0, 1)
-    return (float)(u >> 8) * 5.9604644775390625e-08f;
+// The float of an integer k in [0, 2^24], built exactly from bits (a plain int-to-float
+// conversion runs on the narrow FP64/conversion pipe of this GPU): 2^23 + (k >> 1) is
+// exact as a float with exponent 23, so ((that - 2^23) * 2 + (k & 1)) is k.
+__device__ __forceinline__ float exact_u24_to_float(uint32_t k) {
+    const float half = __uint_as_float(0x4b000000u | (k >> 1)) - 8388608.0f;
+    return fmaf(half, 2.0f, (k & 1u) ? 1.0f : 0.0f);
 }
 
-// One Box-Muller pair from two words.
+__device__ __forceinline__ float u01_open(uint32_t u) {   // (0, 1]
+    return exact_u24_to_float((u >> 8) + 1u) * 5.9604644775390625e-08f;
+}
+__device__ __forceinline__ float u01_half(uint32_t u) {   // [0, 1)
+    return exact_u24_to_float(u >> 8) * 5.9604644775390625e-08f;
+}
+
+// One Box-Muller pair from two words.  The angle is evaluated as
+// phi' = 2 pi (U[0,1) - 1/2) in [-pi, pi), where the hardware sine/cosine are accurate
+// (absolute error ~2^-21), and cos(phi') = -cos(2 pi U), sin(phi') = -sin(2 pi U) restore
+// the definition.  The radius keeps the accurate logf; sqrt(s) = s * rsqrt(s) with s = 0
+// (the uniform equal to 1) mapped to 0.
 __device__ __forceinline__ void box_muller(uint32_t ua, uint32_t ub, float& z0, float& z1) {
-    const float r = sqrtf(-2.0f * logf(u01_open(ua)));
-    float s, c;
-    sincospif(2.0f * u01_half(ub), &s, &c);
-    z0 = r * c;
-    z1 = r * s;
+    const float s = -2.0f * logf(u01_open(ua));
+    const float r = (s > 0.f) ? s * rsqrtf(s) : 0.f;
+    const float ph = 6.2831853071795864769f * (u01_half(ub) - 0.5f);
+    float sn, cs;
+    __sincosf(ph, &sn, &cs);
+    z0 = -r * cs;
+    z1 = -r * sn;
 }
 
 // Normals n0 .. n0+COUNT-1 of (key, t, stream) into out[].  n0 % 4 == 0 when

@@ -21,21 +21,28 @@ int fail(int code, const std::string& msg);
 void count_launches(int n);
 int family_dims(const smc2_config* c, int* D);
 int validate(const smc2_config* c, int* D);
-pf_launch_fn select_kernel(const smc2_config* c, int P);
-int choose_ppt(const smc2_config* c);
+int model_lanes(const smc2_config* c);                // lanes per particle (G)
+bool variant_fits(const smc2_config* c, int P, int regs);  // block size and registers allow it
+pf_kernel_fn lookup_forward(const smc2_config* c, int P, int regs);
+pf_kernel_fn lookup_backward(const smc2_config* c, int P, int regs);
 int choose_kc(const smc2_config* c);
+// launch choice: explicit particles_per_thread / ckpt_every, else the autotuner's cached
+// choice for this shape, else a heuristic default
+void choose_launch(const smc2_config* c, LaunchChoice* lc);
+bool tuned_launch(const smc2_config* c, LaunchChoice* lc);
 void plan_sizes(const smc2_config* c, int D, int kc, Sizes* s);
 
 }  // namespace smc2
 
 struct smc2_handle {
     smc2_config cfg{};        // copy; pointer members cleared
-    int D = 0, P = 4, threads = 32, kc = 1;
+    int D = 0, kc = 1;
+    smc2::LaunchChoice lc;
     smc2::Sizes sizes;
     size_t footprint = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    smc2::pf_launch_fn pf = nullptr;
+    smc2::pf_kernel_fn fwd = nullptr, bwd = nullptr;
     // device state
     float *y = nullptr, *H = nullptr;
     double *prior_m = nullptr, *prior_s = nullptr;

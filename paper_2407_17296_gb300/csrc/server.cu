@@ -291,35 +291,70 @@ extern "C" int smc2_server_destroy(smc2_server* s) {
 
 namespace {
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int, int, int, int>, std::pair<int, int>> g_tune_cache;
+std::map<std::tuple<int, int, int, int, int, int, int, int>, LaunchChoice> g_tune_cache;
+
+std::tuple<int, int, int, int, int, int, int, int> tune_key(const smc2_config* c) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return std::make_tuple(dev, c->model_family, c->d_x, c->d_y, c->M, c->N, c->T, c->pf_resample);
+}
+
+const int kVariants[][2] = {{1, 64}, {1, 128}, {2, 64}, {2, 128}, {4, 64}, {4, 80}, {4, 128}, {8, 64}, {8, 128}};
+
+// best of `reps` timed calls of fn (after one warm-up), in ms; 1e30 if a launch fails
+template <class F>
+float time_best(cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, int reps, F&& fn) {
+    if (fn()) {
+        cudaGetLastError();
+        return 1e30f;
+    }
+    float best = 1e30f;
+    for (int r = 0; r < reps; ++r) {
+        cudaEventRecord(e0, st);
+        const int rc = fn();
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        if (rc) {
+            cudaGetLastError();
+            return 1e30f;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) best = ms;
+    }
+    return best;
+}
 }  // namespace
+
+bool smc2::tuned_launch(const smc2_config* c, LaunchChoice* lc) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(tune_key(c));
+    if (it == g_tune_cache.end()) return false;
+    *lc = it->second;
+    return true;
+}
 
 extern "C" int smc2_autotune(const smc2_config* cfg, int* ppt, int* ckpt) {
     int D = 0;
     int rc = validate(cfg, &D);
     if (rc) return rc;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    const auto key = std::make_tuple(dev, cfg->model_family, cfg->d_x, cfg->M, cfg->N, cfg->T, cfg->pf_resample);
-    {
-        std::lock_guard<std::mutex> lk(g_tune_mu);
-        auto it = g_tune_cache.find(key);
-        if (it != g_tune_cache.end()) {
-            if (ppt) *ppt = it->second.first;
-            if (ckpt) *ckpt = it->second.second;
-            return SMC2_OK;
-        }
+    LaunchChoice best;
+    if (tuned_launch(cfg, &best)) {
+        if (ppt) *ppt = best.pf;
+        if (ckpt) *ckpt = best.kc;
+        return SMC2_OK;
     }
+    choose_launch(cfg, &best);
     const int Tt = cfg->T < 64 ? cfg->T : 64;  // time a prefix of the series; cost is linear in T
-    const int kcs[] = {1, 4, 8, 16};
-    const int ps[] = {1, 2, 4, 8};
-    double* th = nullptr;
-    double* ll = nullptr;
-    double* g = nullptr;
     const size_t N = cfg->N;
-    if (cudaMalloc(&th, sizeof(double) * N * D) != cudaSuccess) return fail(SMC2_E_NOMEM, "autotune alloc");
-    cudaMalloc(&ll, sizeof(double) * N);
-    cudaMalloc(&g, sizeof(double) * N * D);
+    double *th = nullptr, *ll = nullptr, *g = nullptr;
+    if (cudaMalloc(&th, sizeof(double) * N * D) != cudaSuccess || cudaMalloc(&ll, sizeof(double) * N) != cudaSuccess ||
+        cudaMalloc(&g, sizeof(double) * N * D) != cudaSuccess) {
+        cudaFree(th);
+        cudaFree(ll);
+        cudaGetLastError();
+        return fail(SMC2_E_NOMEM, "autotune allocation failed");
+    }
     std::vector<double> th0(N * D, 0.0);
     for (size_t i = 0; i < N; ++i)
         for (int d = 0; d < D; ++d) th0[i * D + d] = cfg->prior_mean ? cfg->prior_mean[d] : 0.0;
@@ -327,47 +362,76 @@ extern "C" int smc2_autotune(const smc2_config* cfg, int* ppt, int* ckpt) {
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    float best = 1e30f;
-    int bp = choose_ppt(cfg), bk = choose_kc(cfg);
-    for (int P : ps) {
-        if (pf_threads(cfg->M, P) > 512) continue;
-        for (int kc : kcs) {
+    auto make = [&](int kc) -> smc2_handle* {
+        smc2_config c = *cfg;
+        c.T = Tt;
+        c.ckpt_every = kc;
+        c.particles_per_thread = 0;
+        c.stream = nullptr;
+        smc2_handle* h = nullptr;
+        if (smc2_create(&c, &h) != SMC2_OK) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return h;
+    };
+    // 1. forward and adjoint variants, timed separately at the default checkpoint interval
+    if (smc2_handle* h = make(best.kc > Tt ? 1 : best.kc)) {
+        const PFArgs a = make_pf_args(h, th, (int)N, 1, 0, nullptr, ll, g);
+        float bf = 1e30f, bb = 1e30f;
+        for (auto& v : kVariants) {
+            pf_kernel_fn f = lookup_forward(cfg, v[0], v[1]);
+            if (!f) continue;
+            const float ms = time_best(h->stream, e0, e1, 3, [&] { return f(a, h->stream, (int)N); });
+            if (ms < bf) {
+                bf = ms;
+                best.pf = v[0];
+                best.rf = v[1];
+            }
+        }
+        pf_kernel_fn fbest = lookup_forward(cfg, best.pf, best.rf);
+        if (fbest && !fbest(a, h->stream, (int)N)) {
+            for (auto& v : kVariants) {
+                pf_kernel_fn b = lookup_backward(cfg, v[0], v[1]);
+                if (!b) continue;
+                const float ms = time_best(h->stream, e0, e1, 3, [&] { return b(a, h->stream, (int)N); });
+                if (ms < bb) {
+                    bb = ms;
+                    best.pb = v[0];
+                    best.rb = v[1];
+                }
+            }
+        }
+        cudaStreamSynchronize(h->stream);
+        smc2_destroy(h);
+    }
+    // 2. checkpoint interval with those variants, among the ones whose full-length
+    //    trajectory fits the storage budget
+    if (cfg->ckpt_every <= 0) {
+        float bk = 1e30f;
+        for (int kc : {1, 4, 8, 16}) {
             if (kc > Tt) continue;
-            smc2_config c = *cfg;
-            c.T = Tt;
-            c.particles_per_thread = P;
-            c.ckpt_every = kc;
-            c.stream = nullptr;
-            smc2_handle* h = nullptr;
-            if (smc2_create(&c, &h) != SMC2_OK) {
-                cudaGetLastError();
-                continue;
-            }
-            float ms = 1e30f;
-            bool okrun = pf_loglik_grad(h, th, (int)N, 1, ll, g) == SMC2_OK;  // warm-up
-            for (int rep = 0; rep < 3 && okrun; ++rep) {
-                cudaEventRecord(e0, h->stream);
-                okrun = pf_loglik_grad(h, th, (int)N, 1, ll, g) == SMC2_OK;
-                cudaEventRecord(e1, h->stream);
-                cudaEventSynchronize(e1);
-                float t = 0.f;
-                cudaEventElapsedTime(&t, e0, e1);
-                if (t < ms) ms = t;
-            }
-            // checkpointing trades memory for recomputation: prefer storing every step only
-            // while it fits the same trajectory budget the heuristic uses
             smc2_config full = *cfg;
-            full.ckpt_every = kc;
             Sizes sz;
             plan_sizes(&full, D, kc, &sz);
-            const bool fits = (double)(sz.xck + sz.lwck + sz.xseg + sz.lwseg) <= 16.0e9;
-            if (okrun && fits && ms < best) {
-                best = ms;
-                bp = P;
-                bk = kc;
+            if ((double)(sz.xck + sz.lwck + sz.xseg + sz.lwseg) > 16.0e9) continue;
+            smc2_handle* h = make(kc);
+            if (!h) continue;
+            h->lc = best;
+            h->lc.kc = kc;
+            h->fwd = lookup_forward(cfg, best.pf, best.rf);
+            h->bwd = lookup_backward(cfg, best.pb, best.rb);
+            const PFArgs a = make_pf_args(h, th, (int)N, 1, 0, nullptr, ll, g);
+            const float ms = time_best(h->stream, e0, e1, 3, [&] { return launch_filters(h, a); });
+            if (ms < bk) {
+                bk = ms;
+                best.kc = kc;
             }
+            cudaStreamSynchronize(h->stream);
             smc2_destroy(h);
         }
+    } else {
+        best.kc = cfg->ckpt_every;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -377,9 +441,9 @@ extern "C" int smc2_autotune(const smc2_config* cfg, int* ppt, int* ckpt) {
     cudaGetLastError();
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune_cache[key] = {bp, bk};
+        g_tune_cache[tune_key(cfg)] = best;
     }
-    if (ppt) *ppt = bp;
-    if (ckpt) *ckpt = bk;
+    if (ppt) *ppt = best.pf;
+    if (ckpt) *ckpt = best.kc;
     return SMC2_OK;
 }

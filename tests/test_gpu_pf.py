@@ -19,7 +19,8 @@ def _report(name, agg):
     print(f"\n[{name}] " + ", ".join(f"{k}={v}" for k, v in sorted(agg.items())))
 
 
-@pytest.mark.parametrize("make,T,M,n", [(W.lg1, 80, 300, 9), (W.lg4, 60, 1000, 7), (W.sv, 90, 517, 6)])
+@pytest.mark.parametrize("make,T,M,n", [(W.lg1, 80, 300, 9), (W.lg4, 60, 1000, 7), (W.sv, 90, 517, 6),
+                                        (W.lg16, 30, 250, 4)])
 @pytest.mark.parametrize("scheme", [0, 1])
 @pytest.mark.parametrize("kc", [1, 7])
 def test_parity_small(make, T, M, n, scheme, kc):
@@ -48,6 +49,25 @@ def test_parity_full_size_lg4():
     assert np.all(np.isfinite(ll)) and np.all(np.isfinite(g))
     agg = check_rows(w, theta, ll, g, anc, flag, [0, 1, 513, 1022, 1023], iteration=2)
     _report("lg4 full", agg)
+
+
+def test_parity_full_size_lg16():
+    """Full 16-dimensional workload (N=2048, M=1024, T=200, D=48; each particle spread over
+    four lanes); sampled filters checked one by one."""
+    w = W.lg16()
+    theta = W.thetas_near(w, w.N, 0.03, seed=23)
+    ll, g, anc, flag = gpu_pf(w, theta, iteration=2)
+    assert np.all(np.isfinite(ll)) and np.all(np.isfinite(g))
+    agg = check_rows(w, theta, ll, g, anc, flag, [0, 1500, 2047], iteration=2)
+    _report("lg16 full", agg)
+
+
+@pytest.mark.parametrize("ppt", [4, 8])
+def test_parity_lg16_particles_per_thread(ppt):
+    w = W.lg16(T=20, N=2, M=500)
+    theta = W.thetas_near(w, 2, 0.03, seed=6)
+    ll, g, anc, flag = gpu_pf(w, theta, particles_per_thread=ppt, ckpt_every=6)
+    check_rows(w, theta, ll, g, anc, flag, range(2))
 
 
 def test_parity_full_size_sv():

@@ -92,6 +92,14 @@ def test_smc2_sv_small_matches_oracle():
     _compare(recs, ref)
 
 
+def test_smc2_lg16_small_matches_oracle():
+    w = W.lg16(T=25, N=16, M=128, K=3)
+    recs, hints = _run_gpu(w, w.K)
+    ref, _ = osmc2.run(w.family, 16, 16, None, w.y, w.N, w.M, w.K, w.gamma, "langevin", w.seed,
+                       hints=hints, band=BAND, flag_band=BAND, band_rel=BAND_REL)
+    _compare(recs, ref, stable=_stable_lg(16))
+
+
 def test_smc2_invariants_full_lg4():
     """Full-size linear-Gaussian job: three iterations stay finite with ESS in [1, N]."""
     w = W.lg4(K=3)
