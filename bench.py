@@ -47,6 +47,11 @@ def _args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--N", type=int, default=0, help="override the number of samples (profiling runs)")
     p.add_argument("--no-autotune", action="store_true", help="use the default launch configuration")
+    p.add_argument("--serve", action="store_true",
+                   help="serving workload: Poisson-arriving jobs, batched server vs one job at a time")
+    p.add_argument("--serve-jobs", type=int, default=256)
+    p.add_argument("--serve-iters", type=int, default=2, help="SMC2 iterations per served job")
+    p.add_argument("--serve-load", type=float, default=0.7, help="arrival rate as a fraction of capacity")
     return p.parse_args()
 
 
@@ -172,13 +177,11 @@ def run_gpu(a, rank, world, local):
     binding.load()
     stream = torch.cuda.Stream(device=dev)
     cfg = binding.config_for(w, stream=stream.cuda_stream)
-    ppt, kc = binding.ctypes.c_int(0), binding.ctypes.c_int(0)
     if not a.no_autotune:
-        binding.check(binding.load().smc2_autotune(binding.ctypes.byref(cfg), binding.ctypes.byref(ppt),
-                                                   binding.ctypes.byref(kc)), "smc2_autotune")
-    cfg = binding.config_for(w, stream=stream.cuda_stream, particles_per_thread=ppt.value,
-                             ckpt_every=kc.value)
+        # tune on parameters near the data-generating ones: the steady state of the sampler
+        binding.autotune(cfg, workloads.thetas_near(w, w.N, 0.05, seed=5))
     h = binding.Handle(cfg)
+    launch = h.launch()
     ps_per_step = w.N * w.M * w.T
 
     def barrier():
@@ -214,14 +217,18 @@ def run_gpu(a, rank, world, local):
     with torch.cuda.stream(stream):
         h.pf_loglik_grad(th, 1, ll, g)
         reps = max(3, a.steps // 2)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
         for r in range(reps):
             h.pf_loglik_grad(th, 2 + r, ll, g)
         e1.record(stream)
+        for r in range(reps):
+            h.pf_loglik_grad(th, 2 + r, ll, None)  # forward pass alone, same filters
+        e2.record(stream)
     torch.cuda.synchronize()
     clocks = clk.stop()
     pf_ms = e0.elapsed_time(e1) / reps
+    fwd_ms = e1.elapsed_time(e2) / reps
 
     # end to end through the C ABI with host buffers: observations in, stats + samples out
     y_host = torch.tensor(w.y, dtype=torch.float32).pin_memory().numpy()
@@ -277,7 +284,8 @@ def run_gpu(a, rank, world, local):
         "data": "synthetic (seeded simulation of the model; no dataset)",
         "config": {"workload": f"{w.name}: LG-diag d_x={w.dx} d_y={w.dy}" if w.family == 0 else f"{w.name}: SV",
                    "N": w.N, "M": w.M, "T": w.T, "D": w.D, "proposal": w.proposal, "gamma": w.gamma,
-                   "particles_per_thread": ppt.value, "ckpt_every": kc.value,
+                   "launch": {"forward_ppt": launch[0], "forward_regs": launch[1], "adjoint_ppt": launch[2],
+                              "adjoint_regs": launch[3], "ckpt_every": launch[4]},
                    "step": "one SMC2 iteration: propose, N filters fwd+adjoint, L-kernel weights, resample",
                    "l2": "inputs larger than L2 (particle trajectory of several GB written and read per step)",
                    "parallelism": f"replicas x{world} (independent jobs)"},
@@ -285,7 +293,8 @@ def run_gpu(a, rank, world, local):
         "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s",
                      "frac": achieved_tops / peak_tops if peak_tops else None, "traffic": traffic,
                      "kernel": "pf_forward_kernel + pf_backward_kernel",
-                     "kernel_ms": pf_ms, "ops_per_particle_step": ALG_OPS.get(w.name),
+                     "kernel_ms": pf_ms, "forward_ms": fwd_ms, "adjoint_ms": pf_ms - fwd_ms,
+                     "ops_per_particle_step": ALG_OPS.get(w.name),
                      "peak_basis": f"{sm_count} SMs x 128 FP32/INT32 lanes x {max_mhz:.0f} MHz"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(w.T * w.dy * 4),
                 "d2h_bytes_per_step": int(w.N * w.D * 8 + w.N * 8 + 8 * (6 + 2 * w.D))},
@@ -335,9 +344,82 @@ def run_reference(a, rank, world):
     }
 
 
+def run_serve(a):
+    """256 jobs of the four model families with T ~ U[50, 1000], N in {256, 1024, 4096},
+    M in {128, 512, 2048} (M <= 1024 for the 16-dimensional model), Poisson arrivals.
+    1. capacity: all jobs submitted at once to the batched server;
+    2. arrivals at serve_load x capacity, batched (up to 16 jobs in flight) and serial
+       (one job at a time, the same arrival times): p50/p99 job latency and throughput."""
+    import numpy as np
+    import torch
+    from dataclasses import replace
+    from paper_2407_17296_gb300 import binding, workloads
+
+    torch.cuda.set_device(0)
+    binding.load()
+    stream = workloads.serving_stream(n_jobs=a.serve_jobs, rate_hz=1.0)
+    jobs = []
+    for t, wl in stream:
+        M = min(wl.M, 1024) if wl.name == "lg16" else wl.M
+        jobs.append((t, replace(wl, K=a.serve_iters, M=M)))
+    work = [wl.N * wl.M * wl.T * wl.K for _, wl in jobs]
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(0.8 * free)
+
+    def run(arrivals, max_active):
+        lat = np.zeros(len(jobs))
+        with binding.Server(budget, max_active) as srv:
+            ids = [None] * len(jobs)
+            done = 0
+            nxt = 0
+            t0 = time.perf_counter()
+            while done < len(jobs):
+                now = time.perf_counter() - t0
+                while nxt < len(jobs) and arrivals[nxt] <= now:
+                    ids[nxt] = srv.submit(binding.config_for(jobs[nxt][1]))
+                    nxt += 1
+                for j in range(nxt):
+                    if ids[j] is not None:
+                        r = srv.poll(ids[j])
+                        if r is not None:
+                            if r["status"] != 0:
+                                raise RuntimeError(f"served job {j} failed: {r['status']}")
+                            lat[j] = r["latency_s"]
+                            ids[j] = None
+                            done += 1
+                time.sleep(0.0005)
+            makespan = time.perf_counter() - t0
+        return lat, makespan
+
+    sat_lat, sat_span = run(np.zeros(len(jobs)), 16)
+    capacity = len(jobs) / sat_span
+    lam = a.serve_load * capacity
+    base = np.array([t for t, _ in jobs])
+    arrivals = base * (1.0 / lam) / (base[-1] / len(jobs))  # same Poisson pattern at rate lam
+    b_lat, b_span = run(arrivals, 16)
+    s_lat, s_span = run(arrivals, 1)
+    total = float(sum(work))
+    return {
+        "metric": "served-job latency p50/p99 and particle-steps/s, batched vs serial",
+        "workload": f"{len(jobs)} jobs, families lg1/lg4/sv/lg16, T~U[50,1000], N in {{256,1024,4096}}, "
+                    f"M in {{128,512,2048}}, {a.serve_iters} SMC2 iterations per job, Poisson arrivals",
+        "capacity_jobs_per_s": capacity, "arrival_rate_jobs_per_s": lam, "load": a.serve_load,
+        "batched": {"p50_s": float(np.percentile(b_lat, 50)), "p99_s": float(np.percentile(b_lat, 99)),
+                    "particle_steps_per_s": total / b_span, "makespan_s": b_span, "max_active": 16},
+        "serial": {"p50_s": float(np.percentile(s_lat, 50)), "p99_s": float(np.percentile(s_lat, 99)),
+                   "particle_steps_per_s": total / s_span, "makespan_s": s_span, "max_active": 1},
+        "saturated_batched": {"particle_steps_per_s": total / sat_span, "makespan_s": sat_span},
+        "hbm_budget_bytes": budget,
+    }
+
+
 def main():
     a = _args()
     rank, world, local = _dist_env()
+    if a.serve:
+        if rank == 0:
+            print(json.dumps(run_serve(a)), flush=True)
+        return
     if a.impl == "reference":
         out = run_reference(a, rank, world)
     else:

@@ -187,10 +187,20 @@ int smc2_footprint(const smc2_config* cfg, size_t* bytes);
 
 int smc2_destroy(smc2_handle* h);
 
-/* Launch-configuration choice for a model shape (the autotuner): particles per thread
- * and checkpoint interval picked by timing candidates on the current device once per
- * (family, d_x, d_y, M, T) and cached in-process.  Writes the choice to *ppt and *ckpt. */
-int smc2_autotune(const smc2_config* cfg, int* ppt, int* ckpt);
+/* Launch-configuration choice for a model shape (the autotuner): for the forward pass and
+ * the adjoint separately, the particles-per-thread / register-cap variant, then the
+ * checkpoint interval, each picked by timing the candidates with CUDA events on the
+ * current device over a 64-step prefix of y, once per (device, family, d_x, d_y, M, N, T,
+ * resampler), and cached in-process; later smc2_create calls with particles_per_thread = 0
+ * and ckpt_every = 0 use it.  theta_host ([N][D] FP64, host) are the parameters to time
+ * with (NULL: every row at the prior mean); representative values matter because the
+ * resampling rate, and so the cost, depends on them.  Writes the forward pass's particles
+ * per thread to *ppt and the checkpoint interval to *ckpt (either may be NULL). */
+int smc2_autotune(const smc2_config* cfg, const double* theta_host, int* ppt, int* ckpt);
+
+/* The launch choice of a handle: out[0..4] = forward particles per thread, forward
+ * register cap, adjoint particles per thread, adjoint register cap, checkpoint interval. */
+int smc2_get_launch(const smc2_handle* h, int* out);
 
 /* Number of kernels this library launched since load (a device-work counter). */
 uint64_t smc2_kernel_launches(void);

@@ -23,7 +23,7 @@ SYSTEMATIC, MULTINOMIAL = 0, 1
 EXPORTS = ("smc2_config_init", "smc2_create", "pf_loglik_grad", "pf_loglik_grad_rows",
            "pf_loglik_grad_host", "smc2_step", "smc2_get_samples", "smc2_get_state",
            "smc2_get_trace", "smc2_set_observations", "smc2_footprint", "smc2_destroy",
-           "smc2_autotune", "smc2_kernel_launches", "smc2_last_error", "smc2_server_create",
+           "smc2_autotune", "smc2_get_launch", "smc2_kernel_launches", "smc2_last_error", "smc2_server_create",
            "smc2_submit", "smc2_poll", "smc2_cancel", "smc2_server_destroy",
            "pf_loglik_grad_static")
 
@@ -108,8 +108,9 @@ def load(path: str = LIB_PATH):
         "smc2_set_observations": (ctypes.c_int, [vp, vp]),
         "smc2_footprint": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_size_t)]),
         "smc2_destroy": (ctypes.c_int, [vp]),
-        "smc2_autotune": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_int),
+        "smc2_autotune": (ctypes.c_int, [ctypes.POINTER(Config), dp, ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int)]),
+        "smc2_get_launch": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int)]),
         "smc2_kernel_launches": (u64, []),
         "smc2_last_error": (ctypes.c_char_p, []),
         "smc2_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(vp)]),
@@ -273,10 +274,77 @@ class Handle:
               "smc2_get_trace")
         return anc, flag, oanc, bool(ores.value)
 
+    def launch(self):
+        """(forward particles/thread, forward register cap, adjoint particles/thread,
+        adjoint register cap, checkpoint interval) chosen for this handle."""
+        out = (ctypes.c_int * 5)()
+        check(self.lib.smc2_get_launch(self.h, out), "smc2_get_launch")
+        return tuple(out)
+
     def set_observations(self, y):
         import numpy as np
         ya = np.ascontiguousarray(np.asarray(y, dtype=np.float32))
         check(self.lib.smc2_set_observations(self.h, _ptr(ya)), "smc2_set_observations")
+
+
+class Server:
+    """Continuous-batching request loop (smc2_server_create ... smc2_server_destroy)."""
+
+    def __init__(self, hbm_budget: int, max_active: int = 8):
+        self.lib = load()
+        s = ctypes.c_void_p()
+        check(self.lib.smc2_server_create(int(hbm_budget), int(max_active), ctypes.byref(s)),
+              "smc2_server_create")
+        self.s = s
+        self.D = {}
+        self.N = {}
+
+    def submit(self, cfg: Config) -> int:
+        jid = ctypes.c_uint64(0)
+        check(self.lib.smc2_submit(self.s, ctypes.byref(cfg), ctypes.byref(jid)), "smc2_submit")
+        self.D[jid.value] = cfg.D
+        self.N[jid.value] = cfg.N
+        return jid.value
+
+    def poll(self, job_id: int):
+        """None while pending; else a dict with the job's results (the job is released)."""
+        import numpy as np
+        D, N = self.D.get(job_id, 1), self.N.get(job_id, 1)
+        r = Result()
+        th = np.zeros((N, D))
+        lw = np.zeros(N)
+        rec = np.zeros(D)
+        r.theta, r.logw, r.recycled_mean = th.ctypes.data, lw.ctypes.data, rec.ctypes.data
+        rc = check(self.lib.smc2_poll(self.s, int(job_id), ctypes.byref(r)), "smc2_poll")
+        if rc == SMC2_PENDING:
+            return None
+        return {"status": r.status, "K": r.K, "latency_s": r.latency_s, "queue_s": r.queue_s,
+                "theta": th, "logw": lw, "recycled_mean": rec}
+
+    def cancel(self, job_id: int):
+        check(self.lib.smc2_cancel(self.s, int(job_id)), "smc2_cancel")
+
+    def close(self):
+        if getattr(self, "s", None) is not None and self.s.value:
+            check(self.lib.smc2_server_destroy(self.s), "smc2_server_destroy")
+            self.s = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def autotune(cfg: Config, theta=None):
+    """Time the launch variants for cfg's shape on the current device (optionally on the
+    given [N][D] parameters) and cache the fastest; returns (particles/thread, ckpt)."""
+    import numpy as np
+    th = None if theta is None else np.ascontiguousarray(theta, dtype=np.float64)
+    ppt, kc = ctypes.c_int(0), ctypes.c_int(0)
+    check(load().smc2_autotune(ctypes.byref(cfg), _ptr(th), ctypes.byref(ppt), ctypes.byref(kc)),
+          "smc2_autotune")
+    return ppt.value, kc.value
 
 
 def footprint(cfg: Config) -> int:
@@ -288,7 +356,8 @@ def footprint(cfg: Config) -> int:
 def config_for(workload, **kw):
     """Config for a workloads.Workload (sizes, data and step size taken from it)."""
     prop = LANGEVIN if workload.proposal == "langevin" else RW
-    args = dict(proposal=prop, gamma=workload.gamma, K_iters=workload.K, seed=workload.seed)
+    args = dict(proposal=prop, gamma=workload.gamma, K_iters=workload.K, seed=workload.seed,
+                prior_mean=workload.prior_mean, prior_std=workload.prior_std)
     args.update(kw)
     return make_config(workload.family, workload.dx, workload.dy, workload.T, workload.N, workload.M,
                        workload.D, workload.y, workload.H, **args)

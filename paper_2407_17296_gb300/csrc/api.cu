@@ -147,12 +147,20 @@ void smc2::choose_launch(const smc2_config* c, LaunchChoice* lc) {
 
 int smc2::choose_kc(const smc2_config* c) {
     if (c->ckpt_every > 0) return c->ckpt_every;
-    // store every step while the trajectory stays modest; otherwise checkpoint
+    // store every step while the trajectory stays within 16 GB; otherwise the interval
+    // that minimises checkpoints + segment scratch, about T/kc + kc steps (kc ~ sqrt(T))
     const double per_step = (double)c->N * c->M * (4.0 * c->d_x + 4.0);
-    const double budget = 16.0e9;
-    int kc = 1;
-    while (kc < c->T && per_step * ((double)c->T / kc + 1.0 + (kc > 1 ? kc : 0)) > budget) kc *= 2;
-    return kc;
+    if (per_step * (c->T + 1.0) <= 16.0e9) return 1;
+    int best = 2;
+    double best_steps = 1e300;
+    for (int kc = 2; kc <= c->T; kc *= 2) {
+        const double steps = std::ceil((double)c->T / kc) + kc;
+        if (steps < best_steps) {
+            best_steps = steps;
+            best = kc;
+        }
+    }
+    return best;
 }
 
 int smc2::validate(const smc2_config* c, int* D) {
@@ -326,6 +334,16 @@ extern "C" int smc2_create(const smc2_config* cfg, smc2_handle** out) {
     ok = ok && cudaStreamSynchronize(h->stream) == cudaSuccess;
     if (!ok) return cleanup(SMC2_E_CUDA, std::string("initial copies failed: ") + cudaGetErrorString(cudaGetLastError()));
     *out = h;
+    return SMC2_OK;
+}
+
+extern "C" int smc2_get_launch(const smc2_handle* h, int* out) {
+    if (!h || !out) return fail(SMC2_E_INVAL, "NULL argument");
+    out[0] = h->lc.pf;
+    out[1] = h->lc.rf;
+    out[2] = h->lc.pb;
+    out[3] = h->lc.rb;
+    out[4] = h->lc.kc;
     return SMC2_OK;
 }
 

@@ -334,7 +334,7 @@ bool smc2::tuned_launch(const smc2_config* c, LaunchChoice* lc) {
     return true;
 }
 
-extern "C" int smc2_autotune(const smc2_config* cfg, int* ppt, int* ckpt) {
+extern "C" int smc2_autotune(const smc2_config* cfg, const double* theta_host, int* ppt, int* ckpt) {
     int D = 0;
     int rc = validate(cfg, &D);
     if (rc) return rc;
@@ -357,7 +357,8 @@ extern "C" int smc2_autotune(const smc2_config* cfg, int* ppt, int* ckpt) {
     }
     std::vector<double> th0(N * D, 0.0);
     for (size_t i = 0; i < N; ++i)
-        for (int d = 0; d < D; ++d) th0[i * D + d] = cfg->prior_mean ? cfg->prior_mean[d] : 0.0;
+        for (int d = 0; d < D; ++d)
+            th0[i * D + d] = theta_host ? theta_host[i * D + d] : (cfg->prior_mean ? cfg->prior_mean[d] : 0.0);
     cudaMemcpy(th, th0.data(), sizeof(double) * N * D, cudaMemcpyHostToDevice);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);

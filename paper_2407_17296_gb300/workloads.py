@@ -15,7 +15,8 @@ Workloads (data seed 12345 + index):
   sv      stochastic volatility, theta = (mu, atanh phi, log sigma), D=3,
           theta* = (-1, atanh 0.95, log 0.25), T=500, N=4096, M=2048, K=20.
   lg16    LG-diag d_x=d_y=16, H=I, D=48, a* ~ U(0, 0.95), q*=0.5, r*=1.0,
-          T=200, N=2048, M=1024, K=30.
+          T=200, N=2048, M=1024, K=30, prior N((0.5, log 0.5, 0), (0.2, 0.3, 0.3)^2)
+          per dimension (the others use N(0, I)).
 Step sizes: Langevin 0.085*sqrt(500/T), random walk 0.175*sqrt(500/T), scaled
 from the values the paper tuned for its T=500 linear-Gaussian model.
 """
@@ -46,6 +47,8 @@ class Workload:
     gamma: float = 0.1
     seed: int = 777
     data_seed: int = 12345
+    prior_mean: Optional[np.ndarray] = None   # None: N(0, I) prior on theta
+    prior_std: Optional[np.ndarray] = None
     extra: dict = field(default_factory=dict)
 
     @property
@@ -126,8 +129,12 @@ def lg16(T=200, N=2048, M=1024, K=30, proposal="langevin") -> Workload:
     a = rng.uniform(0.0, 0.95, size=dx)
     th = np.concatenate([a, np.full(dx, np.log(0.5)), np.full(dy, np.log(1.0))])
     y = simulate_lg(rng, a, np.full(dx, 0.5), np.full(dy, 1.0), None, T)
+    # prior N(m0, diag(s0^2)) centred on stable dynamics: under N(0, I) nearly every one of
+    # the 16 transition coefficients would put some |a_k| >= 1 (explosive) in each sample
+    m0 = np.concatenate([np.full(dx, 0.5), np.full(dx, np.log(0.5)), np.zeros(dy)])
+    s0 = np.concatenate([np.full(dx, 0.2), np.full(dx, 0.3), np.full(dy, 0.3)])
     return Workload("lg16", LG_DIAG, dx, dy, 3 * dx, T, N, M, K, th, y, None, proposal,
-                    step_sizes(T)[proposal], 780, seed)
+                    step_sizes(T)[proposal], 780, seed, prior_mean=m0, prior_std=s0)
 
 
 ALL = {"lg1": lg1, "lg4": lg4, "sv": sv, "lg16": lg16}

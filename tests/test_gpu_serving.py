@@ -1,0 +1,89 @@
+"""Continuous-batching server: jobs of different model families and sizes submitted
+together overlap on the GPU, and each job's result is the same as when it runs alone
+(every kernel is deterministic and each job has its own stream and state)."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2407_17296_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _jobs():
+    return [W.lg1(T=50, N=64, M=128, K=3), W.lg4(T=40, N=32, M=256, K=3),
+            W.sv(T=60, N=48, M=128, K=4), W.lg16(T=20, N=16, M=128, K=2),
+            W.lg4(T=30, N=64, M=100, K=2, proposal="rw")]
+
+
+def _alone(w):
+    from paper_2407_17296_gb300 import binding
+    with binding.Handle(binding.config_for(w)) as h:
+        st = None
+        for _ in range(w.K):
+            st = h.step()
+        th, lw = h.samples()
+    return th, lw, st["recycled_mean"]
+
+
+def _wait(server, ids, timeout=120.0):
+    out = {}
+    t0 = time.time()
+    while len(out) < len(ids):
+        for j in ids:
+            if j not in out:
+                r = server.poll(j)
+                if r is not None:
+                    out[j] = r
+        assert time.time() - t0 < timeout, "served jobs did not finish"
+        time.sleep(0.002)
+    return out
+
+
+def test_results_alone_equal_results_in_the_mix():
+    from paper_2407_17296_gb300 import binding
+    jobs = _jobs()
+    alone = [_alone(w) for w in jobs]
+    with binding.Server(hbm_budget=8 << 30, max_active=8) as srv:
+        ids = [srv.submit(binding.config_for(w)) for w in jobs]
+        res = _wait(srv, ids)
+    for w, j, (th, lw, rec) in zip(jobs, ids, alone):
+        r = res[j]
+        assert r["status"] == 0 and r["K"] == w.K
+        np.testing.assert_array_equal(r["theta"], th)
+        np.testing.assert_array_equal(r["logw"], lw)
+        np.testing.assert_array_equal(r["recycled_mean"], rec)
+        assert r["latency_s"] >= r["queue_s"] >= 0.0
+
+
+def test_admission_by_footprint_and_rejection():
+    from paper_2407_17296_gb300 import binding
+    small = W.lg4(T=40, N=32, M=256, K=2)
+    cfg = binding.config_for(small)
+    fp = binding.footprint(cfg)
+    # room for one job at a time: the second waits until the first frees its memory
+    with binding.Server(hbm_budget=int(fp * 1.5), max_active=8) as srv:
+        ids = [srv.submit(binding.config_for(small)) for _ in range(3)]
+        res = _wait(srv, ids)
+        assert all(res[j]["status"] == 0 for j in ids)
+        # the second job was admitted only after the first one finished
+        first, second = res[ids[0]], res[ids[1]]
+        assert second["queue_s"] >= 0.5 * (first["latency_s"] - first["queue_s"])
+        big = binding.config_for(W.lg4(T=40, N=1024, M=1024, K=1))
+        with pytest.raises(binding.Smc2Error, match="NOMEM"):
+            srv.submit(big)
+
+
+def test_cancel_and_unknown_ids():
+    from paper_2407_17296_gb300 import binding
+    w = W.lg4(T=40, N=32, M=256, K=50)
+    with binding.Server(hbm_budget=1 << 30, max_active=1) as srv:
+        a = srv.submit(binding.config_for(w))
+        b = srv.submit(binding.config_for(w))
+        srv.cancel(b)  # still queued behind a
+        with pytest.raises(binding.Smc2Error, match="NOTFOUND"):
+            srv.poll(b)
+        srv.cancel(a)
+        with pytest.raises(binding.Smc2Error):
+            srv.poll(12345)

@@ -96,6 +96,7 @@ def test_smc2_lg16_small_matches_oracle():
     w = W.lg16(T=25, N=16, M=128, K=3)
     recs, hints = _run_gpu(w, w.K)
     ref, _ = osmc2.run(w.family, 16, 16, None, w.y, w.N, w.M, w.K, w.gamma, "langevin", w.seed,
+                       prior_mean=w.prior_mean, prior_std=w.prior_std,
                        hints=hints, band=BAND, flag_band=BAND, band_rel=BAND_REL)
     _compare(recs, ref, stable=_stable_lg(16))
 
