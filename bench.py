@@ -33,7 +33,7 @@ UNIT = "particle-steps/s"
 
 # Algorithmic FP32/INT32 lane-operations per particle-step (forward + adjoint), counted
 # from the algorithm at source level for each model shape ("Roofline").
-ALG_OPS = {"lg1": 60 + 24, "lg4": 94 + 47, "sv": 64 + 30, "lg16": 4 * 84 + 16 * 25 + 16 * 12}
+ALG_OPS = {"lg1": 33 + 14, "lg4": 94 + 47, "sv": 36 + 15, "lg16": 333 + 154}
 
 
 def _args():

@@ -77,13 +77,14 @@ def systematic_ancestors(logw, nu, hint=None, band=1e-6):
 
 def run(family, dx, dy, H, y, N, M, K, gamma, proposal, seed, prior_mean=None, prior_std=None,
         scheme=SYSTEMATIC, ess_frac=0.5, hints=None, band=1e-6, flag_band=1e-6,
-        outer_band=1e-4, D=None, loglik_grad_fn=None, band_rel=0.0):
+        outer_band=1e-4, D=None, loglik_grad_fn=None, band_rel=0.0, outer_flag_band=1e-3):
     """Run K iterations; returns (list of per-iteration records, recycled mean).
 
     proposal: "rw" (SMC0) or "langevin" (SMC1).
     hints: optional list, per iteration, of dicts with keys pf_anc (N,T,M), pf_flag (N,T),
       outer_anc (N,), outer_flag (bool): decisions taken elsewhere, followed at near-ties
-      (PF level: |c - tau| < band; outer level: |c - tau| < outer_band).
+      (PF level: |c - tau| < band; outer level: |c - tau| < outer_band, and the resampling
+      decision when |ESS/(N/2) - 1| < outer_flag_band).
     loglik_grad_fn: optional theta -> (log p, grad) used in place of the particle filter
       (e.g. the exact Kalman likelihood, to test the sampler on its own).
     """
@@ -165,7 +166,8 @@ def run(family, dx, dy, H, y, N, M, K, gamma, proposal, seed, prior_mean=None, p
         own_flag = ess < N / 2.0
         flag = own_flag
         if hint is not None and "outer_flag" in hint and bool(hint["outer_flag"]) != own_flag:
-            rec["outer_stats"]["flag_disagree"] = 1
+            near = abs(ess / (N / 2.0) - 1.0) < outer_flag_band
+            rec["outer_stats"]["flag_tie" if near else "flag_disagree"] = 1
             flag = bool(hint["outer_flag"])
         if flag:
             nu = _uniform_open(seed, k, 0, 0, STREAM_OUTER_NU)
