@@ -211,6 +211,8 @@ def run_gpu(a, rank, world, local):
 
     # dominant kernels (filter forward + adjoint): pf_loglik_grad on the same stream and inputs
     theta, _ = h.samples()
+    ll_state, _ = h.state()
+    dead = int(np.sum(~np.isfinite(ll_state)))  # filters that ended early (weights vanished)
     th = torch.tensor(theta, dtype=torch.float64, device=dev)
     ll = torch.empty(w.N, dtype=torch.float64, device=dev)
     g = torch.empty(w.N, w.D, dtype=torch.float64, device=dev)
@@ -287,6 +289,7 @@ def run_gpu(a, rank, world, local):
                    "launch": {"forward_ppt": launch[0], "forward_regs": launch[1], "adjoint_ppt": launch[2],
                               "adjoint_regs": launch[3], "ckpt_every": launch[4]},
                    "step": "one SMC2 iteration: propose, N filters fwd+adjoint, L-kernel weights, resample",
+                   "dead_samples": dead,
                    "l2": "inputs larger than L2 (particle trajectory of several GB written and read per step)",
                    "parallelism": f"replicas x{world} (independent jobs)"},
         "smc2_iters_per_s": 1e3 / ms_step,

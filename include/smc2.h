@@ -178,6 +178,12 @@ int smc2_get_trace(smc2_handle* h, uint16_t* pf_anc, uint8_t* pf_flag, int32_t* 
 int pf_loglik_grad_static(const smc2_config* cfg, const double* theta_dev, int n, uint32_t iter,
                           uint32_t row0, double* loglik_dev, double* grad_dev);
 
+/* Read the handle's device status word (synchronises its stream): 0, or kernel error bits
+ * (1: a bounded wait inside a filter kernel expired; that launch's results are invalid).
+ * clear != 0 resets it.  smc2_step and pf_loglik_grad_host report a set status as
+ * SMC2_E_TIMEOUT. */
+int smc2_get_status(smc2_handle* h, int* status, int clear);
+
 /* Replace the observations (T x d_y FP32, host) of an existing handle; the copy is
  * stream-ordered on the handle's stream. */
 int smc2_set_observations(smc2_handle* h, const float* y_host);

@@ -23,7 +23,7 @@ SYSTEMATIC, MULTINOMIAL = 0, 1
 EXPORTS = ("smc2_config_init", "smc2_create", "pf_loglik_grad", "pf_loglik_grad_rows",
            "pf_loglik_grad_host", "smc2_step", "smc2_get_samples", "smc2_get_state",
            "smc2_get_trace", "smc2_set_observations", "smc2_footprint", "smc2_destroy",
-           "smc2_autotune", "smc2_get_launch", "smc2_kernel_launches", "smc2_last_error", "smc2_server_create",
+           "smc2_autotune", "smc2_get_launch", "smc2_get_status", "smc2_kernel_launches", "smc2_last_error", "smc2_server_create",
            "smc2_submit", "smc2_poll", "smc2_cancel", "smc2_server_destroy",
            "pf_loglik_grad_static")
 
@@ -111,6 +111,7 @@ def load(path: str = LIB_PATH):
         "smc2_autotune": (ctypes.c_int, [ctypes.POINTER(Config), dp, ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int)]),
         "smc2_get_launch": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int)]),
+        "smc2_get_status": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
         "smc2_kernel_launches": (u64, []),
         "smc2_last_error": (ctypes.c_char_p, []),
         "smc2_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(vp)]),
@@ -273,6 +274,12 @@ class Handle:
         check(self.lib.smc2_get_trace(self.h, _ptr(anc), _ptr(flag), _ptr(oanc), ctypes.byref(ores)),
               "smc2_get_trace")
         return anc, flag, oanc, bool(ores.value)
+
+    def status(self, clear=False):
+        """Device status word of the handle's kernels (0 = fine)."""
+        st = ctypes.c_int(0)
+        check(self.lib.smc2_get_status(self.h, ctypes.byref(st), int(bool(clear))), "smc2_get_status")
+        return st.value
 
     def launch(self):
         """(forward particles/thread, forward register cap, adjoint particles/thread,

@@ -195,11 +195,11 @@ int smc2::validate(const smc2_config* c, int* D) {
 }
 
 void smc2::plan_sizes(const smc2_config* c, int D, int kc, Sizes* s) {
-    const size_t N = c->N, M = c->M, T = c->T, DX = c->d_x;
+    const size_t N = c->N, M = c->M, T = c->T, DX = c->d_x, Mp = padded_particles(c->M);
     s->n_slots = (kc == 1) ? (int)(T + 1) : (int)((T + kc - 1) / kc);
-    s->xck = N * s->n_slots * M * DX * sizeof(float);
+    s->xck = N * s->n_slots * Mp * DX * sizeof(float) + 256;
     s->lwck = N * s->n_slots * M * sizeof(float);
-    s->xseg = (kc > 1) ? N * kc * M * DX * sizeof(float) : 0;
+    s->xseg = (kc > 1) ? N * kc * Mp * DX * sizeof(float) + 256 : 0;
     s->lwseg = (kc > 1) ? N * kc * M * sizeof(float) : 0;
     s->anc = N * T * M * sizeof(uint16_t);
     s->flag = N * T;
@@ -226,10 +226,11 @@ extern "C" int smc2_footprint(const smc2_config* cfg, size_t* bytes) {
 static void free_handle_memory(smc2_handle* h) {
     void* ptrs[] = {h->y, h->H, h->prior_m, h->prior_s, h->theta, h->theta_new, h->logw, h->logpi,
                     h->gradpi, h->loglik, h->ll_new, h->grad_new, h->tmp, h->stats, h->outer_anc,
-                    h->k_dev, h->xck, h->lwck, h->xseg, h->lwseg, h->anc, h->flag, h->mstep, h->lstep};
+                    h->k_dev, h->status, h->xck, h->lwck, h->xseg, h->lwseg, h->anc, h->flag, h->mstep, h->lstep};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_stats) cudaFreeHost(h->h_stats);
+    if (h->h_status) cudaFreeHost(h->h_status);
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
@@ -290,6 +291,7 @@ extern "C" int smc2_create(const smc2_config* cfg, smc2_handle** out) {
         {(void**)&h->stats, sizeof(double) * (kStatsHead + 2 * D)},
         {(void**)&h->outer_anc, sizeof(int) * N},
         {(void**)&h->k_dev, sizeof(uint32_t)},
+        {(void**)&h->status, sizeof(int)},
         {(void**)&h->xck, s.xck},
         {(void**)&h->lwck, s.lwck},
         {(void**)&h->xseg, s.xseg},
@@ -308,7 +310,8 @@ extern "C" int smc2_create(const smc2_config* cfg, smc2_handle** out) {
                            std::string("cudaMalloc: ") + cudaGetErrorString(e));
         }
     }
-    if (cudaMallocHost((void**)&h->h_stats, sizeof(double) * (kStatsHead + 2 * D)) != cudaSuccess)
+    if (cudaMallocHost((void**)&h->h_stats, sizeof(double) * (kStatsHead + 2 * D)) != cudaSuccess ||
+        cudaMallocHost((void**)&h->h_status, sizeof(int)) != cudaSuccess)
         return cleanup(SMC2_E_NOMEM, "cudaMallocHost failed");
     // inputs
     const cudaMemcpyKind ykind = cfg->y_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -328,6 +331,7 @@ extern "C" int smc2_create(const smc2_config* cfg, smc2_handle** out) {
         ok = ok && cudaMemcpy(h->prior_s, ps, sizeof(double) * D, cudaMemcpyHostToDevice) == cudaSuccess;
     }
     ok = ok && cudaMemsetAsync(h->k_dev, 0, sizeof(uint32_t), h->stream) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(h->status, 0, sizeof(int), h->stream) == cudaSuccess;
     ok = ok && cudaMemsetAsync(h->stats, 0, sizeof(double) * (kStatsHead + 2 * D), h->stream) == cudaSuccess;
     ok = ok && cudaMemsetAsync(h->gradpi, 0, sizeof(double) * N * D, h->stream) == cudaSuccess;
     ok = ok && cudaMemsetAsync(h->flag, 0, s.flag, h->stream) == cudaSuccess;
@@ -387,6 +391,7 @@ PFArgs smc2::make_pf_args(smc2_handle* h, const double* theta, int n, uint32_t i
     a.lstep = h->lstep;
     a.loglik = loglik;
     a.grad = grad;
+    a.status = h->status;
     return a;
 }
 
@@ -428,6 +433,18 @@ extern "C" int pf_loglik_grad_host(smc2_handle* h, const double* theta_host, int
     if (grad_host)
         CUDA_TRY(cudaMemcpyAsync(grad_host, h->grad_new, sizeof(double) * n * D, cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(cudaStreamSynchronize(h->stream));
+    int st = 0;
+    int rc2 = read_status(h, &st);
+    if (rc2) return rc2;
+    if (st) return fail(SMC2_E_TIMEOUT, "a bounded wait in a device kernel expired");
+    return SMC2_OK;
+}
+
+extern "C" int smc2_get_status(smc2_handle* h, int* status, int clear) {
+    if (!h || !status) return fail(SMC2_E_INVAL, "NULL argument");
+    int rc = read_status(h, status);
+    if (rc) return rc;
+    if (clear && *status) CUDA_TRY(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
     return SMC2_OK;
 }
 
@@ -504,11 +521,20 @@ int smc2::step_async(smc2_handle* h) {
     return SMC2_OK;
 }
 
+int smc2::read_status(smc2_handle* h, int* status) {
+    CUDA_TRY(cudaMemcpyAsync(h->h_status, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    *status = *h->h_status;
+    return SMC2_OK;
+}
+
 int smc2::read_stats(smc2_handle* h, smc2_stats* out) {
     const int D = h->D;
     CUDA_TRY(cudaMemcpyAsync(h->h_stats, h->stats, sizeof(double) * (kStatsHead + 2 * D), cudaMemcpyDeviceToHost,
                              h->stream));
+    CUDA_TRY(cudaMemcpyAsync(h->h_status, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (*h->h_status) return fail(SMC2_E_TIMEOUT, "a bounded wait in a device kernel expired");
     if (!out) return SMC2_OK;
     const double* s = h->h_stats;
     out->k = (int32_t)s[kStK];

@@ -26,9 +26,9 @@ struct PFArgs {
     // adjoint storage (see the trajectory layout in pf_kernels.cuh)
     int kc;                 // checkpoint interval; 1 = every step is stored
     int n_slots;            // checkpoint slots per filter
-    float* xck;             // [n][n_slots][M][DX]
+    float* xck;             // [n][n_slots][Mp][DX], Mp = M rounded up to a multiple of 4
     float* lwck;            // [n][n_slots][M]
-    float* xseg;            // [n][kc][M][DX]   (kc > 1)
+    float* xseg;            // [n][kc][Mp][DX]  (kc > 1)
     float* lwseg;           // [n][kc][M]       (kc > 1)
     uint16_t* anc;          // [n][T][M] ancestor tape (row t-1: before step t)
     uint8_t* flag;          // [n][T]   1 if the filter resampled before step t
@@ -37,11 +37,22 @@ struct PFArgs {
     // outputs
     double* loglik;         // [n]
     double* grad;           // [n][D]
+    int* status;            // device status word: bit kStatusTimeout when a bounded wait expired
 };
+
+// Particle rows of stored state slices are padded to a multiple of 4 so that every slice
+// starts on a 16-byte boundary (bulk asynchronous copies need it).
+SMC2_HD inline int padded_particles(int M) { return (M + 3) & ~3; }
+
+// Slots of the adjoint's shared-memory ring of trajectory slices.
+SMC2_HD inline int ring_slots(int DX) { return DX >= 16 ? 2 : 4; }
 
 // Dynamic shared-memory plan (mirrored on the host to size the launch).
 struct SmemLayout {
-    size_t xstage, xbstage, cs, marks, starts, red, scanw, scanwi, dred, total;
+    size_t xstage, xbstage, cs, marks, starts, red, scanw, scanwi, dred, bars, total;
+    // fwd: xstage is the gather staging; bwd: xstage is the ring of trajectory slices
+    // (ring_slots(DX) slots of padded_particles(M) * DX floats), whose first slot also
+    // serves as staging during segment recomputation
     SMC2_HD SmemLayout(int M, int DX, int D, bool fwd, int G = 1) {
         size_t o = 0;
         auto take = [&](size_t bytes) {
@@ -49,7 +60,9 @@ struct SmemLayout {
             o += (bytes + 15) & ~size_t(15);
             return r;
         };
-        xstage = take(sizeof(float) * (size_t)M * DX);
+        const int Mp = (M + 3) & ~3;
+        xstage = fwd ? take(sizeof(float) * (size_t)M * DX)
+                     : take(sizeof(float) * (size_t)Mp * DX * (DX >= 16 ? 2 : 4));
         xbstage = fwd ? o : take(sizeof(float) * (size_t)M * DX);
         cs = fwd ? take(sizeof(float) * (size_t)M) : o;
         marks = take(sizeof(uint16_t) * (size_t)M);      // fwd: range marks; bwd: tape row
@@ -58,6 +71,7 @@ struct SmemLayout {
         scanw = take(sizeof(unsigned long long) * 32);
         scanwi = take(sizeof(int) * 32);
         dred = fwd ? o : take(sizeof(double) * (size_t)D * 32);
+        bars = fwd ? o : take(sizeof(unsigned long long) * 2 * (DX >= 16 ? 2 : 4));
         total = o;
     }
 };

@@ -42,6 +42,7 @@
 #include "models.cuh"
 #include "pf_args.h"
 #include "philox.cuh"
+#include "ring.cuh"
 
 namespace smc2 {
 
@@ -481,12 +482,13 @@ __device__ __forceinline__ float group_sum(float v) {
 }
 
 struct Traj {
-    // slot addressing of the stored trajectory of filter f
+    // slot addressing of the stored trajectory of filter f (state slices padded to Mp rows)
     const PFArgs& a;
     int f, DX;
-    __device__ float* x_ck(int slot) const { return a.xck + ((size_t)f * a.n_slots + slot) * a.M * DX; }
+    __device__ size_t xs() const { return (size_t)padded_particles(a.M) * DX; }
+    __device__ float* x_ck(int slot) const { return a.xck + ((size_t)f * a.n_slots + slot) * xs(); }
     __device__ float* lw_ck(int slot) const { return a.lwck + ((size_t)f * a.n_slots + slot) * a.M; }
-    __device__ float* x_seg(int r) const { return a.xseg + ((size_t)f * a.kc + r) * a.M * DX; }
+    __device__ float* x_seg(int r) const { return a.xseg + ((size_t)f * a.kc + r) * xs(); }
     __device__ float* lw_seg(int r) const { return a.lwseg + ((size_t)f * a.kc + r) * a.M; }
 };
 
@@ -603,9 +605,9 @@ __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, cons
 
 // ---------------------------------------------------------------- adjoint pass
 
-template <class Mdl, int P>
+template <class Mdl, int P, int R>
 __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, const SmemLayout& L,
-                                typename Mdl::Params& sprm) {
+                                typename Mdl::Params& sprm, SliceRing<R>& ring, uint32_t& g) {
     constexpr int DX = Mdl::DX, DY = Mdl::DY, D = Mdl::D, G = Mdl::G, DL = Mdl::DL, DTH = Mdl::DTH;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     const int gl = (G > 1) ? (tid & (G - 1)) : 0;
@@ -643,9 +645,10 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
     for (int d = 0; d < DTH; ++d) thb[d] = 0.f;
 
     // With kc = 1 the whole run is one segment whose every step is a checkpoint slot.
+    // The sweep over a segment reads the state slices X(t1), X(t1-1), ..., X(t0) from the
+    // shared-memory ring, R slices ahead of use; slice g+k holds x_{t1-k}.
     const int S = (kc == 1) ? 1 : (T + kc - 1) / kc;
-    float xt[P][DL];  // states x_t of the step being reversed (carried from the previous iteration)
-    float xn[P][DL];  // states x_{t-1}, loaded one iteration ahead
+    const int Mp = padded_particles(M);
     for (int s = S - 1; s >= 0; --s) {
         const int t0 = (kc == 1) ? 0 : s * kc;
         const int t1 = (kc == 1) ? T : min(t0 + kc, T);
@@ -690,16 +693,30 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
                 store_state<P, DX, DL>(tr.x_seg(t - t0 - 1), tr.lw_seg(t - t0 - 1), j0, gl, M, x, lw);
             }
         }
+        // the recomputed slices (global, generic proxy) and the staging slot (shared) must be
+        // ordered before the bulk copies that refill the ring
+        __syncthreads();
+        const int Ls = t1 - t0 + 1;
+        if (tid == 0) {
+            fence_proxy_async();
+            for (int k = 0; k < R && k < Ls; ++k) ring.produce(g + k, Xp(t1 - k), a.status);
+        }
+        ring.acquire(g, a.status);
         if (s == S - 1) {
             // cotangent of log w_T: normalised final weights (Eq. dloglik)
             const float* lwT = LWp(T);
             const float LT = lstep[T];
 #pragma unroll
             for (int p = 0; p < P; ++p) lwbar[p] = (j0 + p < M) ? __expf(lwT[j0 + p] - LT) : 0.f;
-            load_x<P, DX, DL>(Xp(T), j0, gl, M, xt);
         }
-        load_x<P, DX, DL>(Xp(t1 - 1), j0, gl, M, xn);
-        for (int t = t1; t > t0; --t) {
+        for (int k = 0; k < Ls - 1; ++k) {
+            const int t = t1 - k;
+            ring.acquire(g + k + 1, a.status);
+            const float* st = ring.slot(g + k);      // x_t
+            const float* sp = ring.slot(g + k + 1);  // x_{t-1}
+            float xt[P][DL];
+#pragma unroll
+            for (int p = 0; p < P; ++p) read_staged<DX, DL>(st, min(j0 + p, M - 1), gl, xt[p]);
             const float* yt = a.y + (size_t)(t - 1) * DY + (G > 1 ? gl * DL : 0);
 #pragma unroll
             for (int p = 0; p < P; ++p)
@@ -708,33 +725,26 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
             float xp[P][DL];
             int ai[P];
             if (fl) {
-                stage_x<P, DX, DL>(xstage, j0, gl, M, xn);
                 const uint16_t* row = a.anc + ((size_t)f * T + (t - 1)) * M;
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
                     ai[p] = (j0 + p < M) ? (int)row[j0 + p] : 0;
                     if (lead && j0 + p < M) ancs[j0 + p] = (uint16_t)ai[p];
                 }
-                __syncthreads();
-#pragma unroll
-                for (int p = 0; p < P; ++p) read_staged<DX, DL>(xstage, ai[p], gl, xp[p]);
             } else {
 #pragma unroll
-                for (int p = 0; p < P; ++p)
-#pragma unroll
-                    for (int k = 0; k < DL; ++k) xp[p][k] = xn[p][k];
+                for (int p = 0; p < P; ++p) ai[p] = min(j0 + p, M - 1);
             }
+#pragma unroll
+            for (int p = 0; p < P; ++p) read_staged<DX, DL>(sp, ai[p], gl, xp[p]);
 #pragma unroll
             for (int p = 0; p < P; ++p)
                 if (j0 + p < M) Mdl::bwd_trans(prm, xt[p], xp[p], xbar[p], thb);
-            // x_{t-1} is the state of the next iteration; start loading x_{t-2} now so the
-            // load overlaps the rest of this step
-#pragma unroll
-            for (int p = 0; p < P; ++p)
-#pragma unroll
-                for (int k = 0; k < DL; ++k) xt[p][k] = xn[p][k];
-            if (t - 2 >= t0) load_x<P, DX, DL>(Xp(t - 2), j0, gl, M, xn);
+            // x_t is no longer needed: free its slot and refill it R slices ahead
+            ring.release(g + k);
+            if (tid == 0 && k + R < Ls) ring.produce(g + k + R, Xp(t1 - k - R), a.status);
             if (fl) {
+                __syncthreads();  // the tape row in ancs is complete
                 // adjoint of the gather x'_i = x_{a_i}: sum the cotangents of each parent's offspring
                 if (a.scheme == 0) {
                     gather_adjoint_sorted<P, DX, DL, G>(xbar, ai, j0, gl, M, ancs, xbstage, segw);
@@ -743,14 +753,14 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
                     for (int p = 0; p < P; ++p)
                         if (j0 + p < M)
 #pragma unroll
-                            for (int k = 0; k < DL; ++k) xbstage[(j0 + p) * DX + gl * DL + k] = 0.f;
+                            for (int kk = 0; kk < DL; ++kk) xbstage[(j0 + p) * DX + gl * DL + kk] = 0.f;
                     __syncthreads();
 #pragma unroll
                     for (int p = 0; p < P; ++p)
                         if (j0 + p < M)
 #pragma unroll
-                            for (int k = 0; k < DL; ++k)
-                                atomicAdd(&xbstage[ai[p] * DX + gl * DL + k], xbar[p][k]);
+                            for (int kk = 0; kk < DL; ++kk)
+                                atomicAdd(&xbstage[ai[p] * DX + gl * DL + kk], xbar[p][kk]);
                     __syncthreads();
 #pragma unroll
                     for (int p = 0; p < P; ++p)
@@ -764,11 +774,19 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
                 __syncthreads();
             }
         }
-    }
-    // t = 0: the initial states are in xt
+        if (s == 0) {
+            // t = 0: the initial states are the segment's last slice
+            const float* s0 = ring.slot(g + Ls - 1);
 #pragma unroll
-    for (int p = 0; p < P; ++p)
-        if (j0 + p < M) Mdl::bwd_init(prm, xt[p], xbar[p], thb);
+            for (int p = 0; p < P; ++p) {
+                float x0[DL];
+                read_staged<DX, DL>(s0, min(j0 + p, M - 1), gl, x0);
+                if (j0 + p < M) Mdl::bwd_init(prm, x0, xbar[p], thb);
+            }
+        }
+        ring.release(g + Ls - 1);
+        g += Ls;
+    }
     // gradient: FP64 block sum of the per-thread FP32 partials (lanes of equal gl hold the
     // same parameters; Mdl::theta_index maps a lane's partial to its parameter)
 #pragma unroll
@@ -792,7 +810,7 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
 // a launch is valid while threads * REGS <= 65536 (threads <= kMaxThreads).
 template <class Mdl, int P, int REGS>
 __global__ void __maxnreg__(REGS) pf_forward_kernel(PFArgs a) {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     __shared__ typename Mdl::Params sprm;
     const SmemLayout L(a.M, Mdl::DX, Mdl::D, true, Mdl::G);
     for (int f = blockIdx.x; f < a.n; f += gridDim.x) {
@@ -803,11 +821,27 @@ __global__ void __maxnreg__(REGS) pf_forward_kernel(PFArgs a) {
 
 template <class Mdl, int P, int REGS>
 __global__ void __maxnreg__(REGS) pf_backward_kernel(PFArgs a) {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     __shared__ typename Mdl::Params sprm;
+    constexpr int R = Mdl::DX >= 16 ? 2 : 4;  // ring_slots(DX)
     const SmemLayout L(a.M, Mdl::DX, Mdl::D, false, Mdl::G);
+    SliceRing<R> ring;
+    ring.slots = reinterpret_cast<float*>(smem + L.xstage);
+    ring.full = reinterpret_cast<uint64_t*>(smem + L.bars);
+    ring.empty = ring.full + R;
+    ring.slice_floats = padded_particles(a.M) * Mdl::DX;
+    ring.bytes = (uint32_t)(sizeof(float) * ring.slice_floats);
+    if (threadIdx.x == 0) {
+        for (int r = 0; r < R; ++r) {
+            mbar_init(&ring.full[r], 1);
+            mbar_init(&ring.empty[r], blockDim.x >> 5);
+        }
+        mbar_fence_init();
+    }
+    __syncthreads();
+    uint32_t g = 0;
     for (int f = blockIdx.x; f < a.n; f += gridDim.x) {
-        backward_filter<Mdl, P>(a, f, smem, L, sprm);
+        backward_filter<Mdl, P, R>(a, f, smem, L, sprm, ring, g);
         __syncthreads();
     }
 }

@@ -52,7 +52,7 @@ size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 // Scratch bytes for n filters at checkpoint interval kc (H copy + trajectory + tape + steps).
 size_t static_need(const smc2_config& c, int D, int kc, Sizes* s) {
     plan_sizes(&c, D, kc, s);
-    return align256(sizeof(float) * 256) + align256(s->xck) + align256(s->lwck) + align256(s->xseg) +
+    return align256(sizeof(float) * 256) + align256(sizeof(int)) + align256(s->xck) + align256(s->lwck) + align256(s->xseg) +
            align256(s->lwseg) + align256(s->anc) + align256(s->flag) + 2 * align256(s->steps / 2);
 }
 
@@ -108,6 +108,7 @@ extern "C" int pf_loglik_grad_static(const smc2_config* cfg, const double* theta
         return r;
     };
     float* Hs = reinterpret_cast<float*>(take(sizeof(float) * 256));
+    int* status = reinterpret_cast<int*>(take(sizeof(int)));
     PFArgs a{};
     a.theta = theta_dev;
     a.y = cfg->y;
@@ -141,9 +142,12 @@ extern "C" int pf_loglik_grad_static(const smc2_config* cfg, const double* theta
     a.lstep = reinterpret_cast<float*>(take(s.steps / 2));
     a.loglik = loglik_dev;
     a.grad = grad_dev;
-    // every scratch region is written before it is read within this call: the forward pass
-    // writes the flags and per-step scalars of every step it runs, the tape rows of every
-    // resampling step and every checkpoint slot; nothing has to start at zero.
+    a.status = status;
+    if (cudaMemsetAsync(status, 0, sizeof(int), stream) != cudaSuccess)
+        return fail(SMC2_E_CUDA, "clearing the status word failed");
+    // every other scratch region is written before it is read within this call: the forward
+    // pass writes the flags and per-step scalars of every step it runs, the tape rows of
+    // every resampling step and every checkpoint slot; only the status word starts at zero.
     int lrc = fwd(a, stream, n);
     if (!lrc && a.want_grad) lrc = bwd(a, stream, n);
     if (lrc) return fail(SMC2_E_CUDA, std::string("filter launch failed: ") + cudaGetErrorString(cudaGetLastError()));

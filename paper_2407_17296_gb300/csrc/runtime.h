@@ -50,6 +50,8 @@ struct smc2_handle {
     double *loglik = nullptr, *ll_new = nullptr, *grad_new = nullptr, *tmp = nullptr, *stats = nullptr;
     int* outer_anc = nullptr;
     uint32_t* k_dev = nullptr;
+    int* status = nullptr;      // device status word of the handle's kernels
+    int* h_status = nullptr;    // pinned
     float *xck = nullptr, *lwck = nullptr, *xseg = nullptr, *lwseg = nullptr, *mstep = nullptr, *lstep = nullptr;
     uint16_t* anc = nullptr;
     uint8_t* flag = nullptr;
@@ -68,4 +70,5 @@ OuterArgs make_outer_args(smc2_handle* h);
 int enqueue_step(smc2_handle* h);
 int step_async(smc2_handle* h);
 int read_stats(smc2_handle* h, smc2_stats* out);
+int read_status(smc2_handle* h, int* status);
 }  // namespace smc2

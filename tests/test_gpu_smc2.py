@@ -49,7 +49,7 @@ def _compare(recs, ref, rec_ref=None, weight_floor=1e-12, stable=None):
             assert st["nontie_mismatch"] == 0 and st["flag_mismatch"] == 0, (r["k"], i, st)
             ties += st["tie_followed"] + st["tie_conditioned"]
         assert r["outer_stats"].get("nontie_mismatch", 0) == 0, r["outer_stats"]
-        assert "flag_disagree" not in r["outer_stats"]
+        assert "flag_disagree" not in r["outer_stats"], (r["k"], g["ess"], r["ess"], len(r["logw"]))
         assert g["k"] == r["k"] and g["resampled"] == r["resampled"]
         np.testing.assert_allclose(g["mean"], r["mean"], rtol=0,
                                    atol=MEAN_RTOL * max(1.0, float(np.abs(r["mean"]).max())))
@@ -93,7 +93,11 @@ def test_smc2_sv_small_matches_oracle():
 
 
 def test_smc2_lg16_small_matches_oracle():
+    from dataclasses import replace
     w = W.lg16(T=25, N=16, M=128, K=3)
+    ps = w.prior_std.copy()
+    ps[:16] = 0.1  # stable dynamics in every draw (no |a_k| >= 1 beyond 5 standard deviations)
+    w = replace(w, prior_std=ps)
     recs, hints = _run_gpu(w, w.K)
     ref, _ = osmc2.run(w.family, 16, 16, None, w.y, w.N, w.M, w.K, w.gamma, "langevin", w.seed,
                        prior_mean=w.prior_mean, prior_std=w.prior_std,
