@@ -147,10 +147,10 @@ void smc2::choose_launch(const smc2_config* c, LaunchChoice* lc) {
 
 int smc2::choose_kc(const smc2_config* c) {
     if (c->ckpt_every > 0) return c->ckpt_every;
-    // store every step while the trajectory stays within 16 GB; otherwise the interval
-    // that minimises checkpoints + segment scratch, about T/kc + kc steps (kc ~ sqrt(T))
+    // store every step while the trajectory stays within kTrajectoryBudget; otherwise the
+    // interval that minimises checkpoints + segment scratch, about T/kc + kc steps (kc ~ sqrt(T))
     const double per_step = (double)c->N * c->M * (4.0 * c->d_x + 4.0);
-    if (per_step * (c->T + 1.0) <= 16.0e9) return 1;
+    if (per_step * (c->T + 1.0) <= kTrajectoryBudget) return 1;
     int best = 2;
     double best_steps = 1e300;
     for (int kc = 2; kc <= c->T; kc *= 2) {

@@ -67,7 +67,7 @@ struct SmemLayout {
         cs = fwd ? take(sizeof(float) * (size_t)M) : o;
         marks = take(sizeof(uint16_t) * (size_t)M);      // fwd: range marks; bwd: tape row
         starts = fwd ? o : take(sizeof(float) * 32 * G * (DX / G + 1));  // segmented-scan scratch
-        red = take(sizeof(float4) * 2 * 32);
+        red = take(sizeof(float4) * (2 * 32 + 2));  // two buffers of per-warp partials + results
         scanw = take(sizeof(unsigned long long) * 32);
         scanwi = take(sizeof(int) * 32);
         dred = fwd ? o : take(sizeof(double) * (size_t)D * 32);

@@ -74,11 +74,13 @@ __device__ __forceinline__ float u64_to_float_rz(unsigned long long S) {
 }
 
 // (max, sum exp(v - max), sum exp(2 (v - max))) over all particles of the CTA.
-// Every thread returns bit-identical values (same combination order everywhere).
+// Every thread returns the same values (warp 0 combines, shared memory broadcasts).
 // A NaN log-weight anywhere turns s1 into NaN (the caller treats the filter as broken).
+// Two __syncthreads; red (32 float4) and res (1 float4) must not be reused before the
+// next barrier (callers alternate two buffers).
 template <int P>
-__device__ __forceinline__ void block_lse3(const float (&lwin)[P], bool lead, float4* red, float& m, float& s1,
-                                           float& s2) {
+__device__ __forceinline__ void block_lse3(const float (&lwin)[P], bool lead, float4* red, float4* res, float& m,
+                                           float& s1, float& s2) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     float lw[P];  // only one lane of each group counts its (replicated) particles
 #pragma unroll
@@ -105,23 +107,27 @@ __device__ __forceinline__ void block_lse3(const float (&lwin)[P], bool lead, fl
     }
     if (lane == 0) red[wid] = make_float4(mw, a1, a2, 0.f);
     __syncthreads();
-    // every warp combines the per-warp partials with the same butterfly, so all threads
-    // end with bit-identical results (the combining operations are commutative)
-    const float4 r = (lane < nw) ? red[lane] : make_float4(-INFINITY, 0.f, 0.f, 0.f);
-    float M_ = r.x;
+    // warp 0 combines the per-warp partials and broadcasts (max, s1, s2) through res
+    if (wid == 0) {
+        const float4 r = (lane < nw) ? red[lane] : make_float4(-INFINITY, 0.f, 0.f, 0.f);
+        float M_ = r.x;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) M_ = fmaxf(M_, __shfl_xor_sync(kFull, M_, o));
-    const bool bad = __any_sync(kFull, isnan(r.x) || isnan(r.y));  // a warp of NaNs has a NaN maximum
-    const float e = (r.x > -INFINITY) ? __expf(r.x - M_) : 0.f;
-    float S1 = r.y * e, S2 = r.z * e * e;
+        for (int o = 16; o > 0; o >>= 1) M_ = fmaxf(M_, __shfl_xor_sync(kFull, M_, o));
+        const bool bad = __any_sync(kFull, isnan(r.x) || isnan(r.y));  // a warp of NaNs has a NaN maximum
+        const float e = (r.x > -INFINITY) ? __expf(r.x - M_) : 0.f;
+        float S1 = r.y * e, S2 = r.z * e * e;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        S1 += __shfl_xor_sync(kFull, S1, o);
-        S2 += __shfl_xor_sync(kFull, S2, o);
+        for (int o = 16; o > 0; o >>= 1) {
+            S1 += __shfl_xor_sync(kFull, S1, o);
+            S2 += __shfl_xor_sync(kFull, S2, o);
+        }
+        if (lane == 0) *res = make_float4(M_, bad ? __int_as_float(0x7fc00000) : S1, S2, 0.f);
     }
-    m = M_;
-    s1 = bad ? __int_as_float(0x7fc00000) : S1;
-    s2 = S2;
+    __syncthreads();
+    const float4 out = *res;
+    m = out.x;
+    s1 = out.y;
+    s2 = out.z;
 }
 
 // Exact inclusive prefix sums S_j of the fixed-point weights round(w_j * 2^40) over the
@@ -225,7 +231,7 @@ __device__ __forceinline__ void systematic_ancestors(const float (&lw)[P], bool 
 // a_i = min{j : c_j >= nu_i} by binary search over the cumulative weights.  Two __syncthreads.
 template <int P, int G>
 __device__ __forceinline__ void multinomial_ancestors(const float (&lw)[P], bool lead, int j0, int M,
-                                                      PhiloxKey key, uint32_t t, float* cs,
+                                                      const PhiloxKey& key, uint32_t t, float* cs,
                                                       unsigned long long* scanw, int (&anc)[P]) {
     unsigned long long s[P], base, tot;
     block_fixed_scan<P, G>(lw, lead, j0, M, scanw, s, base, tot);
@@ -461,7 +467,7 @@ __device__ __forceinline__ void read_staged(const float* xstage, int j, int gl, 
 
 // Normals of the lane's dimensions of its P particles: normal index n = j*DX + k.
 template <int P, int DX, int DL>
-__device__ __forceinline__ void draw_normals(PhiloxKey key, uint32_t t, uint32_t stream, int j0, int gl,
+__device__ __forceinline__ void draw_normals(const PhiloxKey& key, uint32_t t, uint32_t stream, int j0, int gl,
                                              float (&eps)[P * DL]) {
     if constexpr (DL == DX) {
         normals<P * DX>(key, t, stream, (uint32_t)(j0 * DX), eps);
@@ -529,8 +535,16 @@ __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, cons
             lw[p] = (j0 + p < M) ? 0.f : -INFINITY;
         }
     }
-    float Lprev = logf((float)M);
-    double acc = 0.0;
+    const float logM = logf((float)M);
+    float Lprev = logM;
+    // log p-hat accumulated as a compensated (Kahan) FP32 sum of the per-step terms
+    float acc = 0.f, comp = 0.f;
+    auto kahan = [&](float v) {
+        const float y = v - comp;
+        const float tt = acc + y;
+        comp = (tt - acc) - y;
+        acc = tt;
+    };
     bool resample = false, dead = false;
     if (store) {
         store_state<P, DX, DL>(tr.x_ck(0), tr.lw_ck(0), j0, gl, M, x, lw);
@@ -560,7 +574,7 @@ __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, cons
                 if (j0 + p < M) read_staged<DX, DL>(xstage, anc[p], gl, x[p]);
                 lw[p] = (j0 + p < M) ? 0.f : -INFINITY;
             }
-            Lprev = logf((float)M);
+            Lprev = logM;
         }
         if (tid == 0 && a.flag) a.flag[(size_t)f * T + (t - 1)] = resample ? 1 : 0;
 
@@ -573,17 +587,19 @@ __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, cons
                 Mdl::transition(prm, x[p], reinterpret_cast<const float(&)[DL]>(eps[p * DL]));
                 float g = Mdl::loglik(prm, x[p], yt);
                 if constexpr (G > 1) g = group_sum<G>(g) + prm.cst;  // whole-particle log g
-                if (j0 + p < M) lw[p] += g;
+                lw[p] += g;  // padding particles stay at -inf
             }
         }
         float m, s1, s2;
-        block_lse3<P>(lw, lead, red + (t & 1) * 32, m, s1, s2);
+        block_lse3<P>(lw, lead, red + (t & 1) * 32, red + 64 + (t & 1), m, s1, s2);
         if (!(isfinite(m) && isfinite(s1) && s1 > 0.f)) {
             dead = true;
             break;
         }
         const float ls1 = logf(s1);
-        if (tid == 0) acc += ((double)m + (double)ls1) - (double)Lprev;
+        kahan(m);
+        kahan(ls1);
+        kahan(-Lprev);
 #pragma unroll
         for (int p = 0; p < P; ++p) lw[p] -= m;
         Lprev = ls1;
@@ -600,7 +616,7 @@ __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, cons
                 store_state<P, DX, DL>(tr.x_ck(t / a.kc), tr.lw_ck(t / a.kc), j0, gl, M, x, lw);
         }
     }
-    if (tid == 0) a.loglik[f] = dead ? -INFINITY : acc;
+    if (tid == 0) a.loglik[f] = dead ? -INFINITY : (double)acc - (double)comp;
 }
 
 // ---------------------------------------------------------------- adjoint pass
@@ -718,9 +734,9 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
 #pragma unroll
             for (int p = 0; p < P; ++p) read_staged<DX, DL>(st, min(j0 + p, M - 1), gl, xt[p]);
             const float* yt = a.y + (size_t)(t - 1) * DY + (G > 1 ? gl * DL : 0);
+            // padding particles have zero cotangents and finite (clamped) states: no guards
 #pragma unroll
-            for (int p = 0; p < P; ++p)
-                if (j0 + p < M) Mdl::bwd_obs(prm, xt[p], yt, lwbar[p], xbar[p], thb);
+            for (int p = 0; p < P; ++p) Mdl::bwd_obs(prm, xt[p], yt, lwbar[p], xbar[p], thb);
             const bool fl = flags[t - 1] != 0;
             float xp[P][DL];
             int ai[P];
@@ -738,8 +754,7 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
 #pragma unroll
             for (int p = 0; p < P; ++p) read_staged<DX, DL>(sp, ai[p], gl, xp[p]);
 #pragma unroll
-            for (int p = 0; p < P; ++p)
-                if (j0 + p < M) Mdl::bwd_trans(prm, xt[p], xp[p], xbar[p], thb);
+            for (int p = 0; p < P; ++p) Mdl::bwd_trans(prm, xt[p], xp[p], xbar[p], thb);
             // x_t is no longer needed: free its slot and refill it R slices ahead
             ring.release(g + k);
             if (tid == 0 && k + R < Ls) ring.produce(g + k + R, Xp(t1 - k - R), a.status);

@@ -26,43 +26,51 @@ namespace smc2 {
 enum : uint32_t { kStreamProp = 0, kStreamResample = 1, kStreamInit = 2,
                   kStreamOuterXi = 3, kStreamOuterNu = 4 };
 
-struct PhiloxKey { uint32_t k0, k1; };
+// The key with its ten round keys (the Weyl schedule k + r * W), expanded once per filter:
+// a filter draws thousands of blocks with the same key.
+struct PhiloxKey {
+    uint32_t k0[10], k1[10];
+};
 
 __host__ __device__ __forceinline__ PhiloxKey philox_key(uint32_t seed_lo, uint32_t seed_hi,
                                                          uint32_t iter, uint32_t row) {
-    return PhiloxKey{seed_lo ^ iter, seed_hi ^ row};
+    PhiloxKey k;
+    k.k0[0] = seed_lo ^ iter;
+    k.k1[0] = seed_hi ^ row;
+#pragma unroll
+    for (int r = 1; r < 10; ++r) {
+        k.k0[r] = k.k0[r - 1] + 0x9E3779B9u;
+        k.k1[r] = k.k1[r - 1] + 0xBB67AE85u;
+    }
+    return k;
 }
 
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, PhiloxKey key) {
-    uint32_t k0 = key.k0, k1 = key.k1;
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const PhiloxKey& key) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        if (r > 0) {
-            k0 += 0x9E3779B9u;
-            k1 += 0xBB67AE85u;
-        }
         const unsigned long long p0 = 0xD2511F53ull * (unsigned long long)c.x;
         const unsigned long long p1 = 0xCD9E8D57ull * (unsigned long long)c.z;
         const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
         const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        c = make_uint4(hi1 ^ c.y ^ key.k0[r], lo1, hi0 ^ c.w ^ key.k1[r], lo0);
     }
     return c;
 }
 
-// The float of an integer k in [0, 2^24], built exactly from bits (a plain int-to-float
-// conversion runs on the narrow FP64/conversion pipe of this GPU): 2^23 + (k >> 1) is
-// exact as a float with exponent 23, so ((that - 2^23) * 2 + (k & 1)) is k.
-__device__ __forceinline__ float exact_u24_to_float(uint32_t k) {
-    const float half = __uint_as_float(0x4b000000u | (k >> 1)) - 8388608.0f;
-    return fmaf(half, 2.0f, (k & 1u) ? 1.0f : 0.0f);
+// Uniforms are built from bits: a plain int-to-float conversion runs on the narrow
+// FP64/conversion pipe of this GPU.
+// k * 2^-24 for an integer k in [0, 2^24], exactly: f = 2^23 + (k >> 1) has exponent 23,
+// so f * 2^-23 - 1 + (k & 1) * 2^-24 = k * 2^-24 (one fused multiply-add, exact result).
+__device__ __forceinline__ float exact_u24_scaled(uint32_t k) {
+    const float f = __uint_as_float(0x4b000000u | (k >> 1));
+    return fmaf(f, 1.1920928955078125e-07f, (k & 1u) ? -0.99999994039535522461f : -1.0f);
 }
 
 __device__ __forceinline__ float u01_open(uint32_t u) {   // (0, 1]
-    return exact_u24_to_float((u >> 8) + 1u) * 5.9604644775390625e-08f;
+    return exact_u24_scaled((u >> 8) + 1u);
 }
 __device__ __forceinline__ float u01_half(uint32_t u) {   // [0, 1)
-    return exact_u24_to_float(u >> 8) * 5.9604644775390625e-08f;
+    return exact_u24_scaled(u >> 8);
 }
 
 // One Box-Muller pair from two words.  The angle is evaluated as
@@ -73,7 +81,7 @@ __device__ __forceinline__ float u01_half(uint32_t u) {   // [0, 1)
 __device__ __forceinline__ void box_muller(uint32_t ua, uint32_t ub, float& z0, float& z1) {
     const float s = -2.0f * logf(u01_open(ua));
     const float r = (s > 0.f) ? s * rsqrtf(s) : 0.f;
-    const float ph = 6.2831853071795864769f * (u01_half(ub) - 0.5f);
+    const float ph = fmaf(u01_half(ub), 6.2831853071795864769f, -3.1415926535897932385f);
     float sn, cs;
     __sincosf(ph, &sn, &cs);
     z0 = -r * cs;
@@ -83,7 +91,7 @@ __device__ __forceinline__ void box_muller(uint32_t ua, uint32_t ub, float& z0, 
 // Normals n0 .. n0+COUNT-1 of (key, t, stream) into out[].  n0 % 4 == 0 when
 // COUNT % 4 == 0; otherwise any n0 (the covering calls are evaluated).
 template <int COUNT>
-__device__ __forceinline__ void normals(PhiloxKey key, uint32_t t, uint32_t stream, uint32_t n0,
+__device__ __forceinline__ void normals(const PhiloxKey& key, uint32_t t, uint32_t stream, uint32_t n0,
                                         float (&out)[COUNT]) {
     if constexpr (COUNT % 4 == 0) {
 #pragma unroll

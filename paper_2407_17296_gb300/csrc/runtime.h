@@ -12,6 +12,10 @@
 
 namespace smc2 {
 
+// Device bytes a handle may spend on storing every step of the particle trajectory before
+// it switches to checkpointing with recomputation (the part holds 288 GB).
+constexpr double kTrajectoryBudget = 48.0e9;
+
 struct Sizes {
     int n_slots = 0;
     size_t xck = 0, lwck = 0, xseg = 0, lwseg = 0, anc = 0, flag = 0, steps = 0, state = 0, obs = 0, total = 0;

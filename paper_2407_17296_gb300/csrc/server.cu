@@ -415,7 +415,7 @@ extern "C" int smc2_autotune(const smc2_config* cfg, const double* theta_host, i
             smc2_config full = *cfg;
             Sizes sz;
             plan_sizes(&full, D, kc, &sz);
-            if ((double)(sz.xck + sz.lwck + sz.xseg + sz.lwseg) > 16.0e9) continue;
+            if ((double)(sz.xck + sz.lwck + sz.xseg + sz.lwseg) > kTrajectoryBudget) continue;
             smc2_handle* h = make(kc);
             if (!h) continue;
             h->lc = best;
