@@ -32,7 +32,9 @@ METRIC = "fwd+grad CRN-PF particle-steps/s"
 UNIT = "particle-steps/s"
 
 # Algorithmic FP32/INT32 lane-operations per particle-step (forward + adjoint), counted
-# from the algorithm at source level for each model shape ("Roofline").
+# from the algorithm at source level for each model shape: the Philox rounds, the uniform
+# maps, Box-Muller (each transcendental one operation), the model arithmetic, the
+# amortised reductions and resampling, and the adjoint of each.
 ALG_OPS = {"lg1": 33 + 14, "lg4": 94 + 47, "sv": 36 + 15, "lg16": 333 + 154}
 
 

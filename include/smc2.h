@@ -131,6 +131,32 @@ int pf_loglik_grad_host(smc2_handle* h, const double* theta_host, int n, uint32_
  */
 int smc2_step(smc2_handle* h, smc2_stats* out);
 
+/*
+ * One SMC^2 iteration split in two calls, for a job whose N particle filters are spread
+ * over several devices or processes (the filters of an iteration are independent: the
+ * importance-sampling and gradient rows of Table I scale with N/P; only the O(N D) outer
+ * update couples the samples).  Every participant holds a replica of the outer state
+ * (a handle created from the same cfg) and:
+ *   smc2_step_filters  proposes theta' for all N samples (Sec. III-D; the same Philox keys on
+ *                      every replica, so the proposals agree) and runs the particle filters
+ *                      of rows row0 .. row0+n-1 only, with the Philox keys of those rows,
+ *                      writing log p-hat to loglik_dev [n] and its gradient to grad_dev
+ *                      [n][D] (caller-owned device buffers, FP64).  Asynchronous on the
+ *                      handle's stream.
+ *   (the caller exchanges the rows, e.g. one all-gather, so each replica has all N)
+ *   smc2_step_update   takes loglik_all_dev [N] and grad_all_dev [N][D] (device, caller-owned,
+ *                      row i = sample i) and completes the iteration exactly as smc2_step:
+ *                      L-kernel weight, normalise, estimate, recycling statistic, ESS,
+ *                      resampling (Sec. III-A..E).  Fills *out (may be NULL); synchronises.
+ * Replicas that pass the same N rows to smc2_step_update stay identical, and equal to one
+ * handle running smc2_step.  The two calls must alternate; smc2_step_update without a
+ * preceding smc2_step_filters, or n < 0, row0 < 0, row0 + n > N, or NULL buffers with n > 0:
+ * SMC2_E_INVAL.  Launch failures: SMC2_E_CUDA.
+ */
+int smc2_step_filters(smc2_handle* h, int row0, int n, double* loglik_dev, double* grad_dev);
+int smc2_step_update(smc2_handle* h, const double* loglik_all_dev, const double* grad_all_dev,
+                     smc2_stats* out);
+
 /* Copy the current samples to host: theta_host [N][D] and logw_host [N] (either may be NULL). */
 int smc2_get_samples(smc2_handle* h, double* theta_host, double* logw_host);
 

@@ -25,7 +25,7 @@
  *     resampling (Eq. weightdiffresample and the display after it), and
  *     grad log p = sum_j w~_j dlog w_j (Eq. dloglik).
  *
- * Readings where the paper is garbled or silent (each listed in the design doc):
+ * Readings where the paper is garbled or silent:
  *   - log p-hat is the log of Eq. likelihood_pf_, i.e. LSE_j(log w_T^j) - log M
  *     with unnormalised initial weights w_0 = 1 (Eq. likelihood_pf as printed,
  *     a mean of log-weights, is not an estimate of the log-likelihood);

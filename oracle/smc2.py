@@ -10,7 +10,7 @@ One iteration k, in the order used throughout this project:
 Iteration 1 draws theta from the prior q_1 and weights by pi/q_1, i.e. by the
 estimated likelihood (Eqs. init_sample, init_weights).
 
-Readings (listed with their reasons in the design doc):
+Readings where the paper is silent or inconsistent:
   * Langevin drift F(theta) = 0.5 gamma^2 grad log pi(theta) (the definition of
     F in Sec. III-D; the later display without the 1/2 is not used);
   * L(theta_{k-1}|theta_k) = N(theta_{k-1}; theta_k + F(theta_k), gamma^2 I),
@@ -75,6 +75,86 @@ def systematic_ancestors(logw, nu, hint=None, band=1e-6):
     return a, stats
 
 
+class State:
+    """Outer-sampler state of N samples (all FP64): theta [N][D], log w, log pi-hat,
+    grad log pi, log p-hat."""
+
+    def __init__(self, N, D):
+        self.theta = np.zeros((N, D))
+        self.logw = np.zeros(N)
+        self.logpi = np.zeros(N)
+        self.gradpi = np.zeros((N, D))
+        self.loglik = np.zeros(N)
+
+
+def propose(state, k, seed, gamma, proposal, m0, s0):
+    """theta' for iteration k: a prior draw at k = 1 (Eq. init_sample), else the random-walk
+    (SMC0) or Langevin (SMC1) move of Sec. III-D with normals from Philox stream 3."""
+    N, D = state.theta.shape
+    xi = np.stack([_normals(seed, k, i, 0, STREAM_OUTER_XI, D) for i in range(N)])
+    if k == 1:
+        return m0 + s0 * xi
+    drift = 0.5 * gamma * gamma * state.gradpi if proposal == "langevin" else np.zeros_like(state.gradpi)
+    return state.theta + drift + gamma * xi
+
+
+def update(state, k, theta_new, ll_new, g_new, seed, gamma, proposal, m0, s0, hint=None,
+           outer_band=1e-4, outer_flag_band=1e-3):
+    """Complete iteration k from the filter outputs at theta_new: weight, normalise,
+    estimate, recycling statistic, ESS, resampling.  Updates state; returns the record."""
+    N = state.logw.shape[0]
+    lp_new = log_prior(theta_new, m0, s0) + ll_new
+    gp_new = grad_log_prior(theta_new, m0, s0) + g_new
+    if k == 1:
+        # w_1 = pi/q_1 = p-hat(y|theta) (Eq. init_weights)
+        logw = ll_new.copy()
+    else:
+        if proposal == "langevin":
+            drift = 0.5 * gamma * gamma * state.gradpi
+            drift_new = 0.5 * gamma * gamma * gp_new
+        else:
+            drift = np.zeros_like(state.gradpi)
+            drift_new = np.zeros_like(gp_new)
+        log_q = log_normal_iso(theta_new, state.theta + drift, gamma)     # q(theta_k | theta_{k-1})
+        log_L = log_normal_iso(state.theta, theta_new + drift_new, gamma)  # L(theta_{k-1} | theta_k)
+        logw = state.logw + lp_new - state.logpi + log_L - log_q         # Eq. l_weights
+    theta, logpi, gradpi, loglik = theta_new, lp_new, gp_new, ll_new
+
+    # normalise, estimate, recycling statistic, ESS
+    L = _lse(logw)
+    wn = np.exp(logw - L)
+    mean = wn @ theta
+    ess = 1.0 / np.sum(wn * wn)
+    l_k = np.exp(2.0 * _lse(logw) - _lse(2.0 * logw))        # (sum w)^2 / sum w^2
+    rec = {"k": k, "ess": float(ess), "l_k": float(l_k), "mean": mean.copy(),
+           "theta": theta.copy(), "logw": logw.copy(), "loglik": loglik.copy(),
+           "grad": gradpi.copy(), "resampled": False, "outer_stats": {}}
+    own_flag = ess < N / 2.0
+    flag = own_flag
+    if hint is not None and "outer_flag" in hint and bool(hint["outer_flag"]) != own_flag:
+        near = abs(ess / (N / 2.0) - 1.0) < outer_flag_band
+        rec["outer_stats"]["flag_tie" if near else "flag_disagree"] = 1
+        flag = bool(hint["outer_flag"])
+    if flag:
+        nu = _uniform_open(seed, k, 0, 0, STREAM_OUTER_NU)
+        hint_a = hint["outer_anc"] if (hint is not None and "outer_anc" in hint) else None
+        a, st = systematic_ancestors(logw, nu, hint_a, band=outer_band)
+        rec["outer_stats"].update(st)
+        rec["ancestors"] = a
+        theta, logpi, gradpi, loglik = theta[a], logpi[a], gradpi[a], loglik[a]
+        logw = np.full(N, L - np.log(N))
+        rec["resampled"] = True
+    state.theta, state.logw, state.logpi, state.gradpi, state.loglik = theta, logw, logpi, gradpi, loglik
+    return rec
+
+
+def recycled_mean(records):
+    """Sec. III-C: sum_k c_k f~_k with c_k = l_k / sum_k l_k (Eq. opt_recycling_constant)."""
+    lks = np.array([r["l_k"] for r in records])
+    ck = lks / lks.sum()
+    return sum(c * r["mean"] for c, r in zip(ck, records))
+
+
 def run(family, dx, dy, H, y, N, M, K, gamma, proposal, seed, prior_mean=None, prior_std=None,
         scheme=SYSTEMATIC, ess_frac=0.5, hints=None, band=1e-6, flag_band=1e-6,
         outer_band=1e-4, D=None, loglik_grad_fn=None, band_rel=0.0, outer_flag_band=1e-3):
@@ -94,93 +174,45 @@ def run(family, dx, dy, H, y, N, M, K, gamma, proposal, seed, prior_mean=None, p
     s0 = np.ones(D) if prior_std is None else np.asarray(prior_std, dtype=np.float64)
     seed = int(seed)
     records = []
-
-    def run_pfs(theta, k, hint):
-        ll = np.zeros(N)
-        g = np.zeros((N, D))
-        agg = {}
-        rows = []
-        if loglik_grad_fn is not None:
-            for i in range(N):
-                ll[i], g[i] = loglik_grad_fn(theta[i])
-            return ll, g, agg, rows
-        for i in range(N):
-            ha = hf = None
-            if hint is not None:
-                ha = hint["pf_anc"][i]
-                hf = hint["pf_flag"][i]
-            r = _pf(family, dx, dy, H, theta[i], y, M, seed, k, i, scheme=scheme,
-                    ess_frac=ess_frac, want_grad=True, hint_anc=ha, hint_flag=hf,
-                    band=band, flag_band=flag_band, want_tape=False, band_rel=band_rel)
-            ll[i] = r["loglik"]
-            g[i] = r["grad"]
-            rows.append(r["stats"])
-            for key, v in r["stats"].items():
-                agg[key] = agg.get(key, 0) + v
-        return ll, g, agg, rows
-
-    theta = np.zeros((N, D))
-    logw = np.zeros(N)
-    logpi = np.zeros(N)
-    gradpi = np.zeros((N, D))
-    loglik = np.zeros(N)
+    state = State(N, D)
     for k in range(1, K + 1):
         hint = hints[k - 1] if hints is not None else None
-        xi = np.stack([_normals(seed, k, i, 0, STREAM_OUTER_XI, D) for i in range(N)])
-        if k == 1:
-            # theta_1 ~ q_1 = prior (Eq. init_sample); w_1 = pi/q_1 = p-hat(y|theta) (Eq. init_weights)
-            theta_new = m0 + s0 * xi
-            ll_new, g_new, pfstats, pfrows = run_pfs(theta_new, k, hint)
-            lp_new = log_prior(theta_new, m0, s0) + ll_new
-            gp_new = grad_log_prior(theta_new, m0, s0) + g_new
-            logw = ll_new.copy()
-        else:
-            if proposal == "langevin":
-                drift = 0.5 * gamma * gamma * gradpi
-            else:
-                drift = np.zeros_like(gradpi)
-            theta_new = theta + drift + gamma * xi
-            ll_new, g_new, pfstats, pfrows = run_pfs(theta_new, k, hint)
-            lp_new = log_prior(theta_new, m0, s0) + ll_new
-            gp_new = grad_log_prior(theta_new, m0, s0) + g_new
-            if proposal == "langevin":
-                drift_new = 0.5 * gamma * gamma * gp_new
-            else:
-                drift_new = np.zeros_like(gp_new)
-            log_q = log_normal_iso(theta_new, theta + drift, gamma)     # q(theta_k | theta_{k-1})
-            log_L = log_normal_iso(theta, theta_new + drift_new, gamma)  # L(theta_{k-1} | theta_k)
-            logw = logw + lp_new - logpi + log_L - log_q                 # Eq. l_weights
-        theta, logpi, gradpi, loglik = theta_new, lp_new, gp_new, ll_new
-
-        # normalise, estimate, recycling statistic, ESS
-        L = _lse(logw)
-        wn = np.exp(logw - L)
-        mean = wn @ theta
-        ess = 1.0 / np.sum(wn * wn)
-        l_k = np.exp(2.0 * _lse(logw) - _lse(2.0 * logw))        # (sum w)^2 / sum w^2
-        rec = {"k": k, "ess": float(ess), "l_k": float(l_k), "mean": mean.copy(),
-               "theta": theta.copy(), "logw": logw.copy(), "loglik": loglik.copy(),
-               "grad": gradpi.copy(), "pf_stats": pfstats, "pf_stats_rows": pfrows,
-               "resampled": False,
-               "outer_stats": {}}
-        own_flag = ess < N / 2.0
-        flag = own_flag
-        if hint is not None and "outer_flag" in hint and bool(hint["outer_flag"]) != own_flag:
-            near = abs(ess / (N / 2.0) - 1.0) < outer_flag_band
-            rec["outer_stats"]["flag_tie" if near else "flag_disagree"] = 1
-            flag = bool(hint["outer_flag"])
-        if flag:
-            nu = _uniform_open(seed, k, 0, 0, STREAM_OUTER_NU)
-            hint_a = hint["outer_anc"] if (hint is not None and "outer_anc" in hint) else None
-            a, st = systematic_ancestors(logw, nu, hint_a, band=outer_band)
-            rec["outer_stats"].update(st)
-            rec["ancestors"] = a
-            theta, logpi, gradpi, loglik = theta[a], logpi[a], gradpi[a], loglik[a]
-            logw = np.full(N, L - np.log(N))
-            rec["resampled"] = True
+        theta_new = propose(state, k, seed, gamma, proposal, m0, s0)
+        ll_new, g_new, pfstats, pfrows = run_filters(family, dx, dy, H, y, M, seed, k, theta_new,
+                                                     range(N), scheme, ess_frac, hint, band, flag_band,
+                                                     band_rel, loglik_grad_fn)
+        rec = update(state, k, theta_new, ll_new, g_new, seed, gamma, proposal, m0, s0, hint,
+                     outer_band, outer_flag_band)
+        rec["pf_stats"] = pfstats
+        rec["pf_stats_rows"] = pfrows
         records.append(rec)
+    return records, recycled_mean(records)
 
-    lks = np.array([r["l_k"] for r in records])
-    ck = lks / lks.sum()                                             # Eq. opt_recycling_constant
-    recycled = sum(c * r["mean"] for c, r in zip(ck, records))       # Sec. III-C
-    return records, recycled
+
+def run_filters(family, dx, dy, H, y, M, seed, k, theta, rows, scheme=SYSTEMATIC, ess_frac=0.5,
+                hint=None, band=1e-6, flag_band=1e-6, band_rel=0.0, loglik_grad_fn=None):
+    """CRN particle filters (forward-mode gradient) of the given rows of theta with the
+    Philox keys of those rows; returns (log p-hat, gradient, aggregated stats, per-row stats)."""
+    rows = list(rows)
+    D = theta.shape[1]
+    ll = np.zeros(len(rows))
+    g = np.zeros((len(rows), D))
+    agg = {}
+    stats_rows = []
+    for r, i in enumerate(rows):
+        if loglik_grad_fn is not None:
+            ll[r], g[r] = loglik_grad_fn(theta[i])
+            continue
+        ha = hf = None
+        if hint is not None:
+            ha = hint["pf_anc"][i]
+            hf = hint["pf_flag"][i]
+        out = _pf(family, dx, dy, H, theta[i], y, M, seed, k, i, scheme=scheme,
+                  ess_frac=ess_frac, want_grad=True, hint_anc=ha, hint_flag=hf,
+                  band=band, flag_band=flag_band, want_tape=False, band_rel=band_rel)
+        ll[r] = out["loglik"]
+        g[r] = out["grad"]
+        stats_rows.append(out["stats"])
+        for key, v in out["stats"].items():
+            agg[key] = agg.get(key, 0) + v
+    return ll, g, agg, stats_rows

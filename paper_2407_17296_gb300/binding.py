@@ -21,7 +21,7 @@ SYSTEMATIC, MULTINOMIAL = 0, 1
 
 # every symbol include/smc2.h declares
 EXPORTS = ("smc2_config_init", "smc2_create", "pf_loglik_grad", "pf_loglik_grad_rows",
-           "pf_loglik_grad_host", "smc2_step", "smc2_get_samples", "smc2_get_state",
+           "pf_loglik_grad_host", "smc2_step", "smc2_step_filters", "smc2_step_update", "smc2_get_samples", "smc2_get_state",
            "smc2_get_trace", "smc2_set_observations", "smc2_footprint", "smc2_destroy",
            "smc2_autotune", "smc2_get_launch", "smc2_get_status", "smc2_kernel_launches", "smc2_last_error", "smc2_server_create",
            "smc2_submit", "smc2_poll", "smc2_cancel", "smc2_server_destroy",
@@ -102,6 +102,8 @@ def load(path: str = LIB_PATH):
         "pf_loglik_grad_rows": (ctypes.c_int, [vp, dp, ctypes.c_int, u32, u32, dp, dp]),
         "pf_loglik_grad_host": (ctypes.c_int, [vp, dp, ctypes.c_int, u32, dp, dp]),
         "smc2_step": (ctypes.c_int, [vp, ctypes.POINTER(Stats)]),
+        "smc2_step_filters": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, dp, dp]),
+        "smc2_step_update": (ctypes.c_int, [vp, dp, dp, ctypes.POINTER(Stats)]),
         "smc2_get_samples": (ctypes.c_int, [vp, dp, dp]),
         "smc2_get_state": (ctypes.c_int, [vp, dp, dp]),
         "smc2_get_trace": (ctypes.c_int, [vp, vp, vp, vp, vp]),
@@ -248,6 +250,26 @@ class Handle:
             st.mean = mean.ctypes.data
             st.recycled_mean = rec.ctypes.data
         check(self.lib.smc2_step(self.h, ctypes.byref(st)), "smc2_step")
+        return {"k": st.k, "resampled": bool(st.resampled), "ess": st.ess, "l_k": st.l_k,
+                "max_logw": st.max_logw, "mean": mean, "recycled_mean": rec}
+
+    def step_filters(self, row0, n, loglik, grad):
+        """Propose for all N samples and run the filters of rows row0 .. row0+n-1 into the
+        device tensors loglik [n] and grad [n][D] (FP64); asynchronous."""
+        check(self.lib.smc2_step_filters(self.h, int(row0), int(n), _ptr(loglik), _ptr(grad)),
+              "smc2_step_filters")
+
+    def step_update(self, loglik_all, grad_all, want_means=True):
+        """Complete the iteration from the filter outputs of all N rows (device tensors)."""
+        import numpy as np
+        st = Stats()
+        mean = np.zeros(self.D)
+        rec = np.zeros(self.D)
+        if want_means:
+            st.mean = mean.ctypes.data
+            st.recycled_mean = rec.ctypes.data
+        check(self.lib.smc2_step_update(self.h, _ptr(loglik_all), _ptr(grad_all), ctypes.byref(st)),
+              "smc2_step_update")
         return {"k": st.k, "resampled": bool(st.resampled), "ess": st.ess, "l_k": st.l_k,
                 "max_logw": st.max_logw, "mean": mean, "recycled_mean": rec}
 

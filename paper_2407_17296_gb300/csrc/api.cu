@@ -556,6 +556,43 @@ extern "C" int smc2_step(smc2_handle* h, smc2_stats* out) {
     return read_stats(h, out);
 }
 
+extern "C" int smc2_step_filters(smc2_handle* h, int row0, int n, double* loglik_dev, double* grad_dev) {
+    if (!h) return fail(SMC2_E_INVAL, "handle is NULL");
+    if (h->split_pending) return fail(SMC2_E_INVAL, "smc2_step_update must follow smc2_step_filters");
+    if (row0 < 0 || n < 0 || row0 + n > h->cfg.N) return fail(SMC2_E_INVAL, "rows must lie in [0, N)");
+    if (n > 0 && (!loglik_dev || !grad_dev)) return fail(SMC2_E_INVAL, "loglik and grad must not be NULL");
+    const OuterArgs o = make_outer_args(h);
+    if (launch_outer_propose(o, h->stream)) return fail(SMC2_E_CUDA, "outer propose launch failed");
+    count_launches(1);
+    if (n > 0) {
+        const PFArgs a = make_pf_args(h, h->theta_new + (size_t)row0 * h->D, n, 0u, (uint32_t)row0, h->k_dev,
+                                      loglik_dev, grad_dev);
+        int rc = launch_filters(h, a);
+        if (rc) return rc;
+    }
+    h->split_pending = true;
+    return SMC2_OK;
+}
+
+extern "C" int smc2_step_update(smc2_handle* h, const double* loglik_all_dev, const double* grad_all_dev,
+                                smc2_stats* out) {
+    if (!h) return fail(SMC2_E_INVAL, "handle is NULL");
+    if (!h->split_pending) return fail(SMC2_E_INVAL, "smc2_step_update without smc2_step_filters");
+    if (!loglik_all_dev || !grad_all_dev) return fail(SMC2_E_INVAL, "loglik and grad must not be NULL");
+    const size_t N = h->cfg.N, D = h->D;
+    if (loglik_all_dev != h->ll_new)
+        CUDA_TRY(cudaMemcpyAsync(h->ll_new, loglik_all_dev, sizeof(double) * N, cudaMemcpyDeviceToDevice, h->stream));
+    if (grad_all_dev != h->grad_new)
+        CUDA_TRY(cudaMemcpyAsync(h->grad_new, grad_all_dev, sizeof(double) * N * D, cudaMemcpyDeviceToDevice,
+                                 h->stream));
+    const OuterArgs o = make_outer_args(h);
+    if (launch_outer_update(o, h->stream)) return fail(SMC2_E_CUDA, "outer update launch failed");
+    count_launches(1);
+    h->split_pending = false;
+    h->k += 1;
+    return read_stats(h, out);
+}
+
 extern "C" int smc2_get_samples(smc2_handle* h, double* theta_host, double* logw_host) {
     if (!h) return fail(SMC2_E_INVAL, "handle is NULL");
     const size_t N = h->cfg.N, D = h->D;

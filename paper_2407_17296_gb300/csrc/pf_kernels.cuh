@@ -537,13 +537,17 @@ __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, cons
     }
     const float logM = logf((float)M);
     float Lprev = logM;
-    // log p-hat accumulated as a compensated (Kahan) FP32 sum of the per-step terms
-    float acc = 0.f, comp = 0.f;
-    auto kahan = [&](float v) {
-        const float y = v - comp;
-        const float tt = acc + y;
-        comp = (tt - acc) - y;
-        acc = tt;
+    // log p-hat = sum_t (m_t + log s1_t - L_{t-1}) accumulated in FP64.  The FP32 terms of
+    // step t are parked in lane t mod 32 (three selects a step); every 32 steps, and at the
+    // end, warp 0 adds the parked terms to per-lane FP64 partials, which are combined once
+    // per filter.  FP64 work is thus 1/32 of the steps and confined to one warp.
+    const int lane = tid & 31;
+    const bool warp0 = tid < 32;
+    double acc = 0.0;
+    float pm = 0.f, pl = 0.f, pp = 0.f;
+    auto flush = [&]() {
+        if (warp0) acc += ((double)pm + (double)pl) - (double)pp;
+        pm = pl = pp = 0.f;
     };
     bool resample = false, dead = false;
     if (store) {
@@ -597,9 +601,12 @@ __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, cons
             break;
         }
         const float ls1 = logf(s1);
-        kahan(m);
-        kahan(ls1);
-        kahan(-Lprev);
+        if (lane == (t & 31)) {
+            pm = m;
+            pl = ls1;
+            pp = Lprev;
+        }
+        if ((t & 31) == 31) flush();
 #pragma unroll
         for (int p = 0; p < P; ++p) lw[p] -= m;
         Lprev = ls1;
@@ -616,7 +623,12 @@ __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, cons
                 store_state<P, DX, DL>(tr.x_ck(t / a.kc), tr.lw_ck(t / a.kc), j0, gl, M, x, lw);
         }
     }
-    if (tid == 0) a.loglik[f] = dead ? -INFINITY : (double)acc - (double)comp;
+    flush();
+    if (warp0) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+        if (tid == 0) a.loglik[f] = dead ? -INFINITY : acc;
+    }
 }
 
 // ---------------------------------------------------------------- adjoint pass

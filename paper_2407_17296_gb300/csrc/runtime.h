@@ -63,6 +63,7 @@ struct smc2_handle {
     uint32_t k = 0;             // iterations enqueued
     cudaGraphExec_t graph_exec = nullptr;
     bool no_graph = false;
+    bool split_pending = false;  // smc2_step_filters issued, smc2_step_update not yet
     int launches_per_step = 0;
 };
 
