@@ -198,10 +198,10 @@ void smc2::plan_sizes(const smc2_config* c, int D, int kc, Sizes* s) {
     const size_t N = c->N, M = c->M, T = c->T, DX = c->d_x, Mp = padded_particles(c->M);
     s->n_slots = (kc == 1) ? (int)(T + 1) : (int)((T + kc - 1) / kc);
     s->xck = N * s->n_slots * Mp * DX * sizeof(float) + 256;
-    s->lwck = N * s->n_slots * M * sizeof(float);
+    s->lwck = N * s->n_slots * Mp * sizeof(float);
     s->xseg = (kc > 1) ? N * kc * Mp * DX * sizeof(float) + 256 : 0;
-    s->lwseg = (kc > 1) ? N * kc * M * sizeof(float) : 0;
-    s->anc = N * T * M * sizeof(uint16_t);
+    s->lwseg = (kc > 1) ? N * kc * Mp * sizeof(float) : 0;
+    s->anc = N * T * (size_t)tape_stride(c->M) * sizeof(uint16_t);
     s->flag = N * T;
     s->steps = 2 * N * (T + 1) * sizeof(float);
     s->state = sizeof(double) * (N * D * 5 + N * 6 + 2 * D + kStatsHead + 2 * D) + sizeof(int) * N + 64;
@@ -397,8 +397,14 @@ PFArgs smc2::make_pf_args(smc2_handle* h, const double* theta, int n, uint32_t i
 
 int smc2::launch_filters(smc2_handle* h, const PFArgs& a) {
     int rc = h->fwd(a, h->stream, a.n);
-    if (!rc && a.want_grad) rc = h->bwd(a, h->stream, a.n);
-    if (rc) return fail(SMC2_E_CUDA, std::string("filter launch failed: ") + cudaGetErrorString(cudaGetLastError()));
+    const char* pass = "forward";
+    if (!rc && a.want_grad) {
+        rc = h->bwd(a, h->stream, a.n);
+        pass = "adjoint";
+    }
+    if (rc)
+        return fail(SMC2_E_CUDA, std::string(pass) + " filter launch failed: " +
+                                     (rc > 0 ? cudaGetErrorString((cudaError_t)rc) : "block too large"));
     count_launches(a.want_grad ? 2 : 1);
     return SMC2_OK;
 }
@@ -615,7 +621,9 @@ extern "C" int smc2_get_trace(smc2_handle* h, uint16_t* pf_anc, uint8_t* pf_flag
                               int32_t* outer_resampled) {
     if (!h) return fail(SMC2_E_INVAL, "handle is NULL");
     const size_t N = h->cfg.N, T = h->cfg.T, M = h->cfg.M;
-    if (pf_anc) CUDA_TRY(cudaMemcpyAsync(pf_anc, h->anc, sizeof(uint16_t) * N * T * M, cudaMemcpyDeviceToHost, h->stream));
+    if (pf_anc)  // tape rows are padded on the device; the host copy has M entries a row
+        CUDA_TRY(cudaMemcpy2DAsync(pf_anc, sizeof(uint16_t) * M, h->anc, sizeof(uint16_t) * tape_stride((int)M),
+                                   sizeof(uint16_t) * M, N * T, cudaMemcpyDeviceToHost, h->stream));
     if (pf_flag) CUDA_TRY(cudaMemcpyAsync(pf_flag, h->flag, N * T, cudaMemcpyDeviceToHost, h->stream));
     if (outer_anc) CUDA_TRY(cudaMemcpyAsync(outer_anc, h->outer_anc, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, h->stream));
     if (outer_resampled) {

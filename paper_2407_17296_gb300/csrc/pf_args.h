@@ -27,10 +27,10 @@ struct PFArgs {
     int kc;                 // checkpoint interval; 1 = every step is stored
     int n_slots;            // checkpoint slots per filter
     float* xck;             // [n][n_slots][Mp][DX], Mp = M rounded up to a multiple of 4
-    float* lwck;            // [n][n_slots][M]
+    float* lwck;            // [n][n_slots][Mp]
     float* xseg;            // [n][kc][Mp][DX]  (kc > 1)
-    float* lwseg;           // [n][kc][M]       (kc > 1)
-    uint16_t* anc;          // [n][T][M] ancestor tape (row t-1: before step t)
+    float* lwseg;           // [n][kc][Mp]      (kc > 1)
+    uint16_t* anc;          // [n][T][Ma] ancestor tape (row t-1: before step t), Ma = tape_stride(M)
     uint8_t* flag;          // [n][T]   1 if the filter resampled before step t
     float* mstep;           // [n][T+1] recentring maximum of step t
     float* lstep;           // [n][T+1] log sum exp of the recentred log-weights after step t
@@ -44,34 +44,37 @@ struct PFArgs {
 // starts on a 16-byte boundary (bulk asynchronous copies need it).
 SMC2_HD inline int padded_particles(int M) { return (M + 3) & ~3; }
 
+// Rows of the ancestor tape are padded to a multiple of 8 entries (16 bytes).
+SMC2_HD inline int tape_stride(int M) { return (M + 7) & ~7; }
+
 // Slots of the adjoint's shared-memory ring of trajectory slices.
 SMC2_HD inline int ring_slots(int DX) { return DX >= 16 ? 2 : 4; }
 
 // Dynamic shared-memory plan (mirrored on the host to size the launch).
 struct SmemLayout {
-    size_t xstage, xbstage, cs, marks, starts, red, scanw, scanwi, dred, bars, total;
+    size_t xstage, cs, marks, starts, red, scanw, scanwi, dred, bars, total;
     // fwd: xstage is the gather staging; bwd: xstage is the ring of trajectory slices
     // (ring_slots(DX) slots of padded_particles(M) * DX floats), whose first slot also
     // serves as staging during segment recomputation
-    SMC2_HD SmemLayout(int M, int DX, int D, bool fwd, int G = 1) {
+    SMC2_HD SmemLayout(int M, int DX, int D, bool fwd, int G, int T) {
         size_t o = 0;
         auto take = [&](size_t bytes) {
             const size_t r = o;
             o += (bytes + 15) & ~size_t(15);
             return r;
         };
-        const int Mp = (M + 3) & ~3;
         xstage = fwd ? take(sizeof(float) * (size_t)M * DX)
-                     : take(sizeof(float) * (size_t)Mp * DX * (DX >= 16 ? 2 : 4));
-        xbstage = fwd ? o : take(sizeof(float) * (size_t)M * DX);
-        cs = fwd ? take(sizeof(float) * (size_t)M) : o;
-        marks = take(sizeof(uint16_t) * (size_t)M);      // fwd: range marks; bwd: tape row
-        starts = fwd ? o : take(sizeof(float) * 32 * G * (DX / G + 1));  // segmented-scan scratch
+                     : take(sizeof(float) * (size_t)padded_particles(M) * DX * ring_slots(DX));
+        // fwd: multinomial cumulative weights; bwd: two log-weight buffers
+        cs = fwd ? take(sizeof(float) * (size_t)M) : take(sizeof(float) * 2 * (size_t)padded_particles(M));
+        // fwd: range marks; bwd: two tape-row buffers
+        marks = fwd ? take(sizeof(uint16_t) * (size_t)M) : take(sizeof(uint16_t) * 2 * (size_t)tape_stride(M));
+        starts = fwd ? o : take(sizeof(float) * 32 * G * (DX / G + 1));  // segmented-sum scratch
         red = take(sizeof(float4) * (2 * 32 + 2));  // two buffers of per-warp partials + results
         scanw = take(sizeof(unsigned long long) * 32);
         scanwi = take(sizeof(int) * 32);
         dred = fwd ? o : take(sizeof(double) * (size_t)D * 32);
-        bars = fwd ? o : take(sizeof(unsigned long long) * 2 * (DX >= 16 ? 2 : 4));
+        bars = fwd ? o : take(sizeof(unsigned long long) * 2 * ring_slots(DX));
         total = o;
     }
 };

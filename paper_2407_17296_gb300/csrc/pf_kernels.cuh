@@ -51,6 +51,16 @@ constexpr unsigned kFull = 0xffffffffu;
 
 // ---------------------------------------------------------------- block primitives
 
+// 16-byte asynchronous copy global -> shared (both addresses 16-byte aligned), completed
+// by cp_async_wait_all in the issuing thread
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // floor(w * 2^40) for w in [0, 1], from the float's bits with integer operations only
 // (conversions between floats and 64-bit integers run on the narrow FP64 pipe).
 __device__ __forceinline__ unsigned long long fixed40(float w) {
@@ -259,15 +269,172 @@ __device__ __forceinline__ void multinomial_ancestors(const float (&lw)[P], bool
     }
 }
 
+// ---------------------------------------------------------------- state I/O helpers
+
+// Lane gl of a group stores/loads/stages dimensions gl*DL .. gl*DL+DL-1 of its particles;
+// rows are particle-major [M][DX], so a group writes DX contiguous floats per particle.
+template <int P, int DX, int DL>
+__device__ __forceinline__ void store_state(float* __restrict__ xdst, float* __restrict__ lwdst, int j0,
+                                            int gl, int M, const float (&x)[P][DL], const float (&lw)[P]) {
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const int j = j0 + p;
+        if (j < M) {
+            float* dst = xdst + (size_t)j * DX + gl * DL;
+            if constexpr (DL % 4 == 0) {
+#pragma unroll
+                for (int k = 0; k < DL; k += 4)
+                    *reinterpret_cast<float4*>(dst + k) = make_float4(x[p][k], x[p][k + 1], x[p][k + 2], x[p][k + 3]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < DL; ++k) dst[k] = x[p][k];
+            }
+            if (lwdst && gl == 0) lwdst[j] = lw[p];
+        }
+    }
+}
+
+template <int P, int DX, int DL>
+__device__ __forceinline__ void load_x(const float* __restrict__ xsrc, int j0, int gl, int M,
+                                       float (&x)[P][DL]) {
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const float* src = xsrc + (size_t)min(j0 + p, M - 1) * DX + gl * DL;
+        if constexpr (DL % 4 == 0) {
+#pragma unroll
+            for (int k = 0; k < DL; k += 4) {
+                const float4 v = *reinterpret_cast<const float4*>(src + k);
+                x[p][k] = v.x; x[p][k + 1] = v.y; x[p][k + 2] = v.z; x[p][k + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < DL; ++k) x[p][k] = src[k];
+        }
+    }
+}
+
+template <int P, int DX, int DL>
+__device__ __forceinline__ void stage_x(float* xstage, int j0, int gl, int M, const float (&x)[P][DL]) {
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const int j = j0 + p;
+        if (j < M) {
+            float* dst = xstage + j * DX + gl * DL;
+            if constexpr (DL % 4 == 0) {
+#pragma unroll
+                for (int k = 0; k < DL; k += 4)
+                    *reinterpret_cast<float4*>(dst + k) = make_float4(x[p][k], x[p][k + 1], x[p][k + 2], x[p][k + 3]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < DL; ++k) dst[k] = x[p][k];
+            }
+        }
+    }
+}
+
+template <int DX, int DL>
+__device__ __forceinline__ void read_staged(const float* xstage, int j, int gl, float (&x)[DL]) {
+    const float* src = xstage + j * DX + gl * DL;
+    if constexpr (DL % 4 == 0) {
+#pragma unroll
+        for (int k = 0; k < DL; k += 4) {
+            const float4 v = *reinterpret_cast<const float4*>(src + k);
+            x[k] = v.x; x[k + 1] = v.y; x[k + 2] = v.z; x[k + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < DL; ++k) x[k] = src[k];
+    }
+}
+
+// Normals of the lane's dimensions of its P particles: normal index n = j*DX + k.
+template <int P, int DX, int DL>
+__device__ __forceinline__ void draw_normals(const PhiloxKey& key, uint32_t t, uint32_t stream, int j0, int gl,
+                                             float (&eps)[P * DL]) {
+    if constexpr (DL == DX) {
+        normals<P * DX>(key, t, stream, (uint32_t)(j0 * DX), eps);
+    } else {
+#pragma unroll
+        for (int p = 0; p < P; ++p)
+            normals<DL>(key, t, stream, (uint32_t)((j0 + p) * DX + gl * DL),
+                        reinterpret_cast<float(&)[DL]>(eps[p * DL]));
+    }
+}
+
+// Sum over the G lanes of a group (every lane gets the same value).
+template <int G>
+__device__ __forceinline__ float group_sum(float v) {
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// Sorted-ancestor gather adjoint used per model shape, as measured: the run walk for the
+// four-dimensional model (short runs; one barrier), the balanced segmented sum elsewhere
+// (the 16-dimensional model resamples at nearly every step with very uneven offspring
+// counts, where a long run serialises the walk; for one-dimensional states the walk's
+// data-dependent loop costs more in the steps that do not resample than it saves).
+template <int G, int DX>
+constexpr bool kGatherWalk = (G == 1 && DX == 4);
+
 // Adjoint of the gather x'_i = x_{a_i} for sorted ancestors (systematic resampling):
-// xbar_new[j] = sum of xbar'[i] over the offspring i of j (a run of equal a_i), zero for
-// parents without offspring.  A segmented prefix sum (thread, warp shuffles, warps) keeps
-// the work balanced whatever the offspring counts, e.g. when one particle owns them all.
-// Each lane handles its own state dimensions; ancs holds the tape row in shared memory
-// (visible to all threads before the call); xbstage receives the per-parent sums; segw is
+// xbar_new[j] = sum of xbar'[i] over the offspring i of j, which form the run of entries
+// equal to j in the sorted tape row (empty for parents without offspring).  Every child
+// stages its cotangent in its own row of `stage` (a ring slot whose states have been
+// consumed); after one barrier the thread owning parents j0 .. j0+P-1 finds the first
+// offspring of j0 by binary search in the tape row and sums its parents' runs in order
+// (deterministic; the work of a thread is its parents' offspring count).
+template <int P, int DX, int DL, int G>
+__device__ __forceinline__ void gather_adjoint_runs(float (&xbar)[P][DL], int j0, int gl, int M,
+                                                    const uint16_t* ancs, float* stage) {
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const int i = j0 + p;
+        if (i < M) {
+            float* dst = stage + (size_t)i * DX + gl * DL;
+            if constexpr (DL % 4 == 0) {
+#pragma unroll
+                for (int k = 0; k < DL; k += 4)
+                    *reinterpret_cast<float4*>(dst + k) =
+                        make_float4(xbar[p][k], xbar[p][k + 1], xbar[p][k + 2], xbar[p][k + 3]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < DL; ++k) dst[k] = xbar[p][k];
+            }
+        }
+    }
+    __syncthreads();
+    int lo = 0, hi = M;  // lower_bound(ancs[0 .. M), j0)
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((int)ancs[mid] < j0) lo = mid + 1;
+        else hi = mid;
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const int j = j0 + p;
+        float acc[DL];
+#pragma unroll
+        for (int k = 0; k < DL; ++k) acc[k] = 0.f;
+        while (lo < M && (int)ancs[lo] == j) {
+            float v[DL];
+            read_staged<DX, DL>(stage, lo, gl, v);
+#pragma unroll
+            for (int k = 0; k < DL; ++k) acc[k] += v[k];
+            ++lo;
+        }
+#pragma unroll
+        for (int k = 0; k < DL; ++k) xbar[p][k] = acc[k];
+    }
+}
+
+// The same adjoint by a segmented prefix sum over the children (thread, warp shuffles,
+// warps), balanced whatever the offspring counts, e.g. when one particle owns them all.
+// Each lane handles its own state dimensions; ancs holds the sorted tape row in shared
+// memory; xbstage (rows of the consumed x_t slice) receives the per-parent sums; segw is
 // 32 x G x (DL + 1) floats of scratch.  Two __syncthreads.
 template <int P, int DX, int DL, int G>
-__device__ __forceinline__ void gather_adjoint_sorted(float (&xbar)[P][DL], const int (&ai)[P], int j0, int gl,
+__device__ __forceinline__ void gather_adjoint_segmented(float (&xbar)[P][DL], const int (&ai)[P], int j0, int gl,
                                                       int M, const uint16_t* ancs, float* xbstage,
                                                       float* segw) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -387,115 +554,50 @@ __device__ __forceinline__ void gather_adjoint_sorted(float (&xbar)[P][DL], cons
             for (int k = 0; k < DL; ++k) xbar[p][k] = xbstage[(j0 + p) * DX + gl * DL + k];
 }
 
-// ---------------------------------------------------------------- state I/O helpers
-
-// Lane gl of a group stores/loads/stages dimensions gl*DL .. gl*DL+DL-1 of its particles;
-// rows are particle-major [M][DX], so a group writes DX contiguous floats per particle.
-template <int P, int DX, int DL>
-__device__ __forceinline__ void store_state(float* __restrict__ xdst, float* __restrict__ lwdst, int j0,
-                                            int gl, int M, const float (&x)[P][DL], const float (&lw)[P]) {
+// Adjoint of the gather for unsorted ancestors (multinomial resampling): each thread clears
+// its own rows of `stage`, then every child adds its cotangent into its parent's row with
+// shared-memory atomics, and each thread reads back its own rows.  Two barriers.
+template <int P, int DX, int DL, int G>
+__device__ __forceinline__ void gather_adjoint_scatter(float (&xbar)[P][DL], const int (&ai)[P], int j0, int gl,
+                                                       int M, float* stage) {
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+        if (j0 + p < M)
+#pragma unroll
+            for (int k = 0; k < DL; ++k) stage[(size_t)(j0 + p) * DX + gl * DL + k] = 0.f;
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+        if (j0 + p < M)
+#pragma unroll
+            for (int k = 0; k < DL; ++k) atomicAdd(&stage[(size_t)ai[p] * DX + gl * DL + k], xbar[p][k]);
+    __syncthreads();
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-        const int j = j0 + p;
-        if (j < M) {
-            float* dst = xdst + (size_t)j * DX + gl * DL;
-            if constexpr (DL % 4 == 0) {
-#pragma unroll
-                for (int k = 0; k < DL; k += 4)
-                    *reinterpret_cast<float4*>(dst + k) = make_float4(x[p][k], x[p][k + 1], x[p][k + 2], x[p][k + 3]);
-            } else {
-#pragma unroll
-                for (int k = 0; k < DL; ++k) dst[k] = x[p][k];
-            }
-            if (lwdst && gl == 0) lwdst[j] = lw[p];
-        }
-    }
-}
-
-template <int P, int DX, int DL>
-__device__ __forceinline__ void load_x(const float* __restrict__ xsrc, int j0, int gl, int M,
-                                       float (&x)[P][DL]) {
-#pragma unroll
-    for (int p = 0; p < P; ++p) {
-        const float* src = xsrc + (size_t)min(j0 + p, M - 1) * DX + gl * DL;
-        if constexpr (DL % 4 == 0) {
-#pragma unroll
-            for (int k = 0; k < DL; k += 4) {
-                const float4 v = *reinterpret_cast<const float4*>(src + k);
-                x[p][k] = v.x; x[p][k + 1] = v.y; x[p][k + 2] = v.z; x[p][k + 3] = v.w;
-            }
+        if (j0 + p < M) {
+            read_staged<DX, DL>(stage, j0 + p, gl, xbar[p]);
         } else {
 #pragma unroll
-            for (int k = 0; k < DL; ++k) x[p][k] = src[k];
+            for (int k = 0; k < DL; ++k) xbar[p][k] = 0.f;
         }
     }
-}
-
-template <int P, int DX, int DL>
-__device__ __forceinline__ void stage_x(float* xstage, int j0, int gl, int M, const float (&x)[P][DL]) {
-#pragma unroll
-    for (int p = 0; p < P; ++p) {
-        const int j = j0 + p;
-        if (j < M) {
-            float* dst = xstage + j * DX + gl * DL;
-            if constexpr (DL % 4 == 0) {
-#pragma unroll
-                for (int k = 0; k < DL; k += 4)
-                    *reinterpret_cast<float4*>(dst + k) = make_float4(x[p][k], x[p][k + 1], x[p][k + 2], x[p][k + 3]);
-            } else {
-#pragma unroll
-                for (int k = 0; k < DL; ++k) dst[k] = x[p][k];
-            }
-        }
-    }
-}
-
-template <int DX, int DL>
-__device__ __forceinline__ void read_staged(const float* xstage, int j, int gl, float (&x)[DL]) {
-    const float* src = xstage + j * DX + gl * DL;
-    if constexpr (DL % 4 == 0) {
-#pragma unroll
-        for (int k = 0; k < DL; k += 4) {
-            const float4 v = *reinterpret_cast<const float4*>(src + k);
-            x[k] = v.x; x[k + 1] = v.y; x[k + 2] = v.z; x[k + 3] = v.w;
-        }
-    } else {
-#pragma unroll
-        for (int k = 0; k < DL; ++k) x[k] = src[k];
-    }
-}
-
-// Normals of the lane's dimensions of its P particles: normal index n = j*DX + k.
-template <int P, int DX, int DL>
-__device__ __forceinline__ void draw_normals(const PhiloxKey& key, uint32_t t, uint32_t stream, int j0, int gl,
-                                             float (&eps)[P * DL]) {
-    if constexpr (DL == DX) {
-        normals<P * DX>(key, t, stream, (uint32_t)(j0 * DX), eps);
-    } else {
-#pragma unroll
-        for (int p = 0; p < P; ++p)
-            normals<DL>(key, t, stream, (uint32_t)((j0 + p) * DX + gl * DL),
-                        reinterpret_cast<float(&)[DL]>(eps[p * DL]));
-    }
-}
-
-// Sum over the G lanes of a group (every lane gets the same value).
-template <int G>
-__device__ __forceinline__ float group_sum(float v) {
-#pragma unroll
-    for (int o = 1; o < G; o <<= 1) v += __shfl_xor_sync(kFull, v, o);
-    return v;
 }
 
 struct Traj {
-    // slot addressing of the stored trajectory of filter f (state slices padded to Mp rows)
+    // slot addressing of the stored trajectory of filter f (state slices padded to Mp rows,
+    // log-weight slices to Mp entries, tape rows to tape_stride(M) entries)
     const PFArgs& a;
     int f, DX;
-    __device__ size_t xs() const { return (size_t)padded_particles(a.M) * DX; }
+    __device__ size_t mp() const { return (size_t)padded_particles(a.M); }
+    __device__ size_t xs() const { return mp() * DX; }
     __device__ float* x_ck(int slot) const { return a.xck + ((size_t)f * a.n_slots + slot) * xs(); }
-    __device__ float* lw_ck(int slot) const { return a.lwck + ((size_t)f * a.n_slots + slot) * a.M; }
+    __device__ float* lw_ck(int slot) const { return a.lwck + ((size_t)f * a.n_slots + slot) * mp(); }
     __device__ float* x_seg(int r) const { return a.xseg + ((size_t)f * a.kc + r) * xs(); }
-    __device__ float* lw_seg(int r) const { return a.lwseg + ((size_t)f * a.kc + r) * a.M; }
+    __device__ float* lw_seg(int r) const { return a.lwseg + ((size_t)f * a.kc + r) * mp(); }
+    // ancestors used at step t + 1 (row t of the filter's tape)
+    __device__ uint16_t* anc_row(int t) const {
+        return a.anc + ((size_t)f * a.T + t) * (size_t)tape_stride(a.M);
+    }
 };
 
 // ---------------------------------------------------------------- forward pass
@@ -568,7 +670,7 @@ __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, cons
                 multinomial_ancestors<P, G>(lw, lead, j0, M, key, (uint32_t)t, cs, scanw, anc);
             }
             if (a.anc && lead) {
-                uint16_t* row = a.anc + ((size_t)f * T + (t - 1)) * M;
+                uint16_t* row = tr.anc_row(t - 1);
 #pragma unroll
                 for (int p = 0; p < P; ++p)
                     if (j0 + p < M) row[j0 + p] = (uint16_t)anc[p];
@@ -635,16 +737,16 @@ __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, cons
 
 template <class Mdl, int P, int R>
 __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, const SmemLayout& L,
-                                typename Mdl::Params& sprm, SliceRing<R>& ring, uint32_t& g) {
+                                typename Mdl::Params& sprm, SliceRing<R, Mdl::DX>& ring, uint32_t& g) {
     constexpr int DX = Mdl::DX, DY = Mdl::DY, D = Mdl::D, G = Mdl::G, DL = Mdl::DL, DTH = Mdl::DTH;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     const int gl = (G > 1) ? (tid & (G - 1)) : 0;
     const bool lead = gl == 0;
     const int M = a.M, T = a.T, kc = a.kc;
     float* xstage = reinterpret_cast<float*>(smem + L.xstage);
-    float* xbstage = reinterpret_cast<float*>(smem + L.xbstage);
-    uint16_t* ancs = reinterpret_cast<uint16_t*>(smem + L.marks);
     float* segw = reinterpret_cast<float*>(smem + L.starts);
+    uint16_t* ancbuf = reinterpret_cast<uint16_t*>(smem + L.marks);  // two tape-row buffers
+    float* lwbuf = reinterpret_cast<float*>(smem + L.cs);             // two log-weight buffers
     double* dred = reinterpret_cast<double*>(smem + L.dred);
 
     const double ll = a.loglik[f];
@@ -652,6 +754,8 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
         for (int d = tid; d < D; d += blockDim.x) a.grad[(size_t)f * D + d] = 0.0;
         return;
     }
+    const uint8_t* flags = a.flag + (size_t)f * T;  // flags[t-1]: resampled before step t
+    auto resampled_before = [&](int t) -> bool { return flags[t - 1] != 0; };
     if (tid == 0) Mdl::make_params(a.theta + (size_t)f * a.D, a.H, sprm);
     __syncthreads();
     typename Mdl::LaneParams prm;
@@ -662,7 +766,6 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
     const Traj tr{a, f, DX};
     const float* lstep = a.lstep + (size_t)f * (T + 1);
     const float* mstep = a.mstep + (size_t)f * (T + 1);
-    const uint8_t* flags = a.flag + (size_t)f * T;
 
     float xbar[P][DL], lwbar[P], thb[DTH];
 #pragma unroll
@@ -674,9 +777,10 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
 
     // With kc = 1 the whole run is one segment whose every step is a checkpoint slot.
     // The sweep over a segment reads the state slices X(t1), X(t1-1), ..., X(t0) from the
-    // shared-memory ring, R slices ahead of use; slice g+k holds x_{t1-k}.
+    // shared-memory ring, R slices ahead of use; slice g+k holds x_{t1-k}.  The tape row and
+    // log-weights of a resampling step are loaded into registers one step ahead of use.
     const int S = (kc == 1) ? 1 : (T + kc - 1) / kc;
-    const int Mp = padded_particles(M);
+    uint32_t nres = 0;  // resampling steps swept so far (parity selects the tape-row buffer)
     for (int s = S - 1; s >= 0; --s) {
         const int t0 = (kc == 1) ? 0 : s * kc;
         const int t1 = (kc == 1) ? T : min(t0 + kc, T);
@@ -689,15 +793,18 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
             return (t == t0) ? tr.lw_ck(s) : tr.lw_seg(t - t0 - 1);
         };
         if (kc > 1) {
-            // recompute the segment (t0, t1] from its checkpoint: same CRN, tape ancestors
+            // recompute the segment (t0, t1] from its checkpoint: same CRN, tape ancestors.
+            // Resampling steps stage states in ring slot 0: every warp must be done with the
+            // previous segment's slices first.
+            __syncthreads();
             float x[P][DL], lw[P];
             load_x<P, DX, DL>(tr.x_ck(s), j0, gl, M, x);
 #pragma unroll
             for (int p = 0; p < P; ++p) lw[p] = (j0 + p < M) ? tr.lw_ck(s)[j0 + p] : -INFINITY;
             for (int t = t0 + 1; t <= t1; ++t) {
-                if (flags[t - 1]) {
+                if (resampled_before(t)) {
                     stage_x<P, DX, DL>(xstage, j0, gl, M, x);
-                    const uint16_t* row = a.anc + ((size_t)f * T + (t - 1)) * M;
+                    const uint16_t* row = tr.anc_row(t - 1);
                     __syncthreads();
 #pragma unroll
                     for (int p = 0; p < P; ++p) {
@@ -713,13 +820,14 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
                     Mdl::transition(prm, x[p], reinterpret_cast<const float(&)[DL]>(eps[p * DL]));
-                    float g = Mdl::loglik(prm, x[p], yt);
-                    if constexpr (G > 1) g = group_sum<G>(g) + prm.cst;
-                    if (j0 + p < M) lw[p] += g;
+                    float gg = Mdl::loglik(prm, x[p], yt);
+                    if constexpr (G > 1) gg = group_sum<G>(gg) + prm.cst;
+                    if (j0 + p < M) lw[p] += gg;
                     lw[p] -= mt;
                 }
                 store_state<P, DX, DL>(tr.x_seg(t - t0 - 1), tr.lw_seg(t - t0 - 1), j0, gl, M, x, lw);
             }
+            fence_proxy_async_shared();  // staged states precede the copies into slot 0
         }
         // the recomputed slices (global, generic proxy) and the staging slot (shared) must be
         // ordered before the bulk copies that refill the ring
@@ -729,7 +837,22 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
             fence_proxy_async();
             for (int k = 0; k < R && k < Ls; ++k) ring.produce(g + k, Xp(t1 - k), a.status);
         }
-        ring.acquire(g, a.status);
+        // tape row and log w_{tt-1} of step tt (which resampled) into buffer b, by
+        // asynchronous copies of 16-byte chunks issued by all threads one step ahead of use
+        // (a block has at least M/8 threads: one tape chunk and at most two log-weight
+        // chunks per thread)
+        auto prefetch = [&](int tt, uint32_t b) {
+            const char* ra = reinterpret_cast<const char*>(tr.anc_row(tt - 1));
+            const char* rl = reinterpret_cast<const char*>(LWp(tt - 1));
+            char* da = reinterpret_cast<char*>(ancbuf + b * (uint32_t)tape_stride(M));
+            char* dl = reinterpret_cast<char*>(lwbuf + b * (uint32_t)padded_particles(M));
+            const int nt = blockDim.x, na = tape_stride(M) / 8, nl = padded_particles(M) / 4;
+            if (tid < na) cp_async16(da + 16 * tid, ra + 16 * tid);
+            if (tid < nl) cp_async16(dl + 16 * tid, rl + 16 * tid);
+            if (tid + nt < nl) cp_async16(dl + 16 * (tid + nt), rl + 16 * (tid + nt));
+            cp_async_commit();
+        };
+        if (t1 > t0 && resampled_before(t1)) prefetch(t1, nres & 1u);
         if (s == S - 1) {
             // cotangent of log w_T: normalised final weights (Eq. dloglik)
             const float* lwT = LWp(T);
@@ -737,10 +860,14 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
 #pragma unroll
             for (int p = 0; p < P; ++p) lwbar[p] = (j0 + p < M) ? __expf(lwT[j0 + p] - LT) : 0.f;
         }
+        ring.acquire(g, a.status);
+        bool fl_next = t1 > t0 && resampled_before(t1);
         for (int k = 0; k < Ls - 1; ++k) {
             const int t = t1 - k;
+            const bool fl = fl_next;
+            fl_next = t - 1 > t0 && resampled_before(t - 1);  // loaded now, used at the end of the step
             ring.acquire(g + k + 1, a.status);
-            const float* st = ring.slot(g + k);      // x_t
+            float* st = ring.slot(g + k);            // x_t (then the staged cotangents)
             const float* sp = ring.slot(g + k + 1);  // x_{t-1}
             float xt[P][DL];
 #pragma unroll
@@ -749,57 +876,48 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
             // padding particles have zero cotangents and finite (clamped) states: no guards
 #pragma unroll
             for (int p = 0; p < P; ++p) Mdl::bwd_obs(prm, xt[p], yt, lwbar[p], xbar[p], thb);
-            const bool fl = flags[t - 1] != 0;
-            float xp[P][DL];
             int ai[P];
+            const uint16_t* ancs = ancbuf + (nres & 1u) * (uint32_t)tape_stride(M);
+            const float* lwrow = lwbuf + (nres & 1u) * (uint32_t)padded_particles(M);
             if (fl) {
-                const uint16_t* row = a.anc + ((size_t)f * T + (t - 1)) * M;
+                // the prefetched tape row and log-weights have landed (each thread waits for
+                // its own copies, the barrier for everyone's); every warp is also done with
+                // this slice as x_{t-1} of the previous step, so its rows may be overwritten
+                cp_async_wait_all();
+                __syncthreads();
 #pragma unroll
-                for (int p = 0; p < P; ++p) {
-                    ai[p] = (j0 + p < M) ? (int)row[j0 + p] : 0;
-                    if (lead && j0 + p < M) ancs[j0 + p] = (uint16_t)ai[p];
-                }
+                for (int p = 0; p < P; ++p) ai[p] = min((int)ancs[min(j0 + p, M - 1)], M - 1);
             } else {
 #pragma unroll
                 for (int p = 0; p < P; ++p) ai[p] = min(j0 + p, M - 1);
             }
+            float xp[P][DL];
 #pragma unroll
             for (int p = 0; p < P; ++p) read_staged<DX, DL>(sp, ai[p], gl, xp[p]);
 #pragma unroll
             for (int p = 0; p < P; ++p) Mdl::bwd_trans(prm, xt[p], xp[p], xbar[p], thb);
-            // x_t is no longer needed: free its slot and refill it R slices ahead
-            ring.release(g + k);
-            if (tid == 0 && k + R < Ls) ring.produce(g + k + R, Xp(t1 - k - R), a.status);
             if (fl) {
-                __syncthreads();  // the tape row in ancs is complete
-                // adjoint of the gather x'_i = x_{a_i}: sum the cotangents of each parent's offspring
-                if (a.scheme == 0) {
-                    gather_adjoint_sorted<P, DX, DL, G>(xbar, ai, j0, gl, M, ancs, xbstage, segw);
-                } else {
-#pragma unroll
-                    for (int p = 0; p < P; ++p)
-                        if (j0 + p < M)
-#pragma unroll
-                            for (int kk = 0; kk < DL; ++kk) xbstage[(j0 + p) * DX + gl * DL + kk] = 0.f;
-                    __syncthreads();
-#pragma unroll
-                    for (int p = 0; p < P; ++p)
-                        if (j0 + p < M)
-#pragma unroll
-                            for (int kk = 0; kk < DL; ++kk)
-                                atomicAdd(&xbstage[ai[p] * DX + gl * DL + kk], xbar[p][kk]);
-                    __syncthreads();
-#pragma unroll
-                    for (int p = 0; p < P; ++p)
-                        if (j0 + p < M) read_staged<DX, DL>(xbstage, j0 + p, gl, xbar[p]);
-                }
+                // adjoint of the gather x'_i = x_{a_i}: sum the cotangents of each parent's
+                // offspring, staged in the rows of x_t (each thread has read its own)
+                if (a.scheme != 0)
+                    gather_adjoint_scatter<P, DX, DL, G>(xbar, ai, j0, gl, M, st);
+                else if (kGatherWalk<G, DX>)
+                    gather_adjoint_runs<P, DX, DL, G>(xbar, j0, gl, M, ancs, st);
+                else
+                    gather_adjoint_segmented<P, DX, DL, G>(xbar, ai, j0, gl, M, ancs, st, segw);
+                // the staged cotangents (generic-proxy writes) precede the bulk copy that
+                // will refill this slot
+                fence_proxy_async_shared();
                 // adjoint of the mean reset log w' = LSE(log w) - log M: cotangent becomes w~_{t-1}
-                const float* lwp = LWp(t - 1);
                 const float Lp = lstep[t - 1];
 #pragma unroll
-                for (int p = 0; p < P; ++p) lwbar[p] = (j0 + p < M) ? __expf(lwp[j0 + p] - Lp) : 0.f;
-                __syncthreads();
+                for (int p = 0; p < P; ++p) lwbar[p] = (j0 + p < M) ? __expf(lwrow[j0 + p] - Lp) : 0.f;
+                ++nres;
             }
+            // the next resampling step's buffer was last read before this step's barrier
+            if (fl_next) prefetch(t - 1, nres & 1u);
+            ring.release(g + k);
+            if (tid == 0 && k + R < Ls) ring.produce(g + k + R, Xp(t1 - k - R), a.status);
         }
         if (s == 0) {
             // t = 0: the initial states are the segment's last slice
@@ -825,9 +943,9 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
     }
     __syncthreads();
     for (int d = tid; d < D; d += blockDim.x) {
-        double g = 0.0;
-        for (int w = 0; w < nw; ++w) g += dred[d * 32 + w];
-        a.grad[(size_t)f * D + d] = g;
+        double gs = 0.0;
+        for (int w = 0; w < nw; ++w) gs += dred[d * 32 + w];
+        a.grad[(size_t)f * D + d] = gs;
     }
 }
 
@@ -839,7 +957,7 @@ template <class Mdl, int P, int REGS>
 __global__ void __maxnreg__(REGS) pf_forward_kernel(PFArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ typename Mdl::Params sprm;
-    const SmemLayout L(a.M, Mdl::DX, Mdl::D, true, Mdl::G);
+    const SmemLayout L(a.M, Mdl::DX, Mdl::D, true, Mdl::G, a.T);
     for (int f = blockIdx.x; f < a.n; f += gridDim.x) {
         forward_filter<Mdl, P>(a, f, smem, L, sprm);
         __syncthreads();
@@ -851,17 +969,15 @@ __global__ void __maxnreg__(REGS) pf_backward_kernel(PFArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ typename Mdl::Params sprm;
     constexpr int R = Mdl::DX >= 16 ? 2 : 4;  // ring_slots(DX)
-    const SmemLayout L(a.M, Mdl::DX, Mdl::D, false, Mdl::G);
-    SliceRing<R> ring;
+    const SmemLayout L(a.M, Mdl::DX, Mdl::D, false, Mdl::G, a.T);
+    SliceRing<R, Mdl::DX> ring;
     ring.slots = reinterpret_cast<float*>(smem + L.xstage);
     ring.full = reinterpret_cast<uint64_t*>(smem + L.bars);
-    ring.empty = ring.full + R;
-    ring.slice_floats = padded_particles(a.M) * Mdl::DX;
-    ring.bytes = (uint32_t)(sizeof(float) * ring.slice_floats);
+    ring.M = a.M;
     if (threadIdx.x == 0) {
         for (int r = 0; r < R; ++r) {
             mbar_init(&ring.full[r], 1);
-            mbar_init(&ring.empty[r], blockDim.x >> 5);
+            mbar_init(&ring.full[R + r], blockDim.x >> 5);
         }
         mbar_fence_init();
     }
@@ -874,30 +990,33 @@ __global__ void __maxnreg__(REGS) pf_backward_kernel(PFArgs a) {
 }
 
 // Launch one pass for a.n filters (grid = a.n CTAs, or fewer for a grid-stride launch).
+// Returns 0, -1 when the block would exceed kMaxThreads, or the cudaError_t of the launch.
 template <class Mdl, int P, int REGS>
 int launch_forward(const PFArgs& a, void* stream, int grid) {
     const int threads = pf_threads(a.M, P, Mdl::G);
-    const size_t smem = SmemLayout(a.M, Mdl::DX, Mdl::D, true, Mdl::G).total;
+    const size_t smem = SmemLayout(a.M, Mdl::DX, Mdl::D, true, Mdl::G, a.T).total;
     if (threads > kMaxThreads) return -1;
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(pf_forward_kernel<Mdl, P, REGS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
-        return -3;
+    if (smem + sizeof(typename Mdl::Params) > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(pf_forward_kernel<Mdl, P, REGS>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return (int)e;
+    }
     pf_forward_kernel<Mdl, P, REGS><<<grid, threads, smem, static_cast<cudaStream_t>(stream)>>>(a);
-    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+    return (int)cudaGetLastError();
 }
 
 template <class Mdl, int P, int REGS>
 int launch_backward(const PFArgs& a, void* stream, int grid) {
     const int threads = pf_threads(a.M, P, Mdl::G);
-    const size_t smem = SmemLayout(a.M, Mdl::DX, Mdl::D, false, Mdl::G).total;
+    const size_t smem = SmemLayout(a.M, Mdl::DX, Mdl::D, false, Mdl::G, a.T).total;
     if (threads > kMaxThreads) return -1;
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(pf_backward_kernel<Mdl, P, REGS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
-        return -3;
+    if (smem + sizeof(typename Mdl::Params) > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(pf_backward_kernel<Mdl, P, REGS>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return (int)e;
+    }
     pf_backward_kernel<Mdl, P, REGS><<<grid, threads, smem, static_cast<cudaStream_t>(stream)>>>(a);
-    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+    return (int)cudaGetLastError();
 }
 
 // The launch variants compiled for every model: (particles per thread, register cap).

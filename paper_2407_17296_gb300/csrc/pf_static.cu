@@ -150,7 +150,9 @@ extern "C" int pf_loglik_grad_static(const smc2_config* cfg, const double* theta
     // every resampling step and every checkpoint slot; only the status word starts at zero.
     int lrc = fwd(a, stream, n);
     if (!lrc && a.want_grad) lrc = bwd(a, stream, n);
-    if (lrc) return fail(SMC2_E_CUDA, std::string("filter launch failed: ") + cudaGetErrorString(cudaGetLastError()));
+    if (lrc)
+        return fail(SMC2_E_CUDA, std::string("filter launch failed: ") +
+                                     (lrc > 0 ? cudaGetErrorString((cudaError_t)lrc) : "block too large"));
     count_launches(a.want_grad ? 2 : 1);
     return SMC2_OK;
 }

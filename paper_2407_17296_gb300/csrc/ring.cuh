@@ -1,17 +1,19 @@
 // ring.cuh -- a shared-memory ring of trajectory slices filled by bulk asynchronous copies.
 //
-// The adjoint reads one slice of stored particle states (M x d_x floats, contiguous in
-// global memory) per reversed step.  Thread 0 issues cp.async.bulk copies of the next
-// R slices into R shared-memory slots; each slot has a "full" mbarrier (completed by the
-// copy's transaction count) and an "empty" mbarrier (one arrival per warp once the warp
-// has finished reading the slot).  Consumers wait on "full", the producer waits on
-// "empty" before refilling a slot.  Every wait is bounded: on expiry the thread records
-// kStatusTimeout in the caller's status word and carries on without the data, so the
-// kernel always terminates and the host sees the failure.
+// The adjoint reads one slice of stored particle states (M x d_x floats, rows padded to a
+// multiple of 4) per reversed step.  Thread 0 issues cp.async.bulk copies of the next R
+// slices into R shared-memory slots; each slot has a "full" mbarrier (completed by the
+// copy's transaction count) and an "empty" mbarrier (one arrival per warp once the warp is
+// done with the slot).  Consumers wait on "full", the producer waits on "empty" before
+// refilling a slot.  Every wait is bounded: on expiry the thread records kStatusTimeout in
+// the caller's status word and carries on without the data, so the kernel always
+// terminates and the host sees the failure.
 #pragma once
 #include <cuda_runtime.h>
 
 #include <cstdint>
+
+#include "pf_args.h"
 
 namespace smc2 {
 
@@ -72,27 +74,32 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32
 // order this thread's earlier generic-proxy global writes before later async-proxy reads
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
 
-template <int R>
+// order this thread's earlier generic-proxy shared-memory writes before later async-proxy
+// accesses of the same memory (e.g. a bulk copy that overwrites a slot it wrote into)
+__device__ __forceinline__ void fence_proxy_async_shared() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+template <int R, int DX>
 struct SliceRing {
-    float* slots;        // R x slice_floats
-    uint64_t* full;      // R
-    uint64_t* empty;     // R
-    int slice_floats;
-    uint32_t bytes;      // bulk copy size (slice rounded up to 16 bytes)
+    float* slots;        // R slots of padded_particles(M) * DX floats
+    uint64_t* full;      // R "full" barriers, then R "empty" barriers
+    int M;               // particles (slot rows, padded to a multiple of 4)
     uint32_t full_phase = 0;   // per-slot parity bits of the next "full" phase to wait for
     uint32_t empty_phase = 0;  // producer only: parity bits for "empty" waits (start "free")
     uint32_t filled = 0;       // producer only: slots that have ever been filled
 
-    __device__ float* slot(uint32_t g) const { return slots + (size_t)(g % R) * slice_floats; }
+    __device__ float* slot(uint32_t g) const { return slots + (size_t)(g % R) * padded_particles(M) * DX; }
 
-    // thread 0 only: copy `src` into the slot of slice g once every warp has released it
+    // thread 0 only: copy slice src into the slot of slice g once every warp has released it
     __device__ void produce(uint32_t g, const float* src, int* status) {
         const uint32_t s = g % R;
         if (filled & (1u << s)) {
-            if (!mbar_wait(&empty[s], (empty_phase >> s) & 1u)) atomicOr(status, kStatusTimeout);
+            if (!mbar_wait(&full[R + s], (empty_phase >> s) & 1u)) atomicOr(status, kStatusTimeout);
             empty_phase ^= 1u << s;
         }
         filled |= 1u << s;
+        const uint32_t bytes = (uint32_t)(sizeof(float) * padded_particles(M) * DX);
         mbar_arrive_expect_tx(&full[s], bytes);
         bulk_copy_g2s(slot(g), src, bytes, &full[s]);
     }
@@ -104,10 +111,10 @@ struct SliceRing {
         full_phase ^= 1u << s;
     }
 
-    // every thread: this warp is done reading slice g
+    // every thread: this warp is done with slice g
     __device__ void release(uint32_t g) {
         __syncwarp();
-        if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[g % R]);
+        if ((threadIdx.x & 31) == 0) mbar_arrive(&full[R + g % R]);
     }
 };
 
