@@ -187,6 +187,10 @@ int smc2::validate(const smc2_config* c, int* D) {
         choose_launch(c, &lc);
         if (!variant_fits(c, lc.pf, lc.rf) || !variant_fits(c, lc.pb, lc.rb))
             return fail(SMC2_E_INVAL, "M too large for this model (no launch configuration fits)");
+        const int G = model_lanes(c);
+        if (SmemLayout(c->M, c->d_x, *D, true, G).total > kSmemLimit ||
+            SmemLayout(c->M, c->d_x, *D, false, G, ring_slots(c->M, c->d_x, *D, G)).total > kSmemLimit)
+            return fail(SMC2_E_INVAL, "M too large for this model (shared memory of a filter block)");
     }
     if (c->prior_std)
         for (int d = 0; d < *D; ++d)

@@ -47,26 +47,29 @@ SMC2_HD inline int padded_particles(int M) { return (M + 3) & ~3; }
 // Rows of the ancestor tape are padded to a multiple of 8 entries (16 bytes).
 SMC2_HD inline int tape_stride(int M) { return (M + 7) & ~7; }
 
-// Slots of the adjoint's shared-memory ring of trajectory slices.
-SMC2_HD inline int ring_slots(int DX) { return DX >= 16 ? 2 : 4; }
+// Largest dynamic shared memory a block may use (227 KB opt-in, less 1 KB for the kernels'
+// static shared variables).
+constexpr size_t kSmemLimit = 227 * 1024 - 1024;
 
 // Dynamic shared-memory plan (mirrored on the host to size the launch).
 struct SmemLayout {
     size_t xstage, cs, marks, starts, red, scanw, scanwi, dred, bars, total;
-    // fwd: xstage is the gather staging; bwd: xstage is the ring of trajectory slices
-    // (ring_slots(DX) slots of padded_particles(M) * DX floats), whose first slot also
-    // serves as staging during segment recomputation
-    SMC2_HD SmemLayout(int M, int DX, int D, bool fwd, int G, int T) {
+    // fwd: xstage is the gather staging.  bwd with R > 0: xstage is the ring of trajectory
+    // slices (R slots of padded_particles(M) * DX floats), whose first slot also serves as
+    // staging during segment recomputation; with R = 0 (slices too large for two slots)
+    // xstage is a plain staging buffer of M * DX floats and slices are read from memory.
+    SMC2_HD SmemLayout(int M, int DX, int D, bool fwd, int G, int R = 0) {
         size_t o = 0;
         auto take = [&](size_t bytes) {
             const size_t r = o;
             o += (bytes + 15) & ~size_t(15);
             return r;
         };
+        const size_t Mp = (size_t)padded_particles(M);
         xstage = fwd ? take(sizeof(float) * (size_t)M * DX)
-                     : take(sizeof(float) * (size_t)padded_particles(M) * DX * ring_slots(DX));
+                     : take(sizeof(float) * Mp * DX * (R > 0 ? R : 1));
         // fwd: multinomial cumulative weights; bwd: two log-weight buffers
-        cs = fwd ? take(sizeof(float) * (size_t)M) : take(sizeof(float) * 2 * (size_t)padded_particles(M));
+        cs = fwd ? take(sizeof(float) * (size_t)M) : take(sizeof(float) * 2 * Mp);
         // fwd: range marks; bwd: two tape-row buffers
         marks = fwd ? take(sizeof(uint16_t) * (size_t)M) : take(sizeof(uint16_t) * 2 * (size_t)tape_stride(M));
         starts = fwd ? o : take(sizeof(float) * 32 * G * (DX / G + 1));  // segmented-sum scratch
@@ -74,10 +77,20 @@ struct SmemLayout {
         scanw = take(sizeof(unsigned long long) * 32);
         scanwi = take(sizeof(int) * 32);
         dred = fwd ? o : take(sizeof(double) * (size_t)D * 32);
-        bars = fwd ? o : take(sizeof(unsigned long long) * 2 * ring_slots(DX));
+        bars = fwd ? o : take(sizeof(unsigned long long) * 2 * (R > 0 ? R : 1));
         total = o;
     }
 };
+
+// Slots of the adjoint's shared-memory ring of trajectory slices: the model shape's
+// preferred count when the plan fits kSmemLimit, else its fallback (0: no ring, slices
+// read from memory).
+SMC2_HD constexpr int ring_preferred(int DX) { return DX >= 16 ? 2 : 4; }
+SMC2_HD constexpr int ring_fallback(int DX) { return DX >= 16 ? 0 : (DX >= 4 ? 2 : 4); }
+SMC2_HD inline int ring_slots(int M, int DX, int D, int G) {
+    return SmemLayout(M, DX, D, false, G, ring_preferred(DX)).total <= kSmemLimit ? ring_preferred(DX)
+                                                                                  : ring_fallback(DX);
+}
 
 // threads of a block: G lanes per chunk of P particles, rounded up to whole warps
 SMC2_HD inline int pf_threads(int M, int P, int G = 1) {

@@ -737,7 +737,8 @@ __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, cons
 
 template <class Mdl, int P, int R>
 __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, const SmemLayout& L,
-                                typename Mdl::Params& sprm, SliceRing<R, Mdl::DX>& ring, uint32_t& g) {
+                                typename Mdl::Params& sprm, SliceRing<(R > 0 ? R : 1), Mdl::DX>& ring,
+                                uint32_t& g) {
     constexpr int DX = Mdl::DX, DY = Mdl::DY, D = Mdl::D, G = Mdl::G, DL = Mdl::DL, DTH = Mdl::DTH;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     const int gl = (G > 1) ? (tid & (G - 1)) : 0;
@@ -833,9 +834,11 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
         // ordered before the bulk copies that refill the ring
         __syncthreads();
         const int Ls = t1 - t0 + 1;
-        if (tid == 0) {
-            fence_proxy_async();
-            for (int k = 0; k < R && k < Ls; ++k) ring.produce(g + k, Xp(t1 - k), a.status);
+        if constexpr (R > 0) {
+            if (tid == 0) {
+                fence_proxy_async();
+                for (int k = 0; k < R && k < Ls; ++k) ring.produce(g + k, Xp(t1 - k), a.status);
+            }
         }
         // tape row and log w_{tt-1} of step tt (which resampled) into buffer b, by
         // asynchronous copies of 16-byte chunks issued by all threads one step ahead of use
@@ -860,18 +863,30 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
 #pragma unroll
             for (int p = 0; p < P; ++p) lwbar[p] = (j0 + p < M) ? __expf(lwT[j0 + p] - LT) : 0.f;
         }
-        ring.acquire(g, a.status);
+        if constexpr (R > 0) ring.acquire(g, a.status);
         bool fl_next = t1 > t0 && resampled_before(t1);
         for (int k = 0; k < Ls - 1; ++k) {
             const int t = t1 - k;
             const bool fl = fl_next;
             fl_next = t - 1 > t0 && resampled_before(t - 1);  // loaded now, used at the end of the step
-            ring.acquire(g + k + 1, a.status);
-            float* st = ring.slot(g + k);            // x_t (then the staged cotangents)
-            const float* sp = ring.slot(g + k + 1);  // x_{t-1}
+            // x_t and x_{t-1} from the ring (then x_t's slot takes the staged cotangents), or
+            // straight from memory with a separate staging buffer when slices are too large
+            const float* sx;
+            const float* sp;
+            float* st;
+            if constexpr (R > 0) {
+                ring.acquire(g + k + 1, a.status);
+                st = ring.slot(g + k);
+                sx = st;
+                sp = ring.slot(g + k + 1);
+            } else {
+                st = xstage;
+                sx = Xp(t);
+                sp = Xp(t - 1);
+            }
             float xt[P][DL];
 #pragma unroll
-            for (int p = 0; p < P; ++p) read_staged<DX, DL>(st, min(j0 + p, M - 1), gl, xt[p]);
+            for (int p = 0; p < P; ++p) read_staged<DX, DL>(sx, min(j0 + p, M - 1), gl, xt[p]);
             const float* yt = a.y + (size_t)(t - 1) * DY + (G > 1 ? gl * DL : 0);
             // padding particles have zero cotangents and finite (clamped) states: no guards
 #pragma unroll
@@ -916,12 +931,16 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
             }
             // the next resampling step's buffer was last read before this step's barrier
             if (fl_next) prefetch(t - 1, nres & 1u);
-            ring.release(g + k);
-            if (tid == 0 && k + R < Ls) ring.produce(g + k + R, Xp(t1 - k - R), a.status);
+            if constexpr (R > 0) {
+                ring.release(g + k);
+                if (tid == 0 && k + R < Ls) ring.produce(g + k + R, Xp(t1 - k - R), a.status);
+            }
         }
         if (s == 0) {
             // t = 0: the initial states are the segment's last slice
-            const float* s0 = ring.slot(g + Ls - 1);
+            const float* s0;
+            if constexpr (R > 0) s0 = ring.slot(g + Ls - 1);
+            else s0 = Xp(t0);
 #pragma unroll
             for (int p = 0; p < P; ++p) {
                 float x0[DL];
@@ -929,7 +948,7 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
                 if (j0 + p < M) Mdl::bwd_init(prm, x0, xbar[p], thb);
             }
         }
-        ring.release(g + Ls - 1);
+        if constexpr (R > 0) ring.release(g + Ls - 1);
         g += Ls;
     }
     // gradient: FP64 block sum of the per-thread FP32 partials (lanes of equal gl hold the
@@ -957,29 +976,28 @@ template <class Mdl, int P, int REGS>
 __global__ void __maxnreg__(REGS) pf_forward_kernel(PFArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ typename Mdl::Params sprm;
-    const SmemLayout L(a.M, Mdl::DX, Mdl::D, true, Mdl::G, a.T);
+    const SmemLayout L(a.M, Mdl::DX, Mdl::D, true, Mdl::G);
     for (int f = blockIdx.x; f < a.n; f += gridDim.x) {
         forward_filter<Mdl, P>(a, f, smem, L, sprm);
         __syncthreads();
     }
 }
 
-template <class Mdl, int P, int REGS>
-__global__ void __maxnreg__(REGS) pf_backward_kernel(PFArgs a) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ typename Mdl::Params sprm;
-    constexpr int R = Mdl::DX >= 16 ? 2 : 4;  // ring_slots(DX)
-    const SmemLayout L(a.M, Mdl::DX, Mdl::D, false, Mdl::G, a.T);
-    SliceRing<R, Mdl::DX> ring;
+template <class Mdl, int P, int R>
+__device__ void backward_all(const PFArgs& a, unsigned char* smem, typename Mdl::Params& sprm) {
+    const SmemLayout L(a.M, Mdl::DX, Mdl::D, false, Mdl::G, R);
+    SliceRing<(R > 0 ? R : 1), Mdl::DX> ring;
     ring.slots = reinterpret_cast<float*>(smem + L.xstage);
     ring.full = reinterpret_cast<uint64_t*>(smem + L.bars);
     ring.M = a.M;
-    if (threadIdx.x == 0) {
-        for (int r = 0; r < R; ++r) {
-            mbar_init(&ring.full[r], 1);
-            mbar_init(&ring.full[R + r], blockDim.x >> 5);
+    if constexpr (R > 0) {
+        if (threadIdx.x == 0) {
+            for (int r = 0; r < R; ++r) {
+                mbar_init(&ring.full[r], 1);
+                mbar_init(&ring.full[R + r], blockDim.x >> 5);
+            }
+            mbar_fence_init();
         }
-        mbar_fence_init();
     }
     __syncthreads();
     uint32_t g = 0;
@@ -989,12 +1007,25 @@ __global__ void __maxnreg__(REGS) pf_backward_kernel(PFArgs a) {
     }
 }
 
+template <class Mdl, int P, int REGS>
+__global__ void __maxnreg__(REGS) pf_backward_kernel(PFArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ typename Mdl::Params sprm;
+    constexpr int Ra = ring_preferred(Mdl::DX), Rb = ring_fallback(Mdl::DX);
+    if constexpr (Ra == Rb) {
+        backward_all<Mdl, P, Ra>(a, smem, sprm);
+    } else {
+        if (ring_slots(a.M, Mdl::DX, Mdl::D, Mdl::G) == Ra) backward_all<Mdl, P, Ra>(a, smem, sprm);
+        else backward_all<Mdl, P, Rb>(a, smem, sprm);
+    }
+}
+
 // Launch one pass for a.n filters (grid = a.n CTAs, or fewer for a grid-stride launch).
 // Returns 0, -1 when the block would exceed kMaxThreads, or the cudaError_t of the launch.
 template <class Mdl, int P, int REGS>
 int launch_forward(const PFArgs& a, void* stream, int grid) {
     const int threads = pf_threads(a.M, P, Mdl::G);
-    const size_t smem = SmemLayout(a.M, Mdl::DX, Mdl::D, true, Mdl::G, a.T).total;
+    const size_t smem = SmemLayout(a.M, Mdl::DX, Mdl::D, true, Mdl::G).total;
     if (threads > kMaxThreads) return -1;
     if (smem + sizeof(typename Mdl::Params) > 48 * 1024) {
         const cudaError_t e = cudaFuncSetAttribute(pf_forward_kernel<Mdl, P, REGS>,
@@ -1008,7 +1039,8 @@ int launch_forward(const PFArgs& a, void* stream, int grid) {
 template <class Mdl, int P, int REGS>
 int launch_backward(const PFArgs& a, void* stream, int grid) {
     const int threads = pf_threads(a.M, P, Mdl::G);
-    const size_t smem = SmemLayout(a.M, Mdl::DX, Mdl::D, false, Mdl::G, a.T).total;
+    const int R = ring_slots(a.M, Mdl::DX, Mdl::D, Mdl::G);
+    const size_t smem = SmemLayout(a.M, Mdl::DX, Mdl::D, false, Mdl::G, R).total;
     if (threads > kMaxThreads) return -1;
     if (smem + sizeof(typename Mdl::Params) > 48 * 1024) {
         const cudaError_t e = cudaFuncSetAttribute(pf_backward_kernel<Mdl, P, REGS>,

@@ -93,3 +93,18 @@ def test_server_rejects_bad_arguments_without_device(lib):
     s = ctypes.c_void_p()
     assert lib.smc2_server_create(0, 1, ctypes.byref(s)) == -1
     assert lib.smc2_server_create(1 << 30, 0, ctypes.byref(s)) == -1
+
+
+@pytest.mark.parametrize("M,ok", [(1024, True), (2048, True), (3000, False), (4096, False)])
+def test_shared_memory_limit_of_the_16_dim_model(lib, M, ok):
+    """A 16-dimensional filter block holds M x 16 staged states: M = 2048 fits (the adjoint
+    then reads slices from memory instead of a ring), M = 3000 does not and is refused."""
+    from paper_2407_17296_gb300 import binding, workloads
+    w = workloads.lg16(T=20, N=4, M=M)
+    c = binding.config_for(w)
+    b = ctypes.c_size_t(0)
+    rc = lib.smc2_footprint(ctypes.byref(c), ctypes.byref(b))
+    if ok:
+        assert rc == 0 and b.value > 0
+    else:
+        assert rc == -1 and "too large" in binding.last_error()

@@ -183,3 +183,15 @@ def test_autograd_function():
         (ll * wts).sum().backward()
         np.testing.assert_array_equal(ll.detach().cpu().numpy(), ll_ref)
         np.testing.assert_allclose(th.grad.cpu().numpy(), g_ref * np.arange(1, 5)[:, None], rtol=1e-12)
+
+
+@pytest.mark.parametrize("make,M,n", [(W.lg16, 2048, 2), (W.lg4, 4096, 2)])
+def test_parity_large_blocks(make, M, n):
+    """Block sizes whose adjoint cannot keep four (or two) state slices in shared memory:
+    the 4-d model with M = 4096 runs a two-slot ring, the 16-d model with M = 2048 reads the
+    slices from memory."""
+    w = make(T=12, N=n, M=M)
+    theta = W.thetas_near(w, n, 0.03, seed=31)
+    for scheme in (0, 1):
+        ll, g, anc, flag = gpu_pf(w, theta, pf_resample=scheme)
+        check_rows(w, theta, ll, g, anc, flag, range(n), scheme=scheme)
