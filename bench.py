@@ -351,7 +351,7 @@ def run_reference(a, rank, world):
 
 def run_serve(a):
     """256 jobs of the four model families with T ~ U[50, 1000], N in {256, 1024, 4096},
-    M in {128, 512, 2048} (M <= 1024 for the 16-dimensional model), Poisson arrivals.
+    M in {128, 512, 2048}, Poisson arrivals.
     1. capacity: all jobs submitted at once to the batched server;
     2. arrivals at serve_load x capacity, batched (up to 16 jobs in flight) and serial
        (one job at a time, the same arrival times): p50/p99 job latency and throughput."""
@@ -365,8 +365,7 @@ def run_serve(a):
     stream = workloads.serving_stream(n_jobs=a.serve_jobs, rate_hz=1.0)
     jobs = []
     for t, wl in stream:
-        M = min(wl.M, 1024) if wl.name == "lg16" else wl.M
-        jobs.append((t, replace(wl, K=a.serve_iters, M=M)))
+        jobs.append((t, replace(wl, K=a.serve_iters)))
     work = [wl.N * wl.M * wl.T * wl.K for _, wl in jobs]
     free, _ = torch.cuda.mem_get_info()
     budget = int(0.8 * free)
