@@ -49,6 +49,8 @@ def _args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--N", type=int, default=0, help="override the number of samples (profiling runs)")
     p.add_argument("--no-autotune", action="store_true", help="use the default launch configuration")
+    p.add_argument("--launch", default=None,
+                   help="pin the launch instead of tuning: fwd_ppt,fwd_regs,adj_ppt,adj_regs,ckpt")
     p.add_argument("--serve", action="store_true",
                    help="serving workload: Poisson-arriving jobs, batched server vs one job at a time")
     p.add_argument("--serve-jobs", type=int, default=256)
@@ -179,7 +181,9 @@ def run_gpu(a, rank, world, local):
     binding.load()
     stream = torch.cuda.Stream(device=dev)
     cfg = binding.config_for(w, stream=stream.cuda_stream)
-    if not a.no_autotune:
+    if a.launch:
+        binding.set_launch(cfg, [int(v) for v in a.launch.split(",")])
+    elif not a.no_autotune:
         # tune on parameters near the data-generating ones: the steady state of the sampler
         binding.autotune(cfg, workloads.thetas_near(w, w.N, 0.05, seed=5))
     h = binding.Handle(cfg)

@@ -234,6 +234,13 @@ int smc2_autotune(const smc2_config* cfg, const double* theta_host, int* ppt, in
  * register cap, adjoint particles per thread, adjoint register cap, checkpoint interval. */
 int smc2_get_launch(const smc2_handle* h, int* out);
 
+/* Pin the launch choice for cfg's shape (the key smc2_autotune caches under: device,
+ * family, d_x, d_y, M, N, T, resampling scheme), in the layout of smc2_get_launch, for
+ * handles created afterwards.  No device work.  SMC2_E_INVAL if no compiled kernel variant
+ * has those particles per thread and register cap for this shape, or the checkpoint
+ * interval is outside [1, T]. */
+int smc2_set_launch(const smc2_config* cfg, const int* launch);
+
 /* Number of kernels this library launched since load (a device-work counter). */
 uint64_t smc2_kernel_launches(void);
 

@@ -23,7 +23,7 @@ SYSTEMATIC, MULTINOMIAL = 0, 1
 EXPORTS = ("smc2_config_init", "smc2_create", "pf_loglik_grad", "pf_loglik_grad_rows",
            "pf_loglik_grad_host", "smc2_step", "smc2_step_filters", "smc2_step_update", "smc2_get_samples", "smc2_get_state",
            "smc2_get_trace", "smc2_set_observations", "smc2_footprint", "smc2_destroy",
-           "smc2_autotune", "smc2_get_launch", "smc2_get_status", "smc2_kernel_launches", "smc2_last_error", "smc2_server_create",
+           "smc2_autotune", "smc2_get_launch", "smc2_set_launch", "smc2_get_status", "smc2_kernel_launches", "smc2_last_error", "smc2_server_create",
            "smc2_submit", "smc2_poll", "smc2_cancel", "smc2_server_destroy",
            "pf_loglik_grad_static")
 
@@ -113,6 +113,7 @@ def load(path: str = LIB_PATH):
         "smc2_autotune": (ctypes.c_int, [ctypes.POINTER(Config), dp, ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int)]),
         "smc2_get_launch": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int)]),
+        "smc2_set_launch": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_int)]),
         "smc2_get_status": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
         "smc2_kernel_launches": (u64, []),
         "smc2_last_error": (ctypes.c_char_p, []),
@@ -374,6 +375,13 @@ def autotune(cfg: Config, theta=None):
     check(load().smc2_autotune(ctypes.byref(cfg), _ptr(th), ctypes.byref(ppt), ctypes.byref(kc)),
           "smc2_autotune")
     return ppt.value, kc.value
+
+
+def set_launch(cfg: Config, launch):
+    """Pin (forward ppt, forward regs, adjoint ppt, adjoint regs, checkpoint interval) for
+    cfg's shape; handles created afterwards use it."""
+    arr = (ctypes.c_int * 5)(*[int(v) for v in launch])
+    check(load().smc2_set_launch(ctypes.byref(cfg), arr), "smc2_set_launch")
 
 
 def footprint(cfg: Config) -> int:

@@ -334,6 +334,25 @@ bool smc2::tuned_launch(const smc2_config* c, LaunchChoice* lc) {
     return true;
 }
 
+extern "C" int smc2_set_launch(const smc2_config* cfg, const int* launch) {
+    int D = 0;
+    int rc = validate(cfg, &D);
+    if (rc) return rc;
+    if (!launch) return fail(SMC2_E_INVAL, "launch is NULL");
+    LaunchChoice lc;
+    lc.pf = launch[0];
+    lc.rf = launch[1];
+    lc.pb = launch[2];
+    lc.rb = launch[3];
+    lc.kc = launch[4];
+    if (!lookup_forward(cfg, lc.pf, lc.rf) || !lookup_backward(cfg, lc.pb, lc.rb))
+        return fail(SMC2_E_INVAL, "no compiled kernel variant fits this launch for cfg's shape");
+    if (lc.kc < 1 || lc.kc > cfg->T) return fail(SMC2_E_INVAL, "checkpoint interval must be in [1, T]");
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[tune_key(cfg)] = lc;
+    return SMC2_OK;
+}
+
 extern "C" int smc2_autotune(const smc2_config* cfg, const double* theta_host, int* ppt, int* ckpt) {
     int D = 0;
     int rc = validate(cfg, &D);

@@ -108,3 +108,13 @@ def test_shared_memory_limit_of_the_16_dim_model(lib, M, ok):
         assert rc == 0 and b.value > 0
     else:
         assert rc == -1 and "too large" in binding.last_error()
+
+
+def test_set_launch_validates_without_device(lib):
+    from paper_2407_17296_gb300 import binding, workloads
+    c = binding.config_for(workloads.lg4(T=20, N=4, M=256))
+    with pytest.raises(binding.Smc2Error):
+        binding.set_launch(c, [3, 64, 2, 64, 1])    # no 3-particle variant
+    with pytest.raises(binding.Smc2Error):
+        binding.set_launch(c, [2, 64, 2, 64, 0])    # checkpoint interval outside [1, T]
+    binding.set_launch(c, [2, 64, 4, 128, 5])
