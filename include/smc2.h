@@ -131,6 +131,14 @@ int pf_loglik_grad_host(smc2_handle* h, const double* theta_host, int n, uint32_
  */
 int smc2_step(smc2_handle* h, smc2_stats* out);
 
+/* Filter-pass timing.  With timing on, smc2_step launches its kernels one by one (not as
+ * the replayed step graph) and records CUDA events on the handle's stream around the
+ * forward and adjoint passes; smc2_get_step_timing then returns their device time for
+ * the last step: ms[0] forward, ms[1] adjoint (waits for those passes to finish).
+ * SMC2_E_INVAL if the last smc2_step ran with timing off. */
+int smc2_set_step_timing(smc2_handle* h, int on);
+int smc2_get_step_timing(smc2_handle* h, float* ms);
+
 /*
  * One SMC^2 iteration split in two calls, for a job whose N particle filters are spread
  * over several devices or processes (the filters of an iteration are independent: the

@@ -21,7 +21,7 @@ SYSTEMATIC, MULTINOMIAL = 0, 1
 
 # every symbol include/smc2.h declares
 EXPORTS = ("smc2_config_init", "smc2_create", "pf_loglik_grad", "pf_loglik_grad_rows",
-           "pf_loglik_grad_host", "smc2_step", "smc2_step_filters", "smc2_step_update", "smc2_get_samples", "smc2_get_state",
+           "pf_loglik_grad_host", "smc2_step", "smc2_step_filters", "smc2_step_update", "smc2_set_step_timing", "smc2_get_step_timing", "smc2_get_samples", "smc2_get_state",
            "smc2_get_trace", "smc2_set_observations", "smc2_footprint", "smc2_destroy",
            "smc2_autotune", "smc2_get_launch", "smc2_set_launch", "smc2_get_status", "smc2_kernel_launches", "smc2_last_error", "smc2_server_create",
            "smc2_submit", "smc2_poll", "smc2_cancel", "smc2_server_destroy",
@@ -103,6 +103,8 @@ def load(path: str = LIB_PATH):
         "pf_loglik_grad_host": (ctypes.c_int, [vp, dp, ctypes.c_int, u32, dp, dp]),
         "smc2_step": (ctypes.c_int, [vp, ctypes.POINTER(Stats)]),
         "smc2_step_filters": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, dp, dp]),
+        "smc2_set_step_timing": (ctypes.c_int, [vp, ctypes.c_int]),
+        "smc2_get_step_timing": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_float)]),
         "smc2_step_update": (ctypes.c_int, [vp, dp, dp, ctypes.POINTER(Stats)]),
         "smc2_get_samples": (ctypes.c_int, [vp, dp, dp]),
         "smc2_get_state": (ctypes.c_int, [vp, dp, dp]),
@@ -253,6 +255,15 @@ class Handle:
         check(self.lib.smc2_step(self.h, ctypes.byref(st)), "smc2_step")
         return {"k": st.k, "resampled": bool(st.resampled), "ess": st.ess, "l_k": st.l_k,
                 "max_logw": st.max_logw, "mean": mean, "recycled_mean": rec}
+
+    def set_step_timing(self, on=True):
+        check(self.lib.smc2_set_step_timing(self.h, 1 if on else 0), "smc2_set_step_timing")
+
+    def step_timing(self):
+        """(forward ms, adjoint ms) of the filter passes of the last step (device events)."""
+        ms = (ctypes.c_float * 2)()
+        check(self.lib.smc2_get_step_timing(self.h, ms), "smc2_get_step_timing")
+        return float(ms[0]), float(ms[1])
 
     def step_filters(self, row0, n, loglik, grad):
         """Propose for all N samples and run the filters of rows row0 .. row0+n-1 into the

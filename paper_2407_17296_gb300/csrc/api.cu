@@ -236,6 +236,8 @@ static void free_handle_memory(smc2_handle* h) {
     if (h->h_stats) cudaFreeHost(h->h_stats);
     if (h->h_status) cudaFreeHost(h->h_status);
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    for (cudaEvent_t e : h->ev)
+        if (e) cudaEventDestroy(e);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
@@ -276,6 +278,8 @@ extern "C" int smc2_create(const smc2_config* cfg, smc2_handle** out) {
             return cleanup(SMC2_E_CUDA, "cudaStreamCreate failed");
         h->own_stream = true;
     }
+    for (cudaEvent_t& e : h->ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return cleanup(SMC2_E_CUDA, "cudaEventCreate failed");
     const size_t N = cfg->N, T = cfg->T;
     struct Alloc { void** p; size_t bytes; };
     Alloc allocs[] = {
@@ -399,13 +403,17 @@ PFArgs smc2::make_pf_args(smc2_handle* h, const double* theta, int n, uint32_t i
     return a;
 }
 
-int smc2::launch_filters(smc2_handle* h, const PFArgs& a) {
+int smc2::launch_filters(smc2_handle* h, const PFArgs& a, bool timed) {
+    // timed: bracket the passes with the handle's events (eager launches only)
+    if (timed) cudaEventRecord(h->ev[0], h->stream);
     int rc = h->fwd(a, h->stream, a.n);
     const char* pass = "forward";
+    if (timed && !rc) cudaEventRecord(h->ev[1], h->stream);
     if (!rc && a.want_grad) {
         rc = h->bwd(a, h->stream, a.n);
         pass = "adjoint";
     }
+    if (timed && !rc) cudaEventRecord(h->ev[2], h->stream);
     if (rc)
         return fail(SMC2_E_CUDA, std::string(pass) + " filter launch failed: " +
                                      (rc > 0 ? cudaGetErrorString((cudaError_t)rc) : "block too large"));
@@ -489,7 +497,7 @@ int smc2::enqueue_step(smc2_handle* h) {
     const OuterArgs o = make_outer_args(h);
     if (launch_outer_propose(o, h->stream)) return fail(SMC2_E_CUDA, "outer propose launch failed");
     const PFArgs a = make_pf_args(h, h->theta_new, h->cfg.N, 0u, 0u, h->k_dev, h->ll_new, h->grad_new);
-    int rc = launch_filters(h, a);
+    int rc = launch_filters(h, a, h->timing);
     if (rc) return rc;
     if (launch_outer_update(o, h->stream)) return fail(SMC2_E_CUDA, "outer update launch failed");
     count_launches(2);
@@ -498,7 +506,7 @@ int smc2::enqueue_step(smc2_handle* h) {
 
 int smc2::step_async(smc2_handle* h) {
     // first iteration eagerly (sets kernel attributes); later ones replay a captured graph
-    if (h->k >= 1 && !h->graph_exec && !h->no_graph) {
+    if (h->k >= 1 && !h->graph_exec && !h->no_graph && !h->timing) {
         cudaGraph_t g = nullptr;
         CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
         const uint64_t before = g_launches.load();
@@ -520,7 +528,7 @@ int smc2::step_async(smc2_handle* h) {
             }
         }
     }
-    if (h->graph_exec) {
+    if (h->graph_exec && !h->timing) {
         CUDA_TRY(cudaGraphLaunch(h->graph_exec, h->stream));
         count_launches(4);
     } else {
@@ -528,6 +536,22 @@ int smc2::step_async(smc2_handle* h) {
         if (rc) return rc;
     }
     h->k += 1;
+    h->ev_recorded = h->timing;
+    return SMC2_OK;
+}
+
+extern "C" int smc2_set_step_timing(smc2_handle* h, int on) {
+    if (!h) return fail(SMC2_E_INVAL, "handle is NULL");
+    h->timing = on != 0;
+    return SMC2_OK;
+}
+
+extern "C" int smc2_get_step_timing(smc2_handle* h, float* ms) {
+    if (!h || !ms) return fail(SMC2_E_INVAL, "NULL argument");
+    if (!h->ev_recorded) return fail(SMC2_E_INVAL, "the last smc2_step did not record its filter timing");
+    CUDA_TRY(cudaEventSynchronize(h->ev[2]));
+    CUDA_TRY(cudaEventElapsedTime(&ms[0], h->ev[0], h->ev[1]));
+    CUDA_TRY(cudaEventElapsedTime(&ms[1], h->ev[1], h->ev[2]));
     return SMC2_OK;
 }
 
@@ -637,6 +661,8 @@ extern "C" int smc2_get_trace(smc2_handle* h, uint16_t* pf_anc, uint8_t* pf_flag
         *outer_resampled = r != 0.0;
     }
     CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (pf_flag)  // the device flags carry a gather-adjoint hint in bit 1
+        for (size_t i = 0; i < N * T; ++i) pf_flag[i] &= 1u;
     return SMC2_OK;
 }
 

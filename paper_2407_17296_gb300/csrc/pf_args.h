@@ -53,7 +53,7 @@ constexpr size_t kSmemLimit = 227 * 1024 - 1024;
 
 // Dynamic shared-memory plan (mirrored on the host to size the launch).
 struct SmemLayout {
-    size_t xstage, cs, marks, starts, red, scanw, scanwi, dred, bars, total;
+    size_t xstage, cs, marks, starts, red, scanw, scanwi, misc, dred, bars, total;
     // fwd: xstage is the gather staging.  bwd with R > 0: xstage is the ring of trajectory
     // slices (R slots of padded_particles(M) * DX floats), whose first slot also serves as
     // staging during segment recomputation; with R = 0 (slices too large for two slots)
@@ -76,6 +76,7 @@ struct SmemLayout {
         red = take(sizeof(float4) * (2 * 32 + 2));  // two buffers of per-warp partials + results
         scanw = take(sizeof(unsigned long long) * 32);
         scanwi = take(sizeof(int) * 32);
+        misc = take(16);  // fwd: largest offspring count of a resampling step
         dred = fwd ? o : take(sizeof(double) * (size_t)D * 32);
         bars = fwd ? o : take(sizeof(unsigned long long) * 2 * (R > 0 ? R : 1));
         total = o;

@@ -47,6 +47,8 @@
 namespace smc2 {
 
 constexpr int kMaxThreads = 1024;
+// largest offspring count of one parent for which the adjoint walks offspring runs
+constexpr int kWalkMaxOffspring = 16;
 constexpr unsigned kFull = 0xffffffffu;
 
 // ---------------------------------------------------------------- block primitives
@@ -184,11 +186,12 @@ __device__ __forceinline__ void block_fixed_scan(const float (&lw)[P], bool lead
 template <int P, int G>
 __device__ __forceinline__ void systematic_ancestors(const float (&lw)[P], bool lead, int j0, int M, float nu,
                                                      uint16_t* marks, unsigned long long* scanw,
-                                                     int* scanwi, int (&anc)[P]) {
+                                                     int* scanwi, int* maxoff, int (&anc)[P], int& max_offspring) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int p = 0; p < P; ++p)
         if (lead && j0 + p < M) marks[j0 + p] = 0;
+    if (threadIdx.x == 0) *maxoff = 0;
     unsigned long long s[P], base, tot;
     block_fixed_scan<P, G>(lw, lead, j0, M, scanw, s, base, tot);
     const float scale = (float)M / u64_to_float_rz(tot);
@@ -197,15 +200,19 @@ __device__ __forceinline__ void systematic_ancestors(const float (&lw)[P], bool 
         const int n = (int)floorf(cm) + 1;
         return min(max(n, 0), M);
     };
-    int lo = count_le(base);
+    int lo = count_le(base), off = 0;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         const int j = j0 + p;
         const int hi = (j == M - 1) ? M : count_le(base + s[p]);
         if (lead && j < M && hi > lo) marks[lo] = (uint16_t)(j + 1);
+        off = max(off, hi - lo);
         lo = hi;
     }
+    off = __reduce_max_sync(kFull, off);
+    if (lane == 0) atomicMax(maxoff, off);
     __syncthreads();
+    max_offspring = *maxoff;  // read before the barrier below; rewritten only at the next call
     int r = 0, rr[P];
 #pragma unroll
     for (int p = 0; p < P; ++p) {
@@ -616,6 +623,7 @@ __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, cons
     float4* red = reinterpret_cast<float4*>(smem + L.red);
     unsigned long long* scanw = reinterpret_cast<unsigned long long*>(smem + L.scanw);
     int* scanwi = reinterpret_cast<int*>(smem + L.scanwi);
+    int* maxoff = reinterpret_cast<int*>(smem + L.misc);
 
     if (tid == 0) Mdl::make_params(a.theta + (size_t)f * a.D, a.H, sprm);
     __syncthreads();
@@ -639,18 +647,6 @@ __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, cons
     }
     const float logM = logf((float)M);
     float Lprev = logM;
-    // log p-hat = sum_t (m_t + log s1_t - L_{t-1}) accumulated in FP64.  The FP32 terms of
-    // step t are parked in lane t mod 32 (three selects a step); every 32 steps, and at the
-    // end, warp 0 adds the parked terms to per-lane FP64 partials, which are combined once
-    // per filter.  FP64 work is thus 1/32 of the steps and confined to one warp.
-    const int lane = tid & 31;
-    const bool warp0 = tid < 32;
-    double acc = 0.0;
-    float pm = 0.f, pl = 0.f, pp = 0.f;
-    auto flush = [&]() {
-        if (warp0) acc += ((double)pm + (double)pl) - (double)pp;
-        pm = pl = pp = 0.f;
-    };
     bool resample = false, dead = false;
     if (store) {
         store_state<P, DX, DL>(tr.x_ck(0), tr.lw_ck(0), j0, gl, M, x, lw);
@@ -660,12 +656,14 @@ __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, cons
         }
     }
     for (int t = 1; t <= T; ++t) {
+        int max_offspring = 0;
         if (resample) {
             stage_x<P, DX, DL>(xstage, j0, gl, M, x);
             int anc[P];
             if (a.scheme == 0) {
                 const uint4 w = philox4x32_10(make_uint4((uint32_t)t, 0u, kStreamResample, 0u), key);
-                systematic_ancestors<P, G>(lw, lead, j0, M, u01_open(w.x), marks, scanw, scanwi, anc);
+                systematic_ancestors<P, G>(lw, lead, j0, M, u01_open(w.x), marks, scanw, scanwi, maxoff, anc,
+                                           max_offspring);
             } else {
                 multinomial_ancestors<P, G>(lw, lead, j0, M, key, (uint32_t)t, cs, scanw, anc);
             }
@@ -682,7 +680,11 @@ __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, cons
             }
             Lprev = logM;
         }
-        if (tid == 0 && a.flag) a.flag[(size_t)f * T + (t - 1)] = resample ? 1 : 0;
+        // flag bit 0: resampled before step t; bit 1: some parent got more than
+        // kWalkMaxOffspring offspring (the adjoint then uses the balanced gather adjoint)
+        if (tid == 0)
+            a.flag[(size_t)f * T + (t - 1)] =
+                resample ? (uint8_t)(1 | (max_offspring > kWalkMaxOffspring ? 2 : 0)) : (uint8_t)0;
 
         {
             float eps[P * DL];
@@ -703,21 +705,15 @@ __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, cons
             break;
         }
         const float ls1 = logf(s1);
-        if (lane == (t & 31)) {
-            pm = m;
-            pl = ls1;
-            pp = Lprev;
-        }
-        if ((t & 31) == 31) flush();
 #pragma unroll
         for (int p = 0; p < P; ++p) lw[p] -= m;
         Lprev = ls1;
         resample = (t < T) && (s1 * s1 < a.ess_frac * (float)M * s2);
+        if (tid == 0) {  // per-step scalars: the adjoint's and the log-likelihood sum's inputs
+            a.mstep[(size_t)f * (T + 1) + t] = m;
+            a.lstep[(size_t)f * (T + 1) + t] = ls1;
+        }
         if (store) {
-            if (tid == 0) {
-                a.mstep[(size_t)f * (T + 1) + t] = m;
-                a.lstep[(size_t)f * (T + 1) + t] = ls1;
-            }
             // with kc = 1 the adjoint reads log w only at steps followed by resampling and at T
             if (a.kc == 1)
                 store_state<P, DX, DL>(tr.x_ck(t), (resample || t == T) ? tr.lw_ck(t) : nullptr, j0, gl, M, x, lw);
@@ -725,8 +721,19 @@ __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, cons
                 store_state<P, DX, DL>(tr.x_ck(t / a.kc), tr.lw_ck(t / a.kc), j0, gl, M, x, lw);
         }
     }
-    flush();
-    if (warp0) {
+    // log p-hat = sum_t (m_t + log s1_t - L_{t-1}) accumulated in FP64 by warp 0 from the
+    // FP32 per-step terms its lane 0 wrote (L_{t-1} = log M at t = 1 and after resampling)
+    if (tid < 32) {
+        __syncwarp();
+        const float* ms = a.mstep + (size_t)f * (T + 1);
+        const float* ls = a.lstep + (size_t)f * (T + 1);
+        const uint8_t* fl = a.flag + (size_t)f * T;
+        double acc = 0.0;
+        if (!dead)
+            for (int t = 1 + (tid & 31); t <= T; t += 32) {
+                const float Lp = (t == 1 || fl[t - 1]) ? logM : ls[t - 1];
+                acc += ((double)ms[t] + (double)ls[t]) - (double)Lp;
+            }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
         if (tid == 0) a.loglik[f] = dead ? -INFINITY : acc;
@@ -756,7 +763,7 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
         return;
     }
     const uint8_t* flags = a.flag + (size_t)f * T;  // flags[t-1]: resampled before step t
-    auto resampled_before = [&](int t) -> bool { return flags[t - 1] != 0; };
+    auto resampled_before = [&](int t) -> bool { return (flags[t - 1] & 1) != 0; };
     if (tid == 0) Mdl::make_params(a.theta + (size_t)f * a.D, a.H, sprm);
     __syncthreads();
     typename Mdl::LaneParams prm;
@@ -864,11 +871,13 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
             for (int p = 0; p < P; ++p) lwbar[p] = (j0 + p < M) ? __expf(lwT[j0 + p] - LT) : 0.f;
         }
         if constexpr (R > 0) ring.acquire(g, a.status);
-        bool fl_next = t1 > t0 && resampled_before(t1);
+        uint8_t fb_next = t1 > t0 ? flags[t1 - 1] : (uint8_t)0;
         for (int k = 0; k < Ls - 1; ++k) {
             const int t = t1 - k;
-            const bool fl = fl_next;
-            fl_next = t - 1 > t0 && resampled_before(t - 1);  // loaded now, used at the end of the step
+            const uint8_t fb = fb_next;
+            const bool fl = fb != 0;
+            fb_next = t - 1 > t0 ? flags[t - 2] : (uint8_t)0;  // loaded now, used at the end of the step
+            const bool fl_next = fb_next != 0;
             // x_t and x_{t-1} from the ring (then x_t's slot takes the staged cotangents), or
             // straight from memory with a separate staging buffer when slices are too large
             const float* sx;
@@ -916,7 +925,7 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
                 // offspring, staged in the rows of x_t (each thread has read its own)
                 if (a.scheme != 0)
                     gather_adjoint_scatter<P, DX, DL, G>(xbar, ai, j0, gl, M, st);
-                else if (kGatherWalk<G, DX>)
+                else if (kGatherWalk<G, DX> && !(fb & 2))
                     gather_adjoint_runs<P, DX, DL, G>(xbar, j0, gl, M, ancs, st);
                 else
                     gather_adjoint_segmented<P, DX, DL, G>(xbar, ai, j0, gl, M, ancs, st, segw);

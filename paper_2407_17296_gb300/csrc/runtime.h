@@ -62,6 +62,9 @@ struct smc2_handle {
     double* h_stats = nullptr;  // pinned
     uint32_t k = 0;             // iterations enqueued
     cudaGraphExec_t graph_exec = nullptr;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // around the filter passes of a step
+    bool timing = false;       // steps run eagerly with the events recorded
+    bool ev_recorded = false;  // the last step recorded them
     bool no_graph = false;
     bool split_pending = false;  // smc2_step_filters issued, smc2_step_update not yet
     int launches_per_step = 0;
@@ -70,7 +73,7 @@ struct smc2_handle {
 namespace smc2 {
 PFArgs make_pf_args(smc2_handle* h, const double* theta, int n, uint32_t iter, uint32_t row0,
                     const uint32_t* iter_dev, double* loglik, double* grad);
-int launch_filters(smc2_handle* h, const PFArgs& a);
+int launch_filters(smc2_handle* h, const PFArgs& a, bool timed = false);
 OuterArgs make_outer_args(smc2_handle* h);
 int enqueue_step(smc2_handle* h);
 int step_async(smc2_handle* h);
