@@ -167,17 +167,17 @@ __global__ void __launch_bounds__(kOuterThreads) outer_update_kernel(OuterArgs a
     }
     __syncthreads();
 
-    // 2. normalise, ESS, estimate, recycling statistic
+    // 2. normalise, ESS, estimate, recycling statistic; the unnormalised weights
+    //    w_i = exp(log w_i - max) are evaluated once into csum (free until the resampling scan)
     double lmax = -INFINITY;
     for (int i = tid; i < N; i += nt) lmax = fmax(lmax, a.logw[i]);
     lmax = block_max_d(lmax, red);
     double s1 = 0.0, s2 = 0.0;
-    if (lmax > -INFINITY) {
-        for (int i = tid; i < N; i += nt) {
-            const double e = exp(a.logw[i] - lmax);
-            s1 += e;
-            s2 += e * e;
-        }
+    for (int i = tid; i < N; i += nt) {
+        const double e = (lmax > -INFINITY) ? exp(a.logw[i] - lmax) : 0.0;
+        csum[i] = e;
+        s1 += e;
+        s2 += e * e;
     }
     s1 = block_sum_d(s1, red);
     s2 = block_sum_d(s2, red);
@@ -189,8 +189,7 @@ __global__ void __launch_bounds__(kOuterThreads) outer_update_kernel(OuterArgs a
         const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
         for (int d = wid; d < D; d += nw) {
             double acc = 0.0;
-            if (lmax > -INFINITY)
-                for (int i = lane; i < N; i += 32) acc += exp(a.logw[i] - lmax) * a.theta[(size_t)i * D + d];
+            for (int i = lane; i < N; i += 32) acc += csum[i] * a.theta[(size_t)i * D + d];
             acc = warp_sum_d(acc);
             if (lane == 0) {
                 const double md = (s1 > 0.0) ? acc / s1 : 0.0;
@@ -215,6 +214,7 @@ __global__ void __launch_bounds__(kOuterThreads) outer_update_kernel(OuterArgs a
     }
 
     // 3. systematic resampling: FP64 prefix sums (per-thread chunk, warp shuffle, warps)
+    __syncthreads();  // every warp is done reading the weights in csum
     {
         const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
         const int chunk = (N + nt - 1) / nt;
@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(kOuterThreads) outer_update_kernel(OuterArgs a
         for (int c = 0; c < chunk; ++c) {
             const int i = i0 + c;
             if (i < N) {
-                run += exp(a.logw[i] - lmax);
+                run += csum[i];  // w_i from step 2 (each thread rewrites only its own chunk)
                 csum[i] = run;
             }
         }
