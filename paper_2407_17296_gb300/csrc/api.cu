@@ -500,7 +500,7 @@ int smc2::enqueue_step(smc2_handle* h) {
     int rc = launch_filters(h, a, h->timing);
     if (rc) return rc;
     if (launch_outer_update(o, h->stream)) return fail(SMC2_E_CUDA, "outer update launch failed");
-    count_launches(2);
+    count_launches(1 + kOuterUpdateLaunches);
     return SMC2_OK;
 }
 
@@ -530,7 +530,7 @@ int smc2::step_async(smc2_handle* h) {
     }
     if (h->graph_exec && !h->timing) {
         CUDA_TRY(cudaGraphLaunch(h->graph_exec, h->stream));
-        count_launches(4);
+        count_launches(3 + kOuterUpdateLaunches);
     } else {
         int rc = enqueue_step(h);
         if (rc) return rc;
@@ -621,7 +621,7 @@ extern "C" int smc2_step_update(smc2_handle* h, const double* loglik_all_dev, co
                                  h->stream));
     const OuterArgs o = make_outer_args(h);
     if (launch_outer_update(o, h->stream)) return fail(SMC2_E_CUDA, "outer update launch failed");
-    count_launches(1);
+    count_launches(kOuterUpdateLaunches);
     h->split_pending = false;
     h->k += 1;
     return read_stats(h, out);

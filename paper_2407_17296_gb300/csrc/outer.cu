@@ -105,70 +105,76 @@ __device__ double log_prior(const double* th, const double* m, const double* inv
     return acc;
 }
 
-__global__ void __launch_bounds__(kOuterThreads) outer_update_kernel(OuterArgs a) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    double* red = reinterpret_cast<double*>(smem);               // 32
-    double* pinv = red + 32;                                      // 64: 1/prior_std, then cst
-    double* csum = pinv + 65;                                     // N
-    int* anc = reinterpret_cast<int*>(csum + a.N);                // N
-    const int N = a.N, D = a.D, tid = threadIdx.x, nt = blockDim.x;
-    const uint32_t k = *a.k_dev + 1u;
-    const double g2 = a.gamma * a.gamma;
-    if (tid == 0) {
+// prior constants shared by a block: pinv[d] = 1/prior_std[d], pinv[64] = -sum log s - D/2 log 2 pi
+__device__ void prior_constants(const OuterArgs& a, double* pinv) {
+    for (int d = threadIdx.x; d < a.D; d += blockDim.x) pinv[d] = 1.0 / a.prior_std[d];
+    if (threadIdx.x == 0) {
         double c = 0.0;
-        for (int d = 0; d < D; ++d) {
-            pinv[d] = 1.0 / a.prior_std[d];
-            c -= log(a.prior_std[d]) + 0.9189385332046727418;
-        }
+        for (int d = 0; d < a.D; ++d) c -= log(a.prior_std[d]) + 0.9189385332046727418;
         pinv[64] = c;
     }
     __syncthreads();
+}
 
-    // 1. pseudo-marginal update of every sample with its particle-filter result
-    for (int i = tid; i < N; i += nt) {
-        const double* thn = a.theta_new + (size_t)i * D;
-        const double lln = a.ll_new[i];
-        const double lpn = (lln > -INFINITY) ? log_prior(thn, a.prior_mean, pinv, pinv[64], D) + lln : -INFINITY;
-        double lw;
-        if (k == 1u) {
-            lw = lln;  // pi / q_1 with q_1 the prior
-        } else {
-            lw = a.logw[i];
-            if (lw > -INFINITY && lpn > -INFINITY && a.logpi[i] > -INFINITY) {
-                double corr = 0.0;
-                if (a.langevin) {
-                    // log L(theta | theta') - log q(theta' | theta)
-                    const double* th = a.theta + (size_t)i * D;
-                    const double* gp = a.gradpi + (size_t)i * D;
-                    const double* gn = a.grad_new + (size_t)i * D;
-                    double qf = 0.0, lf = 0.0;
-                    for (int d = 0; d < D; ++d) {
-                        const double gpn = -(thn[d] - a.prior_mean[d]) * pinv[d] * pinv[d] + gn[d];
-                        const double fwd = thn[d] - th[d] - 0.5 * g2 * gp[d];
-                        const double bwd = th[d] - thn[d] - 0.5 * g2 * gpn;
-                        qf += fwd * fwd;
-                        lf += bwd * bwd;
-                    }
-                    corr = -0.5 * (lf - qf) / g2;
+// 1. pseudo-marginal update of every sample with its particle-filter result (one thread a
+//    sample, any number of blocks)
+__global__ void outer_weight_kernel(OuterArgs a) {
+    __shared__ double pinv[65];
+    prior_constants(a, pinv);
+    const int N = a.N, D = a.D;
+    const uint32_t k = *a.k_dev + 1u;
+    const double g2 = a.gamma * a.gamma;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double* thn = a.theta_new + (size_t)i * D;
+    const double lln = a.ll_new[i];
+    const double lpn = (lln > -INFINITY) ? log_prior(thn, a.prior_mean, pinv, pinv[64], D) + lln : -INFINITY;
+    double lw;
+    if (k == 1u) {
+        lw = lln;  // pi / q_1 with q_1 the prior
+    } else {
+        lw = a.logw[i];
+        if (lw > -INFINITY && lpn > -INFINITY && a.logpi[i] > -INFINITY) {
+            double corr = 0.0;
+            if (a.langevin) {
+                // log L(theta | theta') - log q(theta' | theta)
+                const double* th = a.theta + (size_t)i * D;
+                const double* gp = a.gradpi + (size_t)i * D;
+                const double* gn = a.grad_new + (size_t)i * D;
+                double qf = 0.0, lf = 0.0;
+                for (int d = 0; d < D; ++d) {
+                    const double gpn = -(thn[d] - a.prior_mean[d]) * pinv[d] * pinv[d] + gn[d];
+                    const double fwd = thn[d] - th[d] - 0.5 * g2 * gp[d];
+                    const double bwd = th[d] - thn[d] - 0.5 * g2 * gpn;
+                    qf += fwd * fwd;
+                    lf += bwd * bwd;
                 }
-                lw = lw + (lpn - a.logpi[i]) + corr;
-            } else {
-                lw = -INFINITY;
+                corr = -0.5 * (lf - qf) / g2;
             }
-        }
-        a.logw[i] = lw;
-        a.logpi[i] = lpn;
-        a.loglik[i] = lln;
-        for (int d = 0; d < D; ++d) {
-            const double th = thn[d];
-            a.theta[(size_t)i * D + d] = th;
-            a.gradpi[(size_t)i * D + d] = -(th - a.prior_mean[d]) * pinv[d] * pinv[d] + a.grad_new[(size_t)i * D + d];
+            lw = lw + (lpn - a.logpi[i]) + corr;
+        } else {
+            lw = -INFINITY;
         }
     }
-    __syncthreads();
+    a.logw[i] = lw;
+    a.logpi[i] = lpn;
+    a.loglik[i] = lln;
+    for (int d = 0; d < D; ++d) {
+        const double th = thn[d];
+        a.theta[(size_t)i * D + d] = th;
+        a.gradpi[(size_t)i * D + d] = -(th - a.prior_mean[d]) * pinv[d] * pinv[d] + a.grad_new[(size_t)i * D + d];
+    }
+}
 
-    // 2. normalise, ESS, estimate, recycling statistic; the unnormalised weights
-    //    w_i = exp(log w_i - max) are evaluated once into csum (free until the resampling scan)
+// 2. normalise, ESS, estimate, recycling statistic and, if ESS < N/2, the systematic
+//    ancestors (one block); the unnormalised weights w_i = exp(log w_i - max) are evaluated
+//    once into csum, which the resampling scan then turns into cumulative sums
+__global__ void __launch_bounds__(kOuterThreads) outer_stats_kernel(OuterArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    double* red = reinterpret_cast<double*>(smem);  // 32
+    double* csum = red + 32;                         // N
+    const int N = a.N, D = a.D, tid = threadIdx.x, nt = blockDim.x;
+    const uint32_t k = *a.k_dev + 1u;
     double lmax = -INFINITY;
     for (int i = tid; i < N; i += nt) lmax = fmax(lmax, a.logw[i]);
     lmax = block_max_d(lmax, red);
@@ -207,13 +213,11 @@ __global__ void __launch_bounds__(kOuterThreads) outer_update_kernel(OuterArgs a
         a.stats[kStMaxLogw] = lmax;
         a.stats[kStSumL] = ((k == 1u) ? 0.0 : a.stats[kStSumL]) + ess;
         a.stats[kStK] = (double)k;
+        a.stats[kStLwNew] = lmax + log(s1) - log((double)N);  // log w of every sample after resampling
     }
-    if (!resample) {
-        if (tid == 0) *a.k_dev = k;
-        return;
-    }
+    if (!resample) return;
 
-    // 3. systematic resampling: FP64 prefix sums (per-thread chunk, warp shuffle, warps)
+    // systematic resampling: FP64 prefix sums (per-thread chunk, warp shuffle, warps)
     __syncthreads();  // every warp is done reading the weights in csum
     {
         const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
@@ -223,7 +227,7 @@ __global__ void __launch_bounds__(kOuterThreads) outer_update_kernel(OuterArgs a
         for (int c = 0; c < chunk; ++c) {
             const int i = i0 + c;
             if (i < N) {
-                run += csum[i];  // w_i from step 2 (each thread rewrites only its own chunk)
+                run += csum[i];  // w_i from above (each thread rewrites only its own chunk)
                 csum[i] = run;
             }
         }
@@ -257,45 +261,51 @@ __global__ void __launch_bounds__(kOuterThreads) outer_update_kernel(OuterArgs a
             if (csum[mid] >= tau) hi = mid;
             else lo = mid + 1;
         }
-        anc[i] = lo;
         a.outer_anc[i] = lo;
     }
-    __syncthreads();
-    // gather rows through the scratch buffer
-    for (int idx = tid; idx < N * D; idx += nt) {
+}
+
+// 3. after resampling: gather the ancestors' rows (theta, grad log pi into the scratch rows
+//    tmp and grad_new; log pi-hat and log p-hat into theta_new and ll_new, all free by now)
+__global__ void outer_gather_kernel(OuterArgs a) {
+    if (a.stats[kStResampled] == 0.0) return;
+    const int N = a.N, D = a.D;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N * D; idx += gridDim.x * blockDim.x) {
         const int i = idx / D, d = idx - i * D;
-        a.tmp[idx] = a.theta[(size_t)anc[i] * D + d];
+        const int j = a.outer_anc[i];
+        a.tmp[idx] = a.theta[(size_t)j * D + d];
+        a.grad_new[idx] = a.gradpi[(size_t)j * D + d];
+        if (d == 0) {
+            a.theta_new[i] = a.logpi[j];
+            a.ll_new[i] = a.loglik[j];
+        }
     }
-    __syncthreads();
-    for (int idx = tid; idx < N * D; idx += nt) a.theta[idx] = a.tmp[idx];
-    __syncthreads();
-    for (int idx = tid; idx < N * D; idx += nt) {
-        const int i = idx / D, d = idx - i * D;
-        a.tmp[idx] = a.gradpi[(size_t)anc[i] * D + d];
+}
+
+// 4. copy the gathered rows back, reset log w (sum kept) and advance the iteration counter
+__global__ void outer_commit_kernel(OuterArgs a) {
+    const int N = a.N, D = a.D;
+    if (a.stats[kStResampled] != 0.0) {
+        const double lw_new = a.stats[kStLwNew];
+        for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N * D; idx += gridDim.x * blockDim.x) {
+            const int i = idx / D, d = idx - i * D;
+            a.theta[idx] = a.tmp[idx];
+            a.gradpi[idx] = a.grad_new[idx];
+            if (d == 0) {
+                a.logpi[i] = a.theta_new[i];
+                a.loglik[i] = a.ll_new[i];
+                a.logw[i] = lw_new;
+            }
+        }
     }
-    __syncthreads();
-    for (int idx = tid; idx < N * D; idx += nt) a.gradpi[idx] = a.tmp[idx];
-    __syncthreads();
-    // scalars: logpi and loglik through csum (free now) as scratch
-    for (int i = tid; i < N; i += nt) csum[i] = a.logpi[anc[i]];
-    __syncthreads();
-    for (int i = tid; i < N; i += nt) a.logpi[i] = csum[i];
-    __syncthreads();
-    for (int i = tid; i < N; i += nt) csum[i] = a.loglik[anc[i]];
-    __syncthreads();
-    const double lw_new = lmax + log(s1) - log((double)N);
-    for (int i = tid; i < N; i += nt) {
-        a.loglik[i] = csum[i];
-        a.logw[i] = lw_new;
-    }
-    if (tid == 0) *a.k_dev = k;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.k_dev = *a.k_dev + 1u;
 }
 
 }  // namespace
 
 size_t outer_update_smem(int N, int D) {
     (void)D;
-    return sizeof(double) * (32 + 65 + (size_t)N) + sizeof(int) * (size_t)N;
+    return sizeof(double) * (32 + (size_t)N);
 }
 
 int launch_outer_propose(const OuterArgs& a, void* stream) {
@@ -307,11 +317,17 @@ int launch_outer_propose(const OuterArgs& a, void* stream) {
 }
 
 int launch_outer_update(const OuterArgs& a, void* stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
     const size_t smem = outer_update_smem(a.N, a.D);
     if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(outer_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        cudaFuncSetAttribute(outer_stats_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return -3;
-    outer_update_kernel<<<1, kOuterThreads, smem, static_cast<cudaStream_t>(stream)>>>(a);
+    const int rows = (a.N + 127) / 128;
+    const int elems = (a.N * a.D + 255) / 256;
+    outer_weight_kernel<<<rows, 128, 0, st>>>(a);
+    outer_stats_kernel<<<1, kOuterThreads, smem, st>>>(a);
+    outer_gather_kernel<<<elems, 256, 0, st>>>(a);
+    outer_commit_kernel<<<elems, 256, 0, st>>>(a);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 

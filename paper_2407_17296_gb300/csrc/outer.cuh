@@ -18,18 +18,21 @@ struct OuterArgs {
     double* logpi;                // [N] log prior + log p-hat
     double* gradpi;               // [N][D] grad log prior + grad log p-hat
     double* loglik;               // [N]
-    const double* ll_new;         // [N]  particle-filter outputs at theta_new
-    const double* grad_new;       // [N][D]
+    double* ll_new;               // [N]  particle-filter outputs at theta_new (scratch afterwards)
+    double* grad_new;             // [N][D]
     double* tmp;                  // [N][D] gather scratch
     double* stats;                // [kStatsHead + 2D]
     int* outer_anc;               // [N]
 };
 
 // stats layout (FP64 slots)
-enum { kStEss = 0, kStLk = 1, kStResampled = 2, kStMaxLogw = 3, kStSumL = 4, kStK = 5, kStatsHead = 6 };
+enum { kStEss = 0, kStLk = 1, kStResampled = 2, kStMaxLogw = 3, kStSumL = 4, kStK = 5, kStLwNew = 6, kStatsHead = 7 };
 // then mean [D] at kStatsHead, recycled numerator sum_k l_k f~_k [D] at kStatsHead + D
 
 int launch_outer_propose(const OuterArgs& a, void* stream);
+// Launches the update in kOuterUpdateLaunches kernels: per-sample weights (many blocks),
+// statistics and ancestors (one block), gather and commit of the resampled rows.
+constexpr int kOuterUpdateLaunches = 4;
 int launch_outer_update(const OuterArgs& a, void* stream);
 size_t outer_update_smem(int N, int D);
 
