@@ -37,6 +37,11 @@ UNIT = "particle-steps/s"
 # amortised reductions and resampling, and the adjoint of each.
 ALG_OPS = {"lg1": 33 + 14, "lg4": 94 + 47, "sv": 36 + 15, "lg16": 333 + 154}
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per filter of the forward +
+# adjoint pair, measured with ncu on a launch of 304 filters of the 4-d workload's shape
+# (M = 1024, T = 250, every step stored); a launch of N filters moves N times this.
+TRAFFIC_PER_FILTER = {("lg4", 1024, 250): (1401.364e6 + 1457.115e6) / 304}
+
 
 def _args():
     p = argparse.ArgumentParser()
@@ -267,7 +272,8 @@ def run_gpu(a, rank, world, local):
     max_mhz = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
     peak_tops = sm_count * 128 * max_mhz * 1e6 / 1e12
     achieved_tops = ALG_OPS.get(w.name, 0) * ps_per_step / (pf_ms / 1e3) / 1e12
-    traffic = None
+    per_filter = TRAFFIC_PER_FILTER.get((w.name, w.M, w.T))
+    traffic = per_filter * w.N if per_filter else None
     out = {
         "metric": METRIC,
         "value": value,
