@@ -51,6 +51,7 @@ def _args():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="lg4")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU baseline sample")
+    p.add_argument("--cpu-procs", type=int, default=0, help="oracle processes (0: all host cores)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--N", type=int, default=0, help="override the number of samples (profiling runs)")
     p.add_argument("--no-autotune", action="store_true", help="use the default launch configuration")
@@ -308,7 +309,7 @@ def run_gpu(a, rank, world, local):
         "gpu_launches": int(launches),
     }
     if not a.no_cpu_baseline:
-        rate, cores, info = cpu_oracle_rate(w, a.cpu_seconds)
+        rate, cores, info = cpu_oracle_rate(w, a.cpu_seconds, a.cpu_procs or None)
         out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                "sample": f"{info['filters']} of {info['of']} filters of one iteration "
                                          f"(forward + forward-mode gradient, FP64), spawn pool, "
@@ -327,11 +328,11 @@ def run_reference(a, rank, world):
     w = workloads.ALL[a.workload]()
     per = max(2.0, a.cpu_seconds / max(1, a.steps + a.warmup))
     for _ in range(a.warmup):
-        cpu_oracle_rate(w, per / 4)
+        cpu_oracle_rate(w, per / 4, a.cpu_procs or None)
     rates, infos = [], []
     t0 = time.perf_counter()
     for _ in range(a.steps):
-        r, cores, info = cpu_oracle_rate(w, per)
+        r, cores, info = cpu_oracle_rate(w, per, a.cpu_procs or None)
         rates.append(r)
         infos.append(info)
     wall = time.perf_counter() - t0
