@@ -31,11 +31,18 @@ if ROOT not in sys.path:
 METRIC = "fwd+grad CRN-PF particle-steps/s"
 UNIT = "particle-steps/s"
 
-# Algorithmic FP32/INT32 lane-operations per particle-step (forward + adjoint), counted
-# from the algorithm at source level for each model shape: the Philox rounds, the uniform
-# maps, Box-Muller (each transcendental one operation), the model arithmetic, the
-# amortised reductions and resampling, and the adjoint of each.
-ALG_OPS = {"lg1": 33 + 14, "lg4": 94 + 47, "sv": 36 + 15, "lg16": 333 + 154}
+# Algorithmic lane-operations per particle-step (forward + adjoint, every step stored so
+# no recomputation), per model shape, in the per-item convention of the method's op
+# accounting: a Philox4x32-10 call is 90 operations (10 rounds of two 32x32->64-bit
+# multiplies at two operations each, two three-way XORs at two each and the key bump), a
+# Box-Muller pair 9 (four transcendental + five FP32), propagation 2 d_x, observation
+# d_y d_x + 3 d_y (d_y + 3 d_y with H = I), the log-sum-exp 5, resampling log2 M + 10, and
+# the adjoint twice the forward's non-random FP32/INT32 arithmetic plus its exponentials.  The normals a
+# particle-step needs are drawn four per Philox call, so 1-d states use a quarter call.
+ALG_OPS = {"lg1": 55 + 55, "lg4": 155 + 93, "sv": 61 + 66, "lg16": 553 + 241}
+# The same work counted strictly (each wide multiply, three-way XOR and transcendental one
+# operation; the key schedule is precomputed): the lower bound reported beside it.
+ALG_OPS_STRICT = {"lg1": 33 + 14, "lg4": 94 + 47, "sv": 36 + 15, "lg16": 333 + 154}
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per filter of the forward +
 # adjoint pair, measured with ncu on a launch of 304 filters of the 4-d workload's shape
@@ -273,6 +280,7 @@ def run_gpu(a, rank, world, local):
     max_mhz = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
     peak_tops = sm_count * 128 * max_mhz * 1e6 / 1e12
     achieved_tops = ALG_OPS.get(w.name, 0) * ps_per_step / (pf_ms / 1e3) / 1e12
+    strict_tops = ALG_OPS_STRICT.get(w.name, 0) * ps_per_step / (pf_ms / 1e3) / 1e12
     per_filter = TRAFFIC_PER_FILTER.get((w.name, w.M, w.T))
     traffic = per_filter * w.N if per_filter else None
     out = {
@@ -302,6 +310,8 @@ def run_gpu(a, rank, world, local):
                      "kernel": "pf_forward_kernel + pf_backward_kernel",
                      "kernel_ms": pf_ms, "forward_ms": fwd_ms, "adjoint_ms": pf_ms - fwd_ms,
                      "ops_per_particle_step": ALG_OPS.get(w.name),
+                     "ops_per_particle_step_strict": ALG_OPS_STRICT.get(w.name),
+                     "frac_strict": strict_tops / peak_tops if peak_tops else None,
                      "peak_basis": f"{sm_count} SMs x 128 FP32/INT32 lanes x {max_mhz:.0f} MHz"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(w.T * w.dy * 4),
                 "d2h_bytes_per_step": int(w.N * w.D * 8 + w.N * 8 + 8 * (6 + 2 * w.D))},
