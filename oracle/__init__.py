@@ -23,6 +23,7 @@ from .build import build_oracle
 
 LG_DIAG = 0
 SV = 1
+LG_OPT = 2
 SYSTEMATIC = 0
 MULTINOMIAL = 1
 
@@ -121,7 +122,7 @@ def pf(family, dx, dy, H, theta, y, M, seed, it, row, scheme=SYSTEMATIC, ess_fra
        flag_band=1e-6, want_tape=True, band_rel=0.0):
     """One CRN particle-filter run in FP64 (see oracle.c for the algorithm).
 
-    family: LG_DIAG or SV; H: (dy, dx) float array or None for identity;
+    family: LG_DIAG, SV or LG_OPT; H: (dy, dx) float array or None for identity;
     theta: (D,) float64; y: (T, dy) observations (used as float32).
     Returns a dict with loglik, grad (D,), anc (T, M) uint16, flag (T,) uint8,
     stats (dict of counters) and worst (largest non-tie mismatch distance).

@@ -58,7 +58,7 @@
 #define OR_TWO_PI 6.283185307179586476925286766559
 #define OR_LOG_2PI 1.8378770664093454835606594728112
 
-enum { OR_LG_DIAG = 0, OR_SV = 1 };
+enum { OR_LG_DIAG = 0, OR_SV = 1, OR_LG_OPT = 2 };
 enum { OR_SYSTEMATIC = 0, OR_MULTINOMIAL = 1 };
 enum { OR_STREAM_PROP = 0, OR_STREAM_RESAMPLE = 1, OR_STREAM_INIT = 2,
        OR_STREAM_OUTER_XI = 3, OR_STREAM_OUTER_NU = 4 };
@@ -152,6 +152,12 @@ double oracle_uniform_open(uint64_t seed, uint32_t iter, uint32_t row, uint32_t 
 /* SV:      theta = (mu, atanh phi, log sigma),                             */
 /*   x_0 = mu + sigma/sqrt(1-phi^2) eps_0,                                  */
 /*   x_t = mu + phi (x_{t-1} - mu) + sigma eta_t, y_t ~ N(0, exp(x_t)).     */
+/* LG_OPT:  the linear-Gaussian model of Sec. IV-A, theta = (mu, phi, sigma) */
+/*   in their own units, x_0 ~ N(0, 1), x_t | x_{t-1} ~ N(mu x_{t-1}, phi^2), */
+/*   y_t | x_t ~ N(x_t, sigma^2), filtered with the "optimal" proposal       */
+/*   q(x_t | x_{t-1}, y_t) = N(rho^2 (y_t/sigma^2 + mu x_{t-1}/phi^2), rho^2),*/
+/*   1/rho^2 = 1/phi^2 + 1/sigma^2, whose weight (Eq. weightupdate) is       */
+/*   p(y_t | x_{t-1}) = N(y_t; mu x_{t-1}, phi^2 + sigma^2).                 */
 /* ------------------------------------------------------------------------ */
 
 typedef struct {
@@ -172,7 +178,7 @@ static void model_init(const or_model* m, const double* th, const double* eps, d
 {
     int dx = m->dx, D = m->D;
     memset(J, 0, sizeof(double) * dx * D);
-    if (m->family == OR_LG_DIAG) {
+    if (m->family == OR_LG_DIAG || m->family == OR_LG_OPT) {
         for (int k = 0; k < dx; ++k) x[k] = eps[k];
     } else {
         double mu = th[0], phi = tanh(th[1]), sig = exp(th[2]);
@@ -240,6 +246,46 @@ static double model_loglik(const or_model* m, const double* th, const double* x,
         Lx[0] = -0.5 + 0.5 * y[0] * y[0] * v;
     }
     return L;
+}
+
+/*
+ * LG_OPT weight log p(y | x_prev) = log N(y; mu x_prev, phi^2 + sigma^2) with its partials
+ * Lx = d/dx_prev and Lt = d/dtheta.
+ */
+static double opt_weight(const double* th, double xp, double y, double* Lx, double* Lt)
+{
+    double mu = th[0], phi = th[1], sig = th[2];
+    double s2 = phi * phi + sig * sig;
+    double r = y - mu * xp;
+    double L = -0.5 * (OR_LOG_2PI + log(s2) + r * r / s2);
+    double dL_ds2 = -0.5 / s2 + 0.5 * r * r / (s2 * s2);
+    *Lx = mu * r / s2;
+    Lt[0] = xp * r / s2;
+    Lt[1] = dL_ds2 * 2.0 * phi;
+    Lt[2] = dL_ds2 * 2.0 * sig;
+    return L;
+}
+
+/*
+ * LG_OPT proposal x = (phi^2 y + sigma^2 mu x_prev)/s2 + rho eps, s2 = phi^2 + sigma^2,
+ * rho = phi sigma / sqrt(s2), with Fx = dx/dx_prev and Ft = dx/dtheta.
+ */
+static void opt_transition(const double* th, double xp, double y, double eps, double* xn, double* Fx,
+                           double* Ft)
+{
+    double mu = th[0], phi = th[1], sig = th[2];
+    double p2 = phi * phi, q2 = sig * sig, s2 = p2 + q2;
+    double rho = phi * sig / sqrt(s2);
+    double mean = (p2 * y + q2 * mu * xp) / s2;
+    *xn = mean + rho * eps;
+    *Fx = q2 * mu / s2;
+    /* d mean/d phi = (2 phi y s2 - (p2 y + q2 mu xp) 2 phi)/s2^2 = 2 phi q2 (y - mu xp)/s2^2 */
+    /* d mean/d sig = (2 sig mu xp s2 - (p2 y + q2 mu xp) 2 sig)/s2^2 = 2 sig p2 (mu xp - y)/s2^2 */
+    /* d rho/d phi = sig^3/s2^(3/2), d rho/d sig = phi^3/s2^(3/2) */
+    double s32 = s2 * sqrt(s2);
+    Ft[0] = q2 * xp / s2;
+    Ft[1] = 2.0 * phi * q2 * (y - mu * xp) / (s2 * s2) + sig * q2 / s32 * eps;
+    Ft[2] = 2.0 * sig * p2 * (mu * xp - y) / (s2 * s2) + phi * p2 / s32 * eps;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -311,6 +357,8 @@ int oracle_pf(int family, int dx, int dy, int D, const double* H,
     if (T < 1 || M < 1 || dx < 1 || dy < 1 || D < 1) return -1;
     if (family == OR_SV && (dx != 1 || dy != 1 || D != 3)) return -1;
     if (family == OR_LG_DIAG && D != 2 * dx + dy) return -1;
+    if (family == OR_LG_OPT && (dx != 1 || dy != 1 || D != 3)) return -1;
+    if (family < OR_LG_DIAG || family > OR_LG_OPT) return -1;
     if (replay && (!hint_anc || !hint_flag)) return -1;
 
     long long st[ST_COUNT];
@@ -459,6 +507,22 @@ int oracle_pf(int family, int dx, int dy, int D, const double* H,
         for (int j = 0; j < M; ++j) {
             double* xj = x + (size_t)j * dx;
             double* xnj = xn + (size_t)j * dx;
+            if (family == OR_LG_OPT) {
+                /* optimal proposal: the weight depends on the previous state only */
+                double Lj = opt_weight(theta, xj[0], yt[0], Lx, Lt);
+                opt_transition(theta, xj[0], yt[0], eps[j], xnj, Fx, Ft);
+                lw[j] += Lj;
+                if (fabs(Lj) > step_max_abs) step_max_abs = fabs(Lj);
+                if (want_grad) {
+                    double* Jj = J + (size_t)j * nJ;
+                    double* Jnj = Jn + (size_t)j * nJ;
+                    for (int d = 0; d < D; ++d) {
+                        g[(size_t)j * D + d] += Lt[d] + Lx[0] * Jj[d];   /* through x_{t-1} */
+                        Jnj[d] = Ft[d] + Fx[0] * Jj[d];
+                    }
+                }
+                continue;
+            }
             model_transition(&m, theta, xj, eps + (size_t)j * dx, xnj, Fx, Ft);
             double Lj = model_loglik(&m, theta, xnj, yt, Lx, Lt);
             lw[j] += Lj;

@@ -19,6 +19,8 @@ Readings where the paper is silent or inconsistent:
   * log pi-hat and its gradient travel with each sample through resampling;
   * the prior is N(prior_mean, diag(prior_std^2)).
 """
+import math
+
 import numpy as np
 
 from . import pf as _pf, normals as _normals, uniform_open as _uniform_open
@@ -27,13 +29,28 @@ from . import STREAM_OUTER_XI, STREAM_OUTER_NU, SYSTEMATIC
 LOG_2PI = np.log(2.0 * np.pi)
 
 
-def log_prior(theta, m, s):
+GAUSSIAN_PRIOR = 0
+UNIFORM_PRIOR = 1
+
+
+def log_prior(theta, m, s, kind=GAUSSIAN_PRIOR):
+    """Gaussian N(m, diag(s^2)), or (kind UNIFORM_PRIOR) uniform on the box [m, s] (Sec. IV-A:
+    uniform priors), -inf outside it."""
+    if kind == UNIFORM_PRIOR:
+        inside = np.all((theta >= m) & (theta <= s), axis=-1)
+        return np.where(inside, -np.sum(np.log(s - m)), -np.inf)
     z = (theta - m) / s
     return np.sum(-0.5 * z * z - np.log(s) - 0.5 * LOG_2PI, axis=-1)
 
 
-def grad_log_prior(theta, m, s):
+def grad_log_prior(theta, m, s, kind=GAUSSIAN_PRIOR):
+    if kind == UNIFORM_PRIOR:
+        return np.zeros_like(theta)
     return -(theta - m) / (s * s)
+
+
+def _std_normal_cdf(z):
+    return 0.5 * np.vectorize(math.erfc)(-z / math.sqrt(2.0))
 
 
 def log_normal_iso(x, mean, gamma):
@@ -87,24 +104,27 @@ class State:
         self.loglik = np.zeros(N)
 
 
-def propose(state, k, seed, gamma, proposal, m0, s0):
-    """theta' for iteration k: a prior draw at k = 1 (Eq. init_sample), else the random-walk
-    (SMC0) or Langevin (SMC1) move of Sec. III-D with normals from Philox stream 3."""
+def propose(state, k, seed, gamma, proposal, m0, s0, prior_kind=GAUSSIAN_PRIOR):
+    """theta' for iteration k: a prior draw at k = 1 (Eq. init_sample; a uniform prior maps the
+    normal xi through its CDF), else the random-walk (SMC0) or Langevin (SMC1) move of
+    Sec. III-D with normals from Philox stream 3."""
     N, D = state.theta.shape
     xi = np.stack([_normals(seed, k, i, 0, STREAM_OUTER_XI, D) for i in range(N)])
     if k == 1:
+        if prior_kind == UNIFORM_PRIOR:
+            return m0 + (s0 - m0) * _std_normal_cdf(xi)
         return m0 + s0 * xi
     drift = 0.5 * gamma * gamma * state.gradpi if proposal == "langevin" else np.zeros_like(state.gradpi)
     return state.theta + drift + gamma * xi
 
 
 def update(state, k, theta_new, ll_new, g_new, seed, gamma, proposal, m0, s0, hint=None,
-           outer_band=1e-4, outer_flag_band=1e-3):
+           outer_band=1e-4, outer_flag_band=1e-3, prior_kind=GAUSSIAN_PRIOR):
     """Complete iteration k from the filter outputs at theta_new: weight, normalise,
     estimate, recycling statistic, ESS, resampling.  Updates state; returns the record."""
     N = state.logw.shape[0]
-    lp_new = log_prior(theta_new, m0, s0) + ll_new
-    gp_new = grad_log_prior(theta_new, m0, s0) + g_new
+    lp_new = log_prior(theta_new, m0, s0, prior_kind) + ll_new
+    gp_new = grad_log_prior(theta_new, m0, s0, prior_kind) + g_new
     if k == 1:
         # w_1 = pi/q_1 = p-hat(y|theta) (Eq. init_weights)
         logw = ll_new.copy()
@@ -117,7 +137,11 @@ def update(state, k, theta_new, ll_new, g_new, seed, gamma, proposal, m0, s0, hi
             drift_new = np.zeros_like(gp_new)
         log_q = log_normal_iso(theta_new, state.theta + drift, gamma)     # q(theta_k | theta_{k-1})
         log_L = log_normal_iso(state.theta, theta_new + drift_new, gamma)  # L(theta_{k-1} | theta_k)
-        logw = state.logw + lp_new - state.logpi + log_L - log_q         # Eq. l_weights
+        # Eq. l_weights; a sample whose weight or posterior estimate (old or new) is zero
+        # keeps weight zero (this also covers proposals outside a uniform prior's support)
+        ok = (state.logw > -np.inf) & (lp_new > -np.inf) & (state.logpi > -np.inf)
+        with np.errstate(invalid="ignore"):
+            logw = np.where(ok, state.logw + lp_new - state.logpi + log_L - log_q, -np.inf)
     theta, logpi, gradpi, loglik = theta_new, lp_new, gp_new, ll_new
 
     # normalise, estimate, recycling statistic, ESS
@@ -157,7 +181,8 @@ def recycled_mean(records):
 
 def run(family, dx, dy, H, y, N, M, K, gamma, proposal, seed, prior_mean=None, prior_std=None,
         scheme=SYSTEMATIC, ess_frac=0.5, hints=None, band=1e-6, flag_band=1e-6,
-        outer_band=1e-4, D=None, loglik_grad_fn=None, band_rel=0.0, outer_flag_band=1e-3):
+        outer_band=1e-4, D=None, loglik_grad_fn=None, band_rel=0.0, outer_flag_band=1e-3,
+        prior_kind=GAUSSIAN_PRIOR):
     """Run K iterations; returns (list of per-iteration records, recycled mean).
 
     proposal: "rw" (SMC0) or "langevin" (SMC1).
@@ -169,7 +194,7 @@ def run(family, dx, dy, H, y, N, M, K, gamma, proposal, seed, prior_mean=None, p
       (e.g. the exact Kalman likelihood, to test the sampler on its own).
     """
     if D is None:
-        D = 3 if family == 1 else 2 * dx + dy
+        D = 3 if family in (1, 2) else 2 * dx + dy
     m0 = np.zeros(D) if prior_mean is None else np.asarray(prior_mean, dtype=np.float64)
     s0 = np.ones(D) if prior_std is None else np.asarray(prior_std, dtype=np.float64)
     seed = int(seed)
@@ -177,12 +202,12 @@ def run(family, dx, dy, H, y, N, M, K, gamma, proposal, seed, prior_mean=None, p
     state = State(N, D)
     for k in range(1, K + 1):
         hint = hints[k - 1] if hints is not None else None
-        theta_new = propose(state, k, seed, gamma, proposal, m0, s0)
+        theta_new = propose(state, k, seed, gamma, proposal, m0, s0, prior_kind)
         ll_new, g_new, pfstats, pfrows = run_filters(family, dx, dy, H, y, M, seed, k, theta_new,
                                                      range(N), scheme, ess_frac, hint, band, flag_band,
                                                      band_rel, loglik_grad_fn)
         rec = update(state, k, theta_new, ll_new, g_new, seed, gamma, proposal, m0, s0, hint,
-                     outer_band, outer_flag_band)
+                     outer_band, outer_flag_band, prior_kind)
         rec["pf_stats"] = pfstats
         rec["pf_stats_rows"] = pfrows
         records.append(rec)

@@ -17,6 +17,9 @@ Workloads (data seed 12345 + index):
   lg16    LG-diag d_x=d_y=16, H=I, D=48, a* ~ U(0, 0.95), q*=0.5, r*=1.0,
           T=200, N=2048, M=1024, K=30, prior N((0.5, log 0.5, 0), (0.15, 0.3, 0.3)^2)
           per dimension (the others use N(0, I)).
+  lgssm   the linear-Gaussian model of Sec. IV-A with the optimal proposal,
+          theta = (mu, phi, sigma), theta* = (0.75, 1, 1), uniform priors, T=500,
+          N=64, M=250, K=15.
 Step sizes: Langevin 0.085*sqrt(500/T), random walk 0.175*sqrt(500/T), scaled
 from the values the paper tuned for its T=500 linear-Gaussian model; the 48-parameter
 lg16 uses 0.03*sqrt(200/T) (random walk 0.06*sqrt(200/T)).
@@ -28,6 +31,9 @@ import numpy as np
 
 LG_DIAG = 0
 SV = 1
+LG_OPT = 2
+GAUSSIAN_PRIOR = 0
+UNIFORM_PRIOR = 1
 
 
 @dataclass
@@ -51,6 +57,7 @@ class Workload:
     prior_mean: Optional[np.ndarray] = None   # None: N(0, I) prior on theta
     prior_std: Optional[np.ndarray] = None
     extra: dict = field(default_factory=dict)
+    prior_kind: int = GAUSSIAN_PRIOR          # UNIFORM_PRIOR: U(prior_mean[d], prior_std[d])
 
     @property
     def particle_steps(self) -> int:
@@ -142,7 +149,22 @@ def lg16(T=200, N=2048, M=1024, K=30, proposal="langevin") -> Workload:
                     gam, 780, seed, prior_mean=m0, prior_std=s0)
 
 
-ALL = {"lg1": lg1, "lg4": lg4, "sv": sv, "lg16": lg16}
+def lgssm(T=500, N=64, M=250, K=15, proposal="langevin") -> Workload:
+    """The linear-Gaussian model of Sec. IV-A: x_t ~ N(mu x_{t-1}, phi^2), y_t ~ N(x_t, sigma^2),
+    theta = (mu, phi, sigma) with uniform priors U(-1, 1), U(0, 5), U(0, 5), filtered with the
+    optimal proposal; theta* = (0.75, 1, 1); step sizes 0.085 (Langevin) and 0.175 (random walk)."""
+    seed = 12345 + 5
+    rng = np.random.Generator(np.random.PCG64(seed))
+    th = np.array([0.75, 1.0, 1.0])
+    y = simulate_lg(rng, th[:1], th[1:2], th[2:3], None, T)
+    lo = np.array([-1.0, 0.0, 0.0])
+    hi = np.array([1.0, 5.0, 5.0])
+    return Workload("lgssm", LG_OPT, 1, 1, 3, T, N, M, K, th, y, None, proposal,
+                    {"langevin": 0.085, "rw": 0.175}[proposal], 781, seed,
+                    prior_mean=lo, prior_std=hi, prior_kind=UNIFORM_PRIOR)
+
+
+ALL = {"lg1": lg1, "lg4": lg4, "sv": sv, "lg16": lg16, "lgssm": lgssm}
 
 
 def thetas_near(w: Workload, n: int, scale: float = 0.05, seed: int = 4242) -> np.ndarray:
@@ -157,7 +179,7 @@ def serving_stream(n_jobs=256, rate_hz=50.0, seed=12345 + 4, max_T=1000):
     rng = np.random.Generator(np.random.PCG64(seed))
     t = 0.0
     jobs = []
-    names = list(ALL)
+    names = ["lg1", "lg4", "sv", "lg16"]
     for j in range(n_jobs):
         t += rng.exponential(1.0 / rate_hz)
         fam = names[int(rng.integers(len(names)))]

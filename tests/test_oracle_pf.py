@@ -295,3 +295,61 @@ def test_follow_mode_classifies_planted_mismatches():
     f2[t0] = 0
     s = oracle.pf(0, 4, 2, w.H, th, w.y, M, 3, 1, 0, hint_anc=r["anc"], hint_flag=f2)
     assert s["stats"]["flag_mismatch"] >= 1
+
+
+# --------------------------------------------------------------------------- optimal proposal (Sec. IV-A)
+
+def _lgssm_as_lg1(th):
+    """(mu, phi, sigma) -> the LG-diag parameters (a, log q, log r) of the same model."""
+    return np.array([th[0], np.log(th[1]), np.log(th[2])])
+
+
+@pytest.mark.parametrize("scheme", [oracle.SYSTEMATIC, oracle.MULTINOMIAL])
+def test_optimal_proposal_estimate_unbiased_vs_kalman(scheme):
+    """The optimal proposal's weight p(y_t | x_{t-1}) is right only with its proposal mean and
+    variance: together they give an unbiased likelihood estimate (Kalman, 4.5 standard errors)."""
+    w = W.lgssm(T=5)
+    th = np.array([0.6, 1.3, 0.7])
+    ll_kf, _ = kalman.loglik_grad(_lgssm_as_lg1(th), w.y, None, 1, 1)
+    n = 5000
+    ratios = np.empty(n)
+    resampled = 0
+    for row in range(n):
+        r = oracle.pf(oracle.LG_OPT, 1, 1, None, th, w.y, 6, 77, 1, row, scheme=scheme,
+                      ess_frac=1.0, want_grad=False, want_tape=False)
+        ratios[row] = np.exp(r["loglik"] - ll_kf)
+        resampled += r["stats"]["resample_steps"]
+    assert resampled == 4 * n          # every step after the first resampled
+    assert abs(ratios.mean() - 1.0) < 4.5 * ratios.std() / np.sqrt(n)
+
+
+def test_optimal_proposal_single_step_is_exact_in_the_limit():
+    """T = 1: the weights p(y_1 | x_0) with x_0 ~ N(0, 1) average to N(y_1; 0, mu^2 + phi^2 + sigma^2)."""
+    w = W.lgssm(T=1)
+    th = np.array([0.75, 1.0, 1.0])
+    r = oracle.pf(oracle.LG_OPT, 1, 1, None, th, w.y, 1 << 16, 5, 1, 0, want_grad=False, want_tape=False)
+    exact = stats.norm.logpdf(float(w.y[0, 0]), 0.0, np.sqrt(th[0] ** 2 + th[1] ** 2 + th[2] ** 2))
+    assert r["loglik"] == pytest.approx(exact, abs=5e-3)
+
+
+def test_optimal_proposal_gradient_consistent_with_kalman_without_resampling():
+    w = W.lgssm(T=8)
+    th = np.array([0.7, 1.1, 0.9])
+    _, g_lg1 = kalman.loglik_grad(_lgssm_as_lg1(th), w.y, None, 1, 1)
+    g_kf = g_lg1 * np.array([1.0, 1.0 / th[1], 1.0 / th[2]])   # chain rule to (mu, phi, sigma)
+    rows = 8
+    gs = np.array([oracle.pf(oracle.LG_OPT, 1, 1, None, th, w.y, 1 << 15, 31, 1, row, ess_frac=0.0,
+                             want_tape=False)["grad"] for row in range(rows)])
+    se = gs.std(0, ddof=1) / np.sqrt(rows)
+    assert np.all(np.abs(gs.mean(0) - g_kf) < 5 * se + 0.02)
+
+
+@pytest.mark.parametrize("scheme", [oracle.SYSTEMATIC, oracle.MULTINOMIAL])
+def test_optimal_proposal_gradient_matches_fd_of_fixed_tape(scheme):
+    w = W.lgssm(T=60)
+    th = np.array([0.7, 1.1, 0.9])
+    r = oracle.pf(oracle.LG_OPT, 1, 1, None, th, w.y, 64, 13, 4, 5, scheme=scheme, ess_frac=0.8)
+    assert r["stats"]["resample_steps"] > 2
+    for h in (1e-4, 1e-5):
+        fd = _fd_replay(w, th, 64, r["anc"], r["flag"], h, family=oracle.LG_OPT)
+        np.testing.assert_allclose(r["grad"], fd, rtol=2e-5, atol=2e-5 * max(1.0, np.abs(fd).max()))

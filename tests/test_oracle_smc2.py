@@ -114,3 +114,34 @@ def test_sampler_with_particle_filter_runs_and_keeps_invariants():
         assert 1.0 - 1e-9 <= r["ess"] <= 16 + 1e-9
         assert np.all(np.isfinite(r["theta"])) and np.all(np.isfinite(r["grad"]))
     assert np.all(np.isfinite(rec_mean))
+
+
+def test_sampler_with_uniform_prior_finds_quadrature_posterior_mean():
+    """Sec. IV-A's model and uniform priors, exact likelihood: the recycled estimate after the
+    run lies near the posterior mean computed by quadrature over the prior's box."""
+    from oracle import kalman
+    w = W.lgssm(T=60)
+    gm = np.linspace(0.2, 0.99, 60)
+    gp = np.linspace(0.3, 2.0, 60)
+    gs = np.linspace(0.3, 2.0, 60)
+    A, P, S = np.meshgrid(gm, gp, gs, indexing="ij")
+    lp = _scalar_kf_grid(A, np.log(P), np.log(S), w.y)   # flat prior inside the box
+    p = np.exp(lp - lp.max())
+    p /= p.sum()
+    post = np.array([(p * A).sum(), (p * P).sum(), (p * S).sum()])
+    post_sd = np.sqrt(np.array([(p * A * A).sum(), (p * P * P).sum(), (p * S * S).sum()]) - post ** 2)
+
+    def fn(th):
+        if th[1] <= 0.0 or th[2] <= 0.0:
+            return -np.inf, np.zeros(3)
+        ll, g = kalman.loglik_grad(np.array([th[0], np.log(th[1]), np.log(th[2])]), w.y, None, 1, 1)
+        return ll, g * np.array([1.0, 1.0 / th[1], 1.0 / th[2]])
+
+    recs, rec_mean = smc2.run(w.family, 1, 1, None, w.y, 256, 1, 15, 0.05, "langevin", 5,
+                              prior_mean=w.prior_mean, prior_std=w.prior_std, D=3,
+                              loglik_grad_fn=fn, prior_kind=smc2.UNIFORM_PRIOR)
+    final = recs[-1]["mean"]
+    assert np.all(np.abs(final - post) < 0.5 * post_sd + 0.03), (final, post, post_sd)
+    # every draw of iteration 1 lies inside the box
+    th1 = recs[0]["theta"]
+    assert np.all((th1 >= w.prior_mean) & (th1 <= w.prior_std))
