@@ -42,12 +42,21 @@ extern "C" {
  *    Supported shapes (d_x, d_y): (1,1), (4,2), (16,16) with H = identity.
  *  SMC2_SV: theta = (mu, atanh phi, log sigma), D = 3, d_x = d_y = 1;
  *    x_0 = mu + sigma/sqrt(1-phi^2) eps, x_t = mu + phi (x_{t-1} - mu) + sigma eta_t,
- *    y_t = exp(x_t / 2) eps_t. */
-enum { SMC2_LG_DIAG = 0, SMC2_SV = 1 };
+ *    y_t = exp(x_t / 2) eps_t.
+ *  SMC2_LG_OPT: the linear-Gaussian model of Sec. IV-A, theta = (mu, phi, sigma), D = 3,
+ *    d_x = d_y = 1; x_0 ~ N(0, 1), x_t ~ N(mu x_{t-1}, phi^2), y_t ~ N(x_t, sigma^2),
+ *    filtered with the "optimal" proposal N(rho^2 (y_t/sigma^2 + mu x_{t-1}/phi^2), rho^2),
+ *    1/rho^2 = 1/phi^2 + 1/sigma^2, and weights p(y_t | x_{t-1}) = N(y_t; mu x_{t-1},
+ *    phi^2 + sigma^2). */
+enum { SMC2_LG_DIAG = 0, SMC2_SV = 1, SMC2_LG_OPT = 2 };
 /* Outer proposals (Sec. III-D): SMC0 random walk, SMC1 Langevin. */
 enum { SMC2_RW = 0, SMC2_LANGEVIN = 1 };
 /* Particle-filter resampler (Sec. II-B, App. B). */
 enum { SMC2_SYSTEMATIC = 0, SMC2_MULTINOMIAL = 1 };
+/* Prior on theta: Gaussian N(prior_mean, diag(prior_std^2)), or uniform on the box
+ * [prior_mean[d], prior_std[d]] (Sec. IV-A), whose iteration-1 draws map the sampler's
+ * normals through the standard normal CDF. */
+enum { SMC2_PRIOR_GAUSSIAN = 0, SMC2_PRIOR_UNIFORM = 1 };
 
 typedef struct smc2_config {
     uint32_t struct_size;       /* sizeof(smc2_config): versioning */
@@ -68,6 +77,7 @@ typedef struct smc2_config {
     int32_t ckpt_every;         /* adjoint checkpoint interval in steps; 0 = automatic, 1 = store all */
     int32_t particles_per_thread; /* 0 = automatic (autotuned), else 1, 2, 4 or 8 */
     void* stream;               /* cudaStream_t for all work of the handle; NULL = a private stream */
+    int32_t prior_kind;         /* SMC2_PRIOR_GAUSSIAN (default) or SMC2_PRIOR_UNIFORM */
 } smc2_config;
 
 /* Fill defaults: struct_size, ess_frac 0.5, K_iters 10, systematic, Langevin, gamma 0.1. */

@@ -15,7 +15,8 @@ SMC2_OK = 0
 SMC2_PENDING = 1
 ERRORS = {-1: "SMC2_E_INVAL", -2: "SMC2_E_NOMEM", -3: "SMC2_E_CUDA", -4: "SMC2_E_TIMEOUT",
           -5: "SMC2_E_NOTFOUND", -6: "SMC2_E_BUSY"}
-LG_DIAG, SV = 0, 1
+LG_DIAG, SV, LG_OPT = 0, 1, 2
+PRIOR_GAUSSIAN, PRIOR_UNIFORM = 0, 1
 RW, LANGEVIN = 0, 1
 SYSTEMATIC, MULTINOMIAL = 0, 1
 
@@ -52,6 +53,7 @@ class Config(ctypes.Structure):
         ("ckpt_every", ctypes.c_int32),
         ("particles_per_thread", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
+        ("prior_kind", ctypes.c_int32),
     ]
 
 
@@ -164,7 +166,8 @@ def _ptr(t):
 
 def make_config(family, dx, dy, T, N, M, D, y, H=None, prior_mean=None, prior_std=None,
                 proposal=LANGEVIN, gamma=0.1, K_iters=10, pf_resample=SYSTEMATIC, ess_frac=0.5,
-                seed=777, ckpt_every=0, particles_per_thread=0, stream=None, y_on_device=False):
+                seed=777, ckpt_every=0, particles_per_thread=0, stream=None, y_on_device=False,
+                prior_kind=PRIOR_GAUSSIAN):
     """Build a Config; numpy arrays referenced by it are kept alive on the returned object."""
     import numpy as np
     lib = load()
@@ -199,6 +202,7 @@ def make_config(family, dx, dy, T, N, M, D, y, H=None, prior_mean=None, prior_st
     c.ckpt_every = int(ckpt_every)
     c.particles_per_thread = int(particles_per_thread)
     c.stream = stream
+    c.prior_kind = int(prior_kind)
     c._keep = keep
     return c
 
@@ -405,7 +409,8 @@ def config_for(workload, **kw):
     """Config for a workloads.Workload (sizes, data and step size taken from it)."""
     prop = LANGEVIN if workload.proposal == "langevin" else RW
     args = dict(proposal=prop, gamma=workload.gamma, K_iters=workload.K, seed=workload.seed,
-                prior_mean=workload.prior_mean, prior_std=workload.prior_std)
+                prior_mean=workload.prior_mean, prior_std=workload.prior_std,
+                prior_kind=getattr(workload, "prior_kind", PRIOR_GAUSSIAN))
     args.update(kw)
     return make_config(workload.family, workload.dx, workload.dy, workload.T, workload.N, workload.M,
                        workload.D, workload.y, workload.H, **args)

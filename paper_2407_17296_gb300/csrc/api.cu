@@ -30,6 +30,8 @@ pf_kernel_fn lookup_sv_fwd(int P, int regs);
 pf_kernel_fn lookup_sv_bwd(int P, int regs);
 pf_kernel_fn lookup_lg16_fwd(int P, int regs);
 pf_kernel_fn lookup_lg16_bwd(int P, int regs);
+pf_kernel_fn lookup_opt_fwd(int P, int regs);
+pf_kernel_fn lookup_opt_bwd(int P, int regs);
 }  // namespace smc2
 
 using namespace smc2;
@@ -73,8 +75,8 @@ extern "C" void smc2_config_init(smc2_config* c) {
 // ------------------------------------------------------------------ validation / sizing
 
 int smc2::family_dims(const smc2_config* c, int* D) {
-    if (c->model_family == SMC2_SV) {
-        if (c->d_x != 1 || c->d_y != 1) return fail(SMC2_E_INVAL, "SV needs d_x = d_y = 1");
+    if (c->model_family == SMC2_SV || c->model_family == SMC2_LG_OPT) {
+        if (c->d_x != 1 || c->d_y != 1) return fail(SMC2_E_INVAL, "this model family needs d_x = d_y = 1");
         *D = 3;
         return SMC2_OK;
     }
@@ -94,6 +96,7 @@ int smc2::family_dims(const smc2_config* c, int* D) {
 pf_kernel_fn smc2::lookup_forward(const smc2_config* c, int P, int regs) {
     if (!variant_fits(c, P, regs)) return nullptr;
     if (c->model_family == SMC2_SV) return lookup_sv_fwd(P, regs);
+    if (c->model_family == SMC2_LG_OPT) return lookup_opt_fwd(P, regs);
     if (c->d_x == 1) return lookup_lg1_fwd(P, regs);
     if (c->d_x == 4) return lookup_lg4_fwd(P, regs);
     if (c->d_x == 16) return lookup_lg16_fwd(P, regs);
@@ -103,6 +106,7 @@ pf_kernel_fn smc2::lookup_forward(const smc2_config* c, int P, int regs) {
 pf_kernel_fn smc2::lookup_backward(const smc2_config* c, int P, int regs) {
     if (!variant_fits(c, P, regs)) return nullptr;
     if (c->model_family == SMC2_SV) return lookup_sv_bwd(P, regs);
+    if (c->model_family == SMC2_LG_OPT) return lookup_opt_bwd(P, regs);
     if (c->d_x == 1) return lookup_lg1_bwd(P, regs);
     if (c->d_x == 4) return lookup_lg4_bwd(P, regs);
     if (c->d_x == 16) return lookup_lg16_bwd(P, regs);
@@ -192,9 +196,17 @@ int smc2::validate(const smc2_config* c, int* D) {
             SmemLayout(c->M, c->d_x, *D, false, G, ring_slots(c->M, c->d_x, *D, G)).total > kSmemLimit)
             return fail(SMC2_E_INVAL, "M too large for this model (shared memory of a filter block)");
     }
-    if (c->prior_std)
+    if (c->prior_kind != SMC2_PRIOR_GAUSSIAN && c->prior_kind != SMC2_PRIOR_UNIFORM)
+        return fail(SMC2_E_INVAL, "unknown prior_kind");
+    if (c->prior_kind == SMC2_PRIOR_UNIFORM) {
+        if (!c->prior_mean || !c->prior_std) return fail(SMC2_E_INVAL, "a uniform prior needs its bounds");
+        for (int d = 0; d < *D; ++d)
+            if (!(c->prior_std[d] > c->prior_mean[d]))
+                return fail(SMC2_E_INVAL, "uniform prior bounds must satisfy lower < upper");
+    } else if (c->prior_std) {
         for (int d = 0; d < *D; ++d)
             if (!(c->prior_std[d] > 0.0)) return fail(SMC2_E_INVAL, "prior_std must be positive");
+    }
     return SMC2_OK;
 }
 
@@ -478,6 +490,7 @@ OuterArgs smc2::make_outer_args(smc2_handle* h) {
     o.seed_hi = (uint32_t)(h->cfg.seed >> 32);
     o.prior_mean = h->prior_m;
     o.prior_std = h->prior_s;
+    o.prior_uniform = h->cfg.prior_kind == SMC2_PRIOR_UNIFORM;
     o.k_dev = h->k_dev;
     o.theta = h->theta;
     o.theta_new = h->theta_new;

@@ -28,6 +28,7 @@ struct LGDiag {
     static constexpr int DX = DX_, DY = DY_, D = 2 * DX_ + DY_;
     static constexpr int G = 1, DL = DX_, DTH = D;
     static constexpr bool HIDENT = HIDENT_;
+    static constexpr bool kFused = false;  // separate transition and log g(y|x)
     static constexpr int kFamily = 0;
     struct Params {
         float a[DX], q[DX], rinv[DY];
@@ -132,6 +133,7 @@ struct SV {
     static constexpr int DX = 1, DY = 1, D = 3;
     static constexpr int G = 1, DL = 1, DTH = 3;
     static constexpr bool HIDENT = true;
+    static constexpr bool kFused = false;
     static constexpr int kFamily = 1;
     struct Params {
         float mu, phi, sig, sd0, omp2;  // omp2 = 1 - phi^2
@@ -200,6 +202,7 @@ struct LGSplit {
     static constexpr int DX = DX_, DY = DX_, D = 3 * DX_;
     static constexpr int G = G_, DL = DX_ / G_, DTH = 3 * (DX_ / G_);
     static constexpr bool HIDENT = true;
+    static constexpr bool kFused = false;
     static constexpr int kFamily = 0;
     static_assert(DX_ % G_ == 0, "dimensions must split evenly over the lanes");
     struct Params {
@@ -283,6 +286,80 @@ struct LGSplit {
 
     __device__ __forceinline__ static void bwd_init(const LaneParams&, const float (&)[DL], const float (&)[DL],
                                                     float (&)[DTH]) {}
+};
+
+// The linear-Gaussian model of Sec. IV-A, theta = (mu, phi, sigma) in their own units:
+// x_0 ~ N(0, 1), x_t | x_{t-1} ~ N(mu x_{t-1}, phi^2), y_t | x_t ~ N(x_t, sigma^2), filtered
+// with the optimal proposal q(x_t | x_{t-1}, y_t) = N(a x_{t-1} + b y_t, rho^2), where
+// s2 = phi^2 + sigma^2, a = sigma^2 mu / s2, b = phi^2 / s2, rho = phi sigma / sqrt(s2);
+// its weight (Eq. weightupdate) is p(y_t | x_{t-1}) = N(y_t; mu x_{t-1}, s2), a function of
+// the previous state, so the model provides one fused step (weight, then propagation) and
+// its adjoint instead of separate transition / log g pieces.
+struct LGOpt {
+    static constexpr int DX = 1, DY = 1, D = 3;
+    static constexpr int G = 1, DL = 1, DTH = 3;
+    static constexpr bool HIDENT = true;
+    static constexpr bool kFused = true;
+    static constexpr int kFamily = 2;
+    struct Params {
+        float mu, a, b, rho, rhoinv, s2inv, cst;  // cst = -(log 2 pi + log s2)/2
+        float da_dmu, da_dphi, da_dsig, db_dphi, db_dsig, dr_dphi, dr_dsig, ds2_dphi, ds2_dsig;
+    };
+    using LaneParams = Params;
+    __device__ __forceinline__ static void lane_params(const Params& p, int, LaneParams& lp) { lp = p; }
+    __device__ __forceinline__ static int theta_index(int l, int) { return l; }
+
+    __device__ static void make_params(const double* th, const float*, Params& p) {
+        const double mu = th[0], phi = th[1], sig = th[2];
+        const double p2 = phi * phi, q2 = sig * sig, s2 = p2 + q2, s32 = s2 * sqrt(s2);
+        p.mu = (float)mu;
+        p.a = (float)(q2 * mu / s2);
+        p.b = (float)(p2 / s2);
+        p.rho = (float)(phi * sig / sqrt(s2));
+        p.rhoinv = (float)(sqrt(s2) / (phi * sig));
+        p.s2inv = (float)(1.0 / s2);
+        p.cst = (float)(-0.5 * (1.8378770664093454836 + log(s2)));
+        p.da_dmu = (float)(q2 / s2);
+        p.da_dphi = (float)(-2.0 * phi * q2 * mu / (s2 * s2));
+        p.da_dsig = (float)(2.0 * sig * mu * p2 / (s2 * s2));
+        p.db_dphi = (float)(2.0 * phi * q2 / (s2 * s2));
+        p.db_dsig = (float)(-2.0 * p2 * sig / (s2 * s2));
+        p.dr_dphi = (float)(sig * q2 / s32);
+        p.dr_dsig = (float)(phi * p2 / s32);
+        p.ds2_dphi = (float)(2.0 * phi);
+        p.ds2_dsig = (float)(2.0 * sig);
+    }
+
+    __device__ __forceinline__ static void init(const Params&, const float (&eps)[1], float (&x)[1]) { x[0] = eps[0]; }
+
+    // log p(y_t | x_{t-1}), then x_t from the optimal proposal
+    __device__ __forceinline__ static float step(const Params& p, float (&x)[1], const float (&eps)[1],
+                                                 const float* __restrict__ yt) {
+        const float y = __ldg(yt);
+        const float r = y - p.mu * x[0];
+        const float g = p.cst - 0.5f * r * r * p.s2inv;
+        x[0] = fmaf(p.a, x[0], fmaf(p.b, y, p.rho * eps[0]));
+        return g;
+    }
+
+    // adjoint of step: xt = x_t, xp = x'_{t-1}; xbar in: adjoint of x_t, out: of x'_{t-1}
+    __device__ __forceinline__ static void bwd_step(const Params& p, const float (&xt)[1], const float (&xp)[1],
+                                                    const float* __restrict__ yt, float lwbar, float (&xbar)[1],
+                                                    float (&thb)[3]) {
+        const float y = __ldg(yt);
+        const float r = y - p.mu * xp[0];
+        const float e = (xt[0] - p.a * xp[0] - p.b * y) * p.rhoinv;  // the proposal's eps
+        const float wr = lwbar * r * p.s2inv;                           // lwbar d log g / d(mu x')
+        const float ws2 = lwbar * (0.5f * r * r * p.s2inv - 0.5f) * p.s2inv;  // lwbar d log g / d s2
+        const float xb = xbar[0];
+        thb[0] += xb * xp[0] * p.da_dmu + wr * xp[0];
+        thb[1] += xb * (xp[0] * p.da_dphi + y * p.db_dphi + e * p.dr_dphi) + ws2 * p.ds2_dphi;
+        thb[2] += xb * (xp[0] * p.da_dsig + y * p.db_dsig + e * p.dr_dsig) + ws2 * p.ds2_dsig;
+        xbar[0] = p.a * xb + wr * p.mu;
+    }
+
+    __device__ __forceinline__ static void bwd_init(const Params&, const float (&)[1], const float (&)[1],
+                                                    float (&)[3]) {}
 };
 
 }  // namespace smc2

@@ -53,7 +53,9 @@ __global__ void outer_propose_kernel(OuterArgs a) {
         const double xi = outer_normal(key, d);
         double v;
         if (k == 1u) {
-            v = a.prior_mean[d] + a.prior_std[d] * xi;
+            // prior draw; a uniform prior maps xi through the standard normal CDF
+            v = a.prior_uniform ? a.prior_mean[d] + (a.prior_std[d] - a.prior_mean[d]) * (0.5 * erfc(-xi * 0.70710678118654752440))
+                                : a.prior_mean[d] + a.prior_std[d] * xi;
         } else {
             const double drift = a.langevin ? 0.5 * a.gamma * a.gamma * a.gradpi[idx] : 0.0;
             v = a.theta[idx] + drift + a.gamma * xi;
@@ -105,15 +107,28 @@ __device__ double log_prior(const double* th, const double* m, const double* inv
     return acc;
 }
 
-// prior constants shared by a block: pinv[d] = 1/prior_std[d], pinv[64] = -sum log s - D/2 log 2 pi
+// prior constants shared by a block.  Gaussian: pinv[d] = 1/prior_std[d], pinv[64] =
+// -sum log s - D/2 log 2 pi.  Uniform: pinv[d] = 0 (flat inside the box), pinv[64] =
+// -sum log(upper - lower).
 __device__ void prior_constants(const OuterArgs& a, double* pinv) {
-    for (int d = threadIdx.x; d < a.D; d += blockDim.x) pinv[d] = 1.0 / a.prior_std[d];
+    for (int d = threadIdx.x; d < a.D; d += blockDim.x) pinv[d] = a.prior_uniform ? 0.0 : 1.0 / a.prior_std[d];
     if (threadIdx.x == 0) {
         double c = 0.0;
-        for (int d = 0; d < a.D; ++d) c -= log(a.prior_std[d]) + 0.9189385332046727418;
+        for (int d = 0; d < a.D; ++d)
+            c -= a.prior_uniform ? log(a.prior_std[d] - a.prior_mean[d]) : log(a.prior_std[d]) + 0.9189385332046727418;
         pinv[64] = c;
     }
     __syncthreads();
+}
+
+// log prior density at th: Gaussian, or uniform on the box (-inf outside it)
+__device__ double log_prior_at(const OuterArgs& a, const double* th, const double* pinv) {
+    if (a.prior_uniform) {
+        for (int d = 0; d < a.D; ++d)
+            if (!(th[d] >= a.prior_mean[d] && th[d] <= a.prior_std[d])) return -INFINITY;
+        return pinv[64];
+    }
+    return log_prior(th, a.prior_mean, pinv, pinv[64], a.D);
 }
 
 // 1. pseudo-marginal update of every sample with its particle-filter result (one thread a
@@ -128,7 +143,7 @@ __global__ void outer_weight_kernel(OuterArgs a) {
     if (i >= N) return;
     const double* thn = a.theta_new + (size_t)i * D;
     const double lln = a.ll_new[i];
-    const double lpn = (lln > -INFINITY) ? log_prior(thn, a.prior_mean, pinv, pinv[64], D) + lln : -INFINITY;
+    const double lpn = (lln > -INFINITY) ? log_prior_at(a, thn, pinv) + lln : -INFINITY;
     double lw;
     if (k == 1u) {
         lw = lln;  // pi / q_1 with q_1 the prior

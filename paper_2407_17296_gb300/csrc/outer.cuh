@@ -10,7 +10,8 @@ struct OuterArgs {
     int langevin;                 // 1: SMC1 Langevin proposal, 0: SMC0 random walk
     uint32_t seed_lo, seed_hi;
     const double* prior_mean;     // [D]
-    const double* prior_std;      // [D]
+    const double* prior_std;      // [D]  (uniform prior: the box is [prior_mean, prior_std])
+    int prior_uniform;            // 1: uniform prior on the box
     uint32_t* k_dev;              // iteration counter (1-based), advanced by outer_update
     double* theta;                // [N][D] current samples
     double* theta_new;            // [N][D] proposals (input of the particle filters)

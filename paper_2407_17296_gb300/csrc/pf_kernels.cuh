@@ -692,8 +692,13 @@ __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, cons
             const float* yt = a.y + (size_t)(t - 1) * DY + (G > 1 ? gl * DL : 0);
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                Mdl::transition(prm, x[p], reinterpret_cast<const float(&)[DL]>(eps[p * DL]));
-                float g = Mdl::loglik(prm, x[p], yt);
+                float g;
+                if constexpr (Mdl::kFused) {
+                    g = Mdl::step(prm, x[p], reinterpret_cast<const float(&)[DL]>(eps[p * DL]), yt);
+                } else {
+                    Mdl::transition(prm, x[p], reinterpret_cast<const float(&)[DL]>(eps[p * DL]));
+                    g = Mdl::loglik(prm, x[p], yt);
+                }
                 if constexpr (G > 1) g = group_sum<G>(g) + prm.cst;  // whole-particle log g
                 lw[p] += g;  // padding particles stay at -inf
             }
@@ -827,8 +832,13 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
                 const float mt = mstep[t];
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
-                    Mdl::transition(prm, x[p], reinterpret_cast<const float(&)[DL]>(eps[p * DL]));
-                    float gg = Mdl::loglik(prm, x[p], yt);
+                    float gg;
+                    if constexpr (Mdl::kFused) {
+                        gg = Mdl::step(prm, x[p], reinterpret_cast<const float(&)[DL]>(eps[p * DL]), yt);
+                    } else {
+                        Mdl::transition(prm, x[p], reinterpret_cast<const float(&)[DL]>(eps[p * DL]));
+                        gg = Mdl::loglik(prm, x[p], yt);
+                    }
                     if constexpr (G > 1) gg = group_sum<G>(gg) + prm.cst;
                     if (j0 + p < M) lw[p] += gg;
                     lw[p] -= mt;
@@ -899,7 +909,8 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
             const float* yt = a.y + (size_t)(t - 1) * DY + (G > 1 ? gl * DL : 0);
             // padding particles have zero cotangents and finite (clamped) states: no guards
 #pragma unroll
-            for (int p = 0; p < P; ++p) Mdl::bwd_obs(prm, xt[p], yt, lwbar[p], xbar[p], thb);
+            for (int p = 0; p < P; ++p)
+                if constexpr (!Mdl::kFused) Mdl::bwd_obs(prm, xt[p], yt, lwbar[p], xbar[p], thb);
             int ai[P];
             const uint16_t* ancs = ancbuf + (nres & 1u) * (uint32_t)tape_stride(M);
             const float* lwrow = lwbuf + (nres & 1u) * (uint32_t)padded_particles(M);
@@ -919,7 +930,10 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
 #pragma unroll
             for (int p = 0; p < P; ++p) read_staged<DX, DL>(sp, ai[p], gl, xp[p]);
 #pragma unroll
-            for (int p = 0; p < P; ++p) Mdl::bwd_trans(prm, xt[p], xp[p], xbar[p], thb);
+            for (int p = 0; p < P; ++p) {
+                if constexpr (Mdl::kFused) Mdl::bwd_step(prm, xt[p], xp[p], yt, lwbar[p], xbar[p], thb);
+                else Mdl::bwd_trans(prm, xt[p], xp[p], xbar[p], thb);
+            }
             if (fl) {
                 // adjoint of the gather x'_i = x_{a_i}: sum the cotangents of each parent's
                 // offspring, staged in the rows of x_t (each thread has read its own)

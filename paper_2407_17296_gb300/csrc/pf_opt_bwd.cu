@@ -1,0 +1,16 @@
+// pf_opt_bwd.cu -- backward-pass kernel variants for one model shape
+// (LGOpt).  One translation unit per model and pass so the build compiles in parallel.
+#include "pf_kernels.cuh"
+
+namespace smc2 {
+
+pf_kernel_fn lookup_opt_bwd(int P, int regs) {
+    using Mdl = LGOpt;
+#define SMC2_CASE(PP, RR) \
+    if (P == PP && regs == RR) return &launch_backward<Mdl, PP, RR>;
+    SMC2_PF_VARIANTS(SMC2_CASE)
+#undef SMC2_CASE
+    return nullptr;
+}
+
+}  // namespace smc2

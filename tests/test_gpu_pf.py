@@ -20,7 +20,7 @@ def _report(name, agg):
 
 
 @pytest.mark.parametrize("make,T,M,n", [(W.lg1, 80, 300, 9), (W.lg4, 60, 1000, 7), (W.sv, 90, 517, 6),
-                                        (W.lg16, 30, 250, 4)])
+                                        (W.lg16, 30, 250, 4), (W.lgssm, 80, 250, 6)])
 @pytest.mark.parametrize("scheme", [0, 1])
 @pytest.mark.parametrize("kc", [1, 7])
 def test_parity_small(make, T, M, n, scheme, kc):
@@ -68,6 +68,18 @@ def test_parity_lg16_particles_per_thread(ppt):
     theta = W.thetas_near(w, 2, 0.03, seed=6)
     ll, g, anc, flag = gpu_pf(w, theta, particles_per_thread=ppt, ckpt_every=6)
     check_rows(w, theta, ll, g, anc, flag, range(2))
+
+
+def test_parity_full_size_lgssm():
+    """The model of Sec. IV-A with the optimal proposal at the paper's sizes (N=64, M=250,
+    T=500); every filter checked."""
+    w = W.lgssm()
+    theta = W.thetas_near(w, w.N, 0.05, seed=24)
+    ll, g, anc, flag = gpu_pf(w, theta, iteration=2, ess_frac=0.9)
+    assert np.all(np.isfinite(ll)) and np.all(np.isfinite(g))
+    agg = check_rows(w, theta, ll, g, anc, flag, range(w.N), iteration=2, ess_frac=0.9)
+    assert agg["resample_steps"] > 0
+    _report("lgssm full", agg)
 
 
 def test_parity_full_size_sv():

@@ -105,6 +105,20 @@ def test_smc2_lg16_small_matches_oracle():
     _compare(recs, ref, stable=_stable_lg(16))
 
 
+@pytest.mark.parametrize("proposal", ["langevin", "rw"])
+def test_smc2_lgssm_matches_oracle(proposal):
+    """Sec. IV-A's model with the optimal proposal and uniform priors U(-1,1), U(0,5), U(0,5):
+    samples proposed outside the box get weight zero on both sides."""
+    w = W.lgssm(T=100, N=32, M=128, K=5, proposal=proposal)
+    recs, hints = _run_gpu(w, w.K)
+    ref, rec_ref = osmc2.run(w.family, 1, 1, None, w.y, w.N, w.M, w.K, w.gamma, proposal, w.seed,
+                             prior_mean=w.prior_mean, prior_std=w.prior_std, D=3,
+                             prior_kind=osmc2.UNIFORM_PRIOR,
+                             hints=hints, band=BAND, flag_band=BAND, band_rel=BAND_REL)
+    inside = lambda th: bool(np.all(th >= w.prior_mean) and np.all(th <= w.prior_std))
+    _compare(recs, ref, rec_ref, stable=inside)
+
+
 def test_smc2_invariants_full_lg4():
     """Full-size linear-Gaussian job: three iterations stay finite with ESS in [1, N]."""
     w = W.lg4(K=3)
