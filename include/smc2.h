@@ -228,6 +228,14 @@ int pf_loglik_grad_static(const smc2_config* cfg, const double* theta_dev, int n
  * SMC2_E_TIMEOUT. */
 int smc2_get_status(smc2_handle* h, int* status, int clear);
 
+/* Failure detection without a fault: runs one block whose warps wait on a barrier that
+ * nothing completes, with the filter kernels' bounded wait cut to `polls` polls; the wait
+ * gives up, the block records the timeout in a device status word and finishes.  Sets
+ * *timed_out to 1 when the status word says so.  The CUDA context stays usable.  No
+ * counterpart in the paper.  Errors: SMC2_E_INVAL (polls < 1, NULL), SMC2_E_NOMEM,
+ * SMC2_E_CUDA. */
+int smc2_selftest_bounded_wait(int polls, int* timed_out);
+
 /* Replace the observations (T x d_y FP32, host) of an existing handle; the copy is
  * stream-ordered on the handle's stream. */
 int smc2_set_observations(smc2_handle* h, const float* y_host);

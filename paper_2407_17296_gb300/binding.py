@@ -24,7 +24,7 @@ SYSTEMATIC, MULTINOMIAL = 0, 1
 EXPORTS = ("smc2_config_init", "smc2_create", "pf_loglik_grad", "pf_loglik_grad_rows",
            "pf_loglik_grad_host", "smc2_step", "smc2_step_filters", "smc2_step_update", "smc2_set_step_timing", "smc2_get_step_timing", "smc2_get_samples", "smc2_get_state",
            "smc2_get_trace", "smc2_set_observations", "smc2_footprint", "smc2_destroy",
-           "smc2_autotune", "smc2_get_launch", "smc2_set_launch", "smc2_get_status", "smc2_kernel_launches", "smc2_last_error", "smc2_server_create",
+           "smc2_autotune", "smc2_get_launch", "smc2_set_launch", "smc2_get_status", "smc2_selftest_bounded_wait", "smc2_kernel_launches", "smc2_last_error", "smc2_server_create",
            "smc2_submit", "smc2_poll", "smc2_cancel", "smc2_server_destroy",
            "pf_loglik_grad_static")
 
@@ -119,6 +119,7 @@ def load(path: str = LIB_PATH):
         "smc2_get_launch": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int)]),
         "smc2_set_launch": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_int)]),
         "smc2_get_status": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
+        "smc2_selftest_bounded_wait": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
         "smc2_kernel_launches": (u64, []),
         "smc2_last_error": (ctypes.c_char_p, []),
         "smc2_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(vp)]),
@@ -397,6 +398,13 @@ def set_launch(cfg: Config, launch):
     cfg's shape; handles created afterwards use it."""
     arr = (ctypes.c_int * 5)(*[int(v) for v in launch])
     check(load().smc2_set_launch(ctypes.byref(cfg), arr), "smc2_set_launch")
+
+
+def selftest_bounded_wait(polls=1000) -> bool:
+    """Run a block whose wait nothing completes; True if the bounded wait reported it."""
+    out = ctypes.c_int(0)
+    check(load().smc2_selftest_bounded_wait(int(polls), ctypes.byref(out)), "smc2_selftest_bounded_wait")
+    return bool(out.value)
 
 
 def footprint(cfg: Config) -> int:

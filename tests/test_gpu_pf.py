@@ -207,3 +207,14 @@ def test_parity_large_blocks(make, M, n):
     for scheme in (0, 1):
         ll, g, anc, flag = gpu_pf(w, theta, pf_resample=scheme)
         check_rows(w, theta, ll, g, anc, flag, range(n), scheme=scheme)
+
+
+def test_bounded_wait_reports_timeout_and_context_survives():
+    """Failure detection without a fault: a wait that nothing completes gives up after its poll
+    limit, the status word says so, and the filters still run afterwards."""
+    from paper_2407_17296_gb300 import binding
+    assert binding.selftest_bounded_wait(2000) is True
+    w = W.lg1(T=10, N=2, M=64)
+    theta = W.thetas_near(w, 2, 0.05)
+    ll, g, anc, flag = gpu_pf(w, theta)
+    assert np.all(np.isfinite(ll))
