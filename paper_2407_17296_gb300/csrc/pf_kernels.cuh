@@ -6,8 +6,8 @@
 // group holds state dimensions gl*DL .. gl*DL+DL-1 (DL = d_x / G) of those particles
 // in registers for the whole pass, and per-particle scalars (log-weights, their
 // cotangents) are replicated across the group.  G = 1 for small d_x; the
-// 16-dimensional model spreads each particle over G = 4 lanes.  Cross-particle work per step goes through warp shuffles and a
-// little shared memory:
+// 16-dimensional model spreads each particle over G = 4 lanes.  Cross-particle work per
+// step goes through warp shuffles and a little shared memory:
 //   * log-sum-exp and ESS: one block reduction of (max, sum e, sum e^2);
 //   * resampling: an exact 64-bit fixed-point prefix sum of the weights
 //     (monotone and independent of summation order), offspring ranges from
@@ -19,7 +19,9 @@
 //                               log w <- LSE(log w) - log M   (Eq. weightresample)
 //   x_t = f(x_{t-1}, theta, eps_t)                             (Eq. reparam_epsilon)
 //   log w_t = log w_{t-1} + log g(y_t | x_t)                   (Eq. priorproposalweight)
-//   log p-hat += LSE(log w_t) - LSE(log w_{t-1})  in FP64      (Eq. likelihood_pf_)
+//   log p-hat = sum_t LSE(log w_t) - LSE(log w_{t-1}), in FP64 (Eq. likelihood_pf_)
+// (models with a fused step -- the optimal proposal of Sec. IV-A -- weight by
+// p(y_t | x_{t-1}) before propagating with a proposal that depends on y_t).
 // The log-weights are recentred by their maximum after every step so that the
 // important particles sit near 0 in FP32; the offsets cancel in the increments.
 //
@@ -31,10 +33,13 @@
 // each parent's offspring (the adjoint of x' = x^kappa, with d kappa/d theta = 0).
 //
 // Trajectory storage for the adjoint (checkpointing): with interval kc = 1 the
-// forward pass stores (x_t, log w_t) for every t; with kc > 1 it stores them at
+// forward pass stores x_t for every t and log w_t where the adjoint needs it (after
+// steps followed by resampling, and at T); with kc > 1 it stores (x_t, log w_t) at
 // t = 0, kc, 2kc, ... and the adjoint recomputes each segment from its checkpoint
-// (same Philox numbers, ancestors read from the tape) into a per-filter scratch
-// of kc steps before sweeping it backwards.
+// (same Philox numbers, ancestors read from the tape) into a per-filter scratch of kc
+// steps before sweeping it backwards.  The sweep streams state slices through a
+// shared-memory ring filled by bulk asynchronous copies (ring.cuh); the tape row and
+// log-weights of a resampling step arrive one step ahead by asynchronous copies.
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
