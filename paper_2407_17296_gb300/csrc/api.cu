@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <new>
 #include <string>
 
 #include "../../include/smc2.h"
@@ -244,9 +245,9 @@ static void free_handle_memory(smc2_handle* h) {
                     h->gradpi, h->loglik, h->ll_new, h->grad_new, h->tmp, h->stats, h->outer_anc,
                     h->k_dev, h->status, h->xck, h->lwck, h->xseg, h->lwseg, h->anc, h->flag, h->mstep, h->lstep};
     for (void* p : ptrs)
-        if (p) cudaFree(p);
-    if (h->h_stats) cudaFreeHost(h->h_stats);
-    if (h->h_status) cudaFreeHost(h->h_status);
+        if (p) cudaFreeAsync(p, h->stream);
+    delete[] h->h_stats;
+    delete[] h->h_status;
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
     for (cudaEvent_t e : h->ev)
         if (e) cudaEventDestroy(e);
@@ -321,18 +322,20 @@ extern "C" int smc2_create(const smc2_config* cfg, smc2_handle** out) {
         {(void**)&h->mstep, s.steps / 2},
         {(void**)&h->lstep, s.steps / 2},
     };
+    // stream-ordered allocations: creating or destroying a handle never waits for the work
+    // of other handles (a served job that finishes does not stall the ones still running)
     for (auto& a : allocs) {
         if (a.bytes == 0) continue;
-        cudaError_t e = cudaMalloc(a.p, a.bytes);
+        cudaError_t e = cudaMallocAsync(a.p, a.bytes, h->stream);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return cleanup(e == cudaErrorMemoryAllocation ? SMC2_E_NOMEM : SMC2_E_CUDA,
-                           std::string("cudaMalloc: ") + cudaGetErrorString(e));
+                           std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
         }
     }
-    if (cudaMallocHost((void**)&h->h_stats, sizeof(double) * (kStatsHead + 2 * D)) != cudaSuccess ||
-        cudaMallocHost((void**)&h->h_status, sizeof(int)) != cudaSuccess)
-        return cleanup(SMC2_E_NOMEM, "cudaMallocHost failed");
+    h->h_stats = new (std::nothrow) double[kStatsHead + 2 * D];
+    h->h_status = new (std::nothrow) int[1];
+    if (!h->h_stats || !h->h_status) return cleanup(SMC2_E_NOMEM, "host allocation failed");
     // inputs
     const cudaMemcpyKind ykind = cfg->y_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     bool ok = cudaMemcpyAsync(h->y, cfg->y, sizeof(float) * T * cfg->d_y, ykind, h->stream) == cudaSuccess;
@@ -341,14 +344,17 @@ extern "C" int smc2_create(const smc2_config* cfg, smc2_handle** out) {
         for (int r = 0; r < cfg->d_y; ++r)
             for (int c = 0; c < cfg->d_x; ++c)
                 Hh[r * cfg->d_x + c] = cfg->H ? cfg->H[r * cfg->d_x + c] : (r == c ? 1.f : 0.f);
-        ok = ok && cudaMemcpy(h->H, Hh, sizeof(float) * cfg->d_y * cfg->d_x, cudaMemcpyHostToDevice) == cudaSuccess;
+        ok = ok && cudaMemcpyAsync(h->H, Hh, sizeof(float) * cfg->d_y * cfg->d_x, cudaMemcpyHostToDevice,
+                                   h->stream) == cudaSuccess;
         double pm[64], ps[64];
         for (int d = 0; d < D; ++d) {
             pm[d] = cfg->prior_mean ? cfg->prior_mean[d] : 0.0;
             ps[d] = cfg->prior_std ? cfg->prior_std[d] : 1.0;
         }
-        ok = ok && cudaMemcpy(h->prior_m, pm, sizeof(double) * D, cudaMemcpyHostToDevice) == cudaSuccess;
-        ok = ok && cudaMemcpy(h->prior_s, ps, sizeof(double) * D, cudaMemcpyHostToDevice) == cudaSuccess;
+        ok = ok && cudaMemcpyAsync(h->prior_m, pm, sizeof(double) * D, cudaMemcpyHostToDevice, h->stream) == cudaSuccess;
+        ok = ok && cudaMemcpyAsync(h->prior_s, ps, sizeof(double) * D, cudaMemcpyHostToDevice, h->stream) == cudaSuccess;
+        // the staging of pageable sources is complete when the stream reaches this point
+        ok = ok && cudaStreamSynchronize(h->stream) == cudaSuccess;
     }
     ok = ok && cudaMemsetAsync(h->k_dev, 0, sizeof(uint32_t), h->stream) == cudaSuccess;
     ok = ok && cudaMemsetAsync(h->status, 0, sizeof(int), h->stream) == cudaSuccess;

@@ -55,11 +55,11 @@ struct smc2_handle {
     int* outer_anc = nullptr;
     uint32_t* k_dev = nullptr;
     int* status = nullptr;      // device status word of the handle's kernels
-    int* h_status = nullptr;    // pinned
+    int* h_status = nullptr;    // host copy of the status word
     float *xck = nullptr, *lwck = nullptr, *xseg = nullptr, *lwseg = nullptr, *mstep = nullptr, *lstep = nullptr;
     uint16_t* anc = nullptr;
     uint8_t* flag = nullptr;
-    double* h_stats = nullptr;  // pinned
+    double* h_stats = nullptr;  // host copy of the outer statistics
     uint32_t k = 0;             // iterations enqueued
     cudaGraphExec_t graph_exec = nullptr;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // around the filter passes of a step

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <chrono>
+#include <cstdint>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -197,6 +198,14 @@ extern "C" int smc2_server_create(size_t hbm_budget, int max_active, smc2_server
         delete s;
         return fail(SMC2_E_CUDA, "cudaGetDevice failed");
     }
+    // served jobs allocate from the device's stream-ordered pool; keep freed memory in the
+    // pool for the next admission instead of returning it to the driver
+    cudaMemPool_t pool = nullptr;
+    if (cudaDeviceGetDefaultMemPool(&pool, s->device) == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
     s->worker = std::thread(worker_loop, s);
     *out = s;
     return SMC2_OK;
