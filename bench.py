@@ -225,14 +225,17 @@ def run_gpu(a, rank, world, local):
     h.set_step_timing(True)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    stats = []
     fwd_t, adj_t = [], []
-    for _ in range(a.steps):
-        stats.append(h.step(want_means=False))
-        # the dominant kernels' device time inside this step (events on the handle's stream)
+    left = a.steps
+    while left > 0:
+        n = min(left, 512)
+        h.run(n, want_means=False)  # n iterations back to back, one host round trip
+        # the dominant kernels' mean device time over those iterations (events on the
+        # handle's stream around the forward and adjoint passes of every iteration)
         f_ms, b_ms = h.step_timing()
-        fwd_t.append(f_ms)
-        adj_t.append(b_ms)
+        fwd_t += [f_ms] * n
+        adj_t += [b_ms] * n
+        left -= n
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier()

@@ -141,11 +141,17 @@ int pf_loglik_grad_host(smc2_handle* h, const double* theta_host, int n, uint32_
  */
 int smc2_step(smc2_handle* h, smc2_stats* out);
 
-/* Filter-pass timing.  With timing on, smc2_step launches its kernels one by one (not as
- * the replayed step graph) and records CUDA events on the handle's stream around the
- * forward and adjoint passes; smc2_get_step_timing then returns their device time for
- * the last step: ms[0] forward, ms[1] adjoint (waits for those passes to finish).
- * SMC2_E_INVAL if the last smc2_step ran with timing off. */
+/* K SMC^2 iterations back to back (asynchronous on the handle's stream; no host
+ * round trip between them), then fills *out (may be NULL) with the statistics of the last
+ * one, synchronising once.  Equivalent to K calls of smc2_step.  Errors as smc2_step. */
+int smc2_run(smc2_handle* h, int K, smc2_stats* out);
+
+/* Filter-pass timing.  With timing on, iterations launch their kernels one by one (not as
+ * the replayed step graph) and record CUDA events on the handle's stream around the
+ * forward and adjoint passes; smc2_get_step_timing returns the mean device time of the
+ * passes over the iterations run since timing was switched on or last queried (up to the
+ * last 512): ms[0] forward, ms[1] adjoint (waits for them to finish).  SMC2_E_INVAL if no
+ * timed iteration ran since then. */
 int smc2_set_step_timing(smc2_handle* h, int on);
 int smc2_get_step_timing(smc2_handle* h, float* ms);
 

@@ -22,7 +22,7 @@ SYSTEMATIC, MULTINOMIAL = 0, 1
 
 # every symbol include/smc2.h declares
 EXPORTS = ("smc2_config_init", "smc2_create", "pf_loglik_grad", "pf_loglik_grad_rows",
-           "pf_loglik_grad_host", "smc2_step", "smc2_step_filters", "smc2_step_update", "smc2_set_step_timing", "smc2_get_step_timing", "smc2_get_samples", "smc2_get_state",
+           "pf_loglik_grad_host", "smc2_step", "smc2_step_filters", "smc2_step_update", "smc2_run", "smc2_set_step_timing", "smc2_get_step_timing", "smc2_get_samples", "smc2_get_state",
            "smc2_get_trace", "smc2_set_observations", "smc2_footprint", "smc2_destroy",
            "smc2_autotune", "smc2_get_launch", "smc2_set_launch", "smc2_get_status", "smc2_selftest_bounded_wait", "smc2_kernel_launches", "smc2_last_error", "smc2_server_create",
            "smc2_submit", "smc2_poll", "smc2_cancel", "smc2_server_destroy",
@@ -105,6 +105,7 @@ def load(path: str = LIB_PATH):
         "pf_loglik_grad_host": (ctypes.c_int, [vp, dp, ctypes.c_int, u32, dp, dp]),
         "smc2_step": (ctypes.c_int, [vp, ctypes.POINTER(Stats)]),
         "smc2_step_filters": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, dp, dp]),
+        "smc2_run": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(Stats)]),
         "smc2_set_step_timing": (ctypes.c_int, [vp, ctypes.c_int]),
         "smc2_get_step_timing": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_float)]),
         "smc2_step_update": (ctypes.c_int, [vp, dp, dp, ctypes.POINTER(Stats)]),
@@ -261,11 +262,25 @@ class Handle:
         return {"k": st.k, "resampled": bool(st.resampled), "ess": st.ess, "l_k": st.l_k,
                 "max_logw": st.max_logw, "mean": mean, "recycled_mean": rec}
 
+    def run(self, K, want_means=True):
+        """K iterations back to back; statistics of the last one."""
+        import numpy as np
+        st = Stats()
+        mean = np.zeros(self.D)
+        rec = np.zeros(self.D)
+        if want_means:
+            st.mean = mean.ctypes.data
+            st.recycled_mean = rec.ctypes.data
+        check(self.lib.smc2_run(self.h, int(K), ctypes.byref(st)), "smc2_run")
+        return {"k": st.k, "resampled": bool(st.resampled), "ess": st.ess, "l_k": st.l_k,
+                "max_logw": st.max_logw, "mean": mean, "recycled_mean": rec}
+
     def set_step_timing(self, on=True):
         check(self.lib.smc2_set_step_timing(self.h, 1 if on else 0), "smc2_set_step_timing")
 
     def step_timing(self):
-        """(forward ms, adjoint ms) of the filter passes of the last step (device events)."""
+        """Mean (forward ms, adjoint ms) of the filter passes of the iterations run since the
+        last query (device events)."""
         ms = (ctypes.c_float * 2)()
         check(self.lib.smc2_get_step_timing(self.h, ms), "smc2_get_step_timing")
         return float(ms[0]), float(ms[1])

@@ -9,6 +9,7 @@
 // eager iteration.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -249,7 +250,7 @@ static void free_handle_memory(smc2_handle* h) {
     delete[] h->h_stats;
     delete[] h->h_status;
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
-    for (cudaEvent_t e : h->ev)
+    for (cudaEvent_t e : h->tev)
         if (e) cudaEventDestroy(e);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
@@ -291,8 +292,6 @@ extern "C" int smc2_create(const smc2_config* cfg, smc2_handle** out) {
             return cleanup(SMC2_E_CUDA, "cudaStreamCreate failed");
         h->own_stream = true;
     }
-    for (cudaEvent_t& e : h->ev)
-        if (cudaEventCreate(&e) != cudaSuccess) return cleanup(SMC2_E_CUDA, "cudaEventCreate failed");
     const size_t N = cfg->N, T = cfg->T;
     struct Alloc { void** p; size_t bytes; };
     Alloc allocs[] = {
@@ -422,16 +421,17 @@ PFArgs smc2::make_pf_args(smc2_handle* h, const double* theta, int n, uint32_t i
 }
 
 int smc2::launch_filters(smc2_handle* h, const PFArgs& a, bool timed) {
-    // timed: bracket the passes with the handle's events (eager launches only)
-    if (timed) cudaEventRecord(h->ev[0], h->stream);
+    // timed: bracket the passes with the events of the step's timing slot (eager launches only)
+    cudaEvent_t* ev = timed ? &h->tev[3 * (h->tev_next % kTimingSlots)] : nullptr;
+    if (timed) cudaEventRecord(ev[0], h->stream);
     int rc = h->fwd(a, h->stream, a.n);
     const char* pass = "forward";
-    if (timed && !rc) cudaEventRecord(h->ev[1], h->stream);
+    if (timed && !rc) cudaEventRecord(ev[1], h->stream);
     if (!rc && a.want_grad) {
         rc = h->bwd(a, h->stream, a.n);
         pass = "adjoint";
     }
-    if (timed && !rc) cudaEventRecord(h->ev[2], h->stream);
+    if (timed && !rc) cudaEventRecord(ev[2], h->stream);
     if (rc)
         return fail(SMC2_E_CUDA, std::string(pass) + " filter launch failed: " +
                                      (rc > 0 ? cudaGetErrorString((cudaError_t)rc) : "block too large"));
@@ -555,23 +555,51 @@ int smc2::step_async(smc2_handle* h) {
         if (rc) return rc;
     }
     h->k += 1;
-    h->ev_recorded = h->timing;
+    if (h->timing) {
+        h->tev_next = (h->tev_next + 1) % kTimingSlots;
+        h->tev_pending = std::min(h->tev_pending + 1, kTimingSlots);
+    }
     return SMC2_OK;
 }
 
 extern "C" int smc2_set_step_timing(smc2_handle* h, int on) {
     if (!h) return fail(SMC2_E_INVAL, "handle is NULL");
+    if (on && h->tev.empty()) {
+        h->tev.assign(3 * kTimingSlots, nullptr);
+        for (cudaEvent_t& e : h->tev) CUDA_TRY(cudaEventCreate(&e));
+    }
     h->timing = on != 0;
+    h->tev_pending = 0;
     return SMC2_OK;
 }
 
 extern "C" int smc2_get_step_timing(smc2_handle* h, float* ms) {
     if (!h || !ms) return fail(SMC2_E_INVAL, "NULL argument");
-    if (!h->ev_recorded) return fail(SMC2_E_INVAL, "the last smc2_step did not record its filter timing");
-    CUDA_TRY(cudaEventSynchronize(h->ev[2]));
-    CUDA_TRY(cudaEventElapsedTime(&ms[0], h->ev[0], h->ev[1]));
-    CUDA_TRY(cudaEventElapsedTime(&ms[1], h->ev[1], h->ev[2]));
+    if (h->tev_pending == 0) return fail(SMC2_E_INVAL, "no timed smc2_step since the last query");
+    double f = 0.0, b = 0.0;
+    for (int i = 1; i <= h->tev_pending; ++i) {
+        const int slot = ((h->tev_next - i) % kTimingSlots + kTimingSlots) % kTimingSlots;
+        cudaEvent_t* ev = &h->tev[3 * slot];
+        float a = 0.f, c = 0.f;
+        CUDA_TRY(cudaEventSynchronize(ev[2]));
+        CUDA_TRY(cudaEventElapsedTime(&a, ev[0], ev[1]));
+        CUDA_TRY(cudaEventElapsedTime(&c, ev[1], ev[2]));
+        f += a;
+        b += c;
+    }
+    ms[0] = (float)(f / h->tev_pending);
+    ms[1] = (float)(b / h->tev_pending);
+    h->tev_pending = 0;
     return SMC2_OK;
+}
+
+extern "C" int smc2_run(smc2_handle* h, int K, smc2_stats* out) {
+    if (!h || K < 1) return fail(SMC2_E_INVAL, "handle is NULL or K < 1");
+    for (int k = 0; k < K; ++k) {
+        int rc = step_async(h);
+        if (rc) return rc;
+    }
+    return read_stats(h, out);
 }
 
 int smc2::read_status(smc2_handle* h, int* status) {

@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include <cstddef>
 #include <cstdint>
 #include <string>
@@ -38,6 +40,8 @@ void plan_sizes(const smc2_config* c, int D, int kc, Sizes* s);
 
 }  // namespace smc2
 
+constexpr int kTimingSlots = 512;
+
 struct smc2_handle {
     smc2_config cfg{};        // copy; pointer members cleared
     int D = 0, kc = 1;
@@ -62,9 +66,13 @@ struct smc2_handle {
     double* h_stats = nullptr;  // host copy of the outer statistics
     uint32_t k = 0;             // iterations enqueued
     cudaGraphExec_t graph_exec = nullptr;
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // around the filter passes of a step
-    bool timing = false;       // steps run eagerly with the events recorded
-    bool ev_recorded = false;  // the last step recorded them
+    // filter-pass timing: with timing on, steps run eagerly and record three events each
+    // (before the forward pass, between the passes, after the adjoint) into a ring of
+    // kTimingSlots slots; smc2_get_step_timing averages the steps recorded since its last call
+    bool timing = false;
+    std::vector<cudaEvent_t> tev;  // 3 * kTimingSlots, created when timing is first switched on
+    int tev_next = 0;              // slot of the next timed step
+    int tev_pending = 0;           // timed steps not yet reported (<= kTimingSlots)
     bool no_graph = false;
     bool split_pending = false;  // smc2_step_filters issued, smc2_step_update not yet
     int launches_per_step = 0;

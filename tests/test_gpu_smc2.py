@@ -148,3 +148,24 @@ def test_step_timing_mode_gives_the_same_samples():
             out.append(h.samples())
     np.testing.assert_array_equal(out[0][0], out[1][0])
     np.testing.assert_array_equal(out[0][1], out[1][1])
+
+
+def test_run_equals_repeated_steps():
+    """smc2_run(K) enqueues K iterations back to back: same samples and statistics as K
+    calls of smc2_step."""
+    from paper_2407_17296_gb300 import binding
+    w = W.lg4(T=30, N=16, M=256, K=5)
+    outs = []
+    for use_run in (False, True):
+        with binding.Handle(binding.config_for(w)) as h:
+            if use_run:
+                st = h.run(5)
+            else:
+                for _ in range(5):
+                    st = h.step()
+            outs.append((st, h.samples()))
+    (s0, (th0, lw0)), (s1, (th1, lw1)) = outs
+    assert s0["k"] == s1["k"] == 5 and s0["ess"] == s1["ess"]
+    np.testing.assert_array_equal(s0["recycled_mean"], s1["recycled_mean"])
+    np.testing.assert_array_equal(th0, th1)
+    np.testing.assert_array_equal(lw0, lw1)
