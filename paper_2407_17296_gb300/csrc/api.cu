@@ -96,7 +96,7 @@ int smc2::family_dims(const smc2_config* c, int* D) {
 }
 
 pf_kernel_fn smc2::lookup_forward(const smc2_config* c, int P, int regs) {
-    if (!variant_fits(c, P, regs)) return nullptr;
+    if (!variant_fits(c, P, regs, true)) return nullptr;
     if (c->model_family == SMC2_SV) return lookup_sv_fwd(P, regs);
     if (c->model_family == SMC2_LG_OPT) return lookup_opt_fwd(P, regs);
     if (c->d_x == 1) return lookup_lg1_fwd(P, regs);
@@ -106,7 +106,7 @@ pf_kernel_fn smc2::lookup_forward(const smc2_config* c, int P, int regs) {
 }
 
 pf_kernel_fn smc2::lookup_backward(const smc2_config* c, int P, int regs) {
-    if (!variant_fits(c, P, regs)) return nullptr;
+    if (!variant_fits(c, P, regs, false)) return nullptr;
     if (c->model_family == SMC2_SV) return lookup_sv_bwd(P, regs);
     if (c->model_family == SMC2_LG_OPT) return lookup_opt_bwd(P, regs);
     if (c->d_x == 1) return lookup_lg1_bwd(P, regs);
@@ -115,18 +115,24 @@ pf_kernel_fn smc2::lookup_backward(const smc2_config* c, int P, int regs) {
     return nullptr;
 }
 
-int smc2::model_lanes(const smc2_config* c) { return (c->model_family == SMC2_LG_DIAG && c->d_x == 16) ? 4 : 1; }
+// The 16-dimensional model spreads a particle over 2 lanes in the forward pass (8 state
+// dimensions each: less replicated per-particle work) and over 4 in the adjoint (a smaller
+// per-lane cotangent state); the stored trajectory does not depend on the split.
+int smc2::model_lanes(const smc2_config* c, bool forward) {
+    if (c->model_family == SMC2_LG_DIAG && c->d_x == 16) return forward ? 2 : 4;
+    return 1;
+}
 
-bool smc2::variant_fits(const smc2_config* c, int P, int regs) {
-    const int threads = pf_threads(c->M, P, model_lanes(c));
+bool smc2::variant_fits(const smc2_config* c, int P, int regs, bool forward) {
+    const int threads = pf_threads(c->M, P, model_lanes(c, forward));
     return threads <= 1024 && threads * regs <= 65536;
 }
 
 // Register cap used with an explicitly requested particles-per-thread value: the largest
 // of 128, 80, 64 that the block size allows.
-static int default_regs(const smc2_config* c, int P) {
+static int default_regs(const smc2_config* c, int P, bool forward) {
     for (int r : {128, 80, 64})
-        if (variant_fits(c, P, r)) return r;
+        if (variant_fits(c, P, r, forward)) return r;
     return 64;
 }
 
@@ -135,18 +141,23 @@ void smc2::choose_launch(const smc2_config* c, LaunchChoice* lc) {
     const bool tuned = tuned_launch(c, &t);
     if (c->particles_per_thread) {
         lc->pf = lc->pb = c->particles_per_thread;
-        lc->rf = lc->rb = default_regs(c, c->particles_per_thread);
+        lc->rf = default_regs(c, c->particles_per_thread, true);
+        lc->rb = default_regs(c, c->particles_per_thread, false);
     } else if (tuned) {
         *lc = t;
     } else {
         // enough particles per thread to keep every Philox call whole and the block <= 512
         // threads (1024 for the lane-split model), 64 registers when that still fits
-        const int G = model_lanes(c);
-        const int cap = (G > 1) ? 1024 : 512;
-        int P = (c->d_x >= 4) ? 2 : 4;
-        while (pf_threads(c->M, P, G) > cap && P < 8) P *= 2;
-        lc->pf = lc->pb = P;
-        lc->rf = lc->rb = variant_fits(c, P, 64) && P <= 4 ? 64 : default_regs(c, P);
+        for (int pass = 0; pass < 2; ++pass) {
+            const bool fwd = pass == 0;
+            const int G = model_lanes(c, fwd);
+            const int cap = (G > 1) ? 1024 : 512;
+            int P = (c->d_x >= 4) ? 2 : 4;
+            while (pf_threads(c->M, P, G) > cap && P < 8) P *= 2;
+            const int regs = variant_fits(c, P, 64, fwd) && P <= 4 ? 64 : default_regs(c, P, fwd);
+            (fwd ? lc->pf : lc->pb) = P;
+            (fwd ? lc->rf : lc->rb) = regs;
+        }
     }
     lc->kc = (c->ckpt_every > 0) ? c->ckpt_every : (tuned ? t.kc : choose_kc(c));
 }
@@ -187,15 +198,16 @@ int smc2::validate(const smc2_config* c, int* D) {
     if (c->ckpt_every < 0) return fail(SMC2_E_INVAL, "ckpt_every must be >= 0");
     const int P = c->particles_per_thread;
     if (P != 0 && P != 1 && P != 2 && P != 4 && P != 8) return fail(SMC2_E_INVAL, "particles_per_thread must be 0, 1, 2, 4 or 8");
-    if (P != 0 && !variant_fits(c, P, 64)) return fail(SMC2_E_INVAL, "M too large for particles_per_thread");
+    if (P != 0 && (!variant_fits(c, P, 64, true) || !variant_fits(c, P, 64, false)))
+        return fail(SMC2_E_INVAL, "M too large for particles_per_thread");
     {
         LaunchChoice lc;
         choose_launch(c, &lc);
-        if (!variant_fits(c, lc.pf, lc.rf) || !variant_fits(c, lc.pb, lc.rb))
+        if (!variant_fits(c, lc.pf, lc.rf, true) || !variant_fits(c, lc.pb, lc.rb, false))
             return fail(SMC2_E_INVAL, "M too large for this model (no launch configuration fits)");
-        const int G = model_lanes(c);
-        if (SmemLayout(c->M, c->d_x, *D, true, G).total > kSmemLimit ||
-            SmemLayout(c->M, c->d_x, *D, false, G, ring_slots(c->M, c->d_x, *D, G)).total > kSmemLimit)
+        const int Gf = model_lanes(c, true), Gb = model_lanes(c, false);
+        if (SmemLayout(c->M, c->d_x, *D, true, Gf).total > kSmemLimit ||
+            SmemLayout(c->M, c->d_x, *D, false, Gb, ring_slots(c->M, c->d_x, *D, Gb)).total > kSmemLimit)
             return fail(SMC2_E_INVAL, "M too large for this model (shared memory of a filter block)");
     }
     if (c->prior_kind != SMC2_PRIOR_GAUSSIAN && c->prior_kind != SMC2_PRIOR_UNIFORM)

@@ -27,8 +27,8 @@ int fail(int code, const std::string& msg);
 void count_launches(int n);
 int family_dims(const smc2_config* c, int* D);
 int validate(const smc2_config* c, int* D);
-int model_lanes(const smc2_config* c);                // lanes per particle (G)
-bool variant_fits(const smc2_config* c, int P, int regs);  // block size and registers allow it
+int model_lanes(const smc2_config* c, bool forward);  // lanes per particle (G) of a pass
+bool variant_fits(const smc2_config* c, int P, int regs, bool forward);  // block size and registers allow it
 pf_kernel_fn lookup_forward(const smc2_config* c, int P, int regs);
 pf_kernel_fn lookup_backward(const smc2_config* c, int P, int regs);
 int choose_kc(const smc2_config* c);
