@@ -69,25 +69,30 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // floor(w * 2^40) for w in [0, 1], from the float's bits with integer operations only
-// (conversions between floats and 64-bit integers run on the narrow FP64 pipe).
+// (conversions between floats and 64-bit integers run on the narrow FP64 pipe) and no
+// branches: w = m * 2^(e - 150) with m the 24-bit significand, so w * 2^40 is
+// (m * 2^17) >> (127 - e); zero and denormal weights shift out all 41 bits.
 __device__ __forceinline__ unsigned long long fixed40(float w) {
     const uint32_t b = __float_as_uint(w);
-    const int e = (int)((b >> 23) & 0xffu);
-    if (e == 0) return 0ull;                          // zero (or a denormal weight)
-    const uint32_t m = (b & 0x7fffffu) | 0x800000u;   // w = m * 2^(e - 150)
-    const int sh = e - 110;                           // w * 2^40 = m * 2^sh, sh <= 17
-    if (sh >= 0) return (unsigned long long)m << sh;
-    if (sh <= -24) return 0ull;
-    return (unsigned long long)(m >> (-sh));
+    const uint32_t e = min((b >> 23) & 0xffu, 127u);
+    const unsigned long long m = (unsigned long long)((b & 0x7fffffu) | 0x800000u) << 17;
+    return m >> min(127u - e, 63u);
 }
 
 // S as a float, rounded toward zero (monotone in S), with integer operations only.
 __device__ __forceinline__ float u64_to_float_rz(unsigned long long S) {
-    if (S == 0ull) return 0.f;
-    const int lz = __clzll((long long)S);
-    const uint32_t m = (uint32_t)((S << lz) >> 40);  // leading 24 bits, top bit set
-    const uint32_t E = (uint32_t)(63 - lz);          // S ~ m * 2^(E - 23)
-    return __uint_as_float(((E + 127u) << 23) | (m & 0x7fffffu));
+    const int lz = __clzll((long long)S);                   // 64 for S = 0
+    const uint32_t m = (uint32_t)((S << (lz & 63)) >> 40);  // leading 24 bits, top bit set
+    const uint32_t E = (uint32_t)(63 - lz);                 // S ~ m * 2^(E - 23)
+    const float f = __uint_as_float(((E + 127u) << 23) | (m & 0x7fffffu));
+    return S ? f : 0.f;
+}
+
+// min(max(floor(c) + 1, 0), M) for |c| < 2^22: the addition of 1.5 * 2^23 rounded down
+// leaves floor(c) in the low bits of the sum.
+__device__ __forceinline__ int count_below(float c, int M) {
+    const int n = __float_as_int(__fadd_rd(c, 12582912.f)) - 0x4B400000 + 1;
+    return min(max(n, 0), M);
 }
 
 // (max, sum exp(v - max), sum exp(2 (v - max))) over all particles of the CTA.
@@ -149,20 +154,24 @@ __device__ __forceinline__ void block_lse3(const float (&lwin)[P], bool lead, fl
 
 // Exact inclusive prefix sums S_j of the fixed-point weights round(w_j * 2^40) over the
 // CTA's particles.  Returns the thread's base (sum before its first particle), its local
-// inclusive sums s[p], and the grand total.  One __syncthreads.
+// inclusive sums s[p] (and the same sums in FP32, in units of 2^40: sf[p]), and the grand
+// total.  One __syncthreads.
 template <int P, int G>
 __device__ __forceinline__ void block_fixed_scan(const float (&lw)[P], bool lead, int j0, int M,
                                                  unsigned long long* scanw,
-                                                 unsigned long long (&s)[P],
+                                                 unsigned long long (&s)[P], float (&sf)[P],
                                                  unsigned long long& base,
                                                  unsigned long long& total) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     unsigned long long run = 0ull;
+    float runf = 0.f;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         const float w = (lead && j0 + p < M) ? __expf(lw[p]) : 0.f;  // lw <= 0 after recentring
         run += fixed40(w);
+        runf += w;
         s[p] = run;
+        sf[p] = runf;
     }
     unsigned long long inc = run;
 #pragma unroll
@@ -184,40 +193,68 @@ __device__ __forceinline__ void block_fixed_scan(const float (&lw)[P], bool lead
     if constexpr (G > 1) base = __shfl_sync(kFull, base, lane & ~(G - 1));  // the group leader's base
 }
 
+// P particle-indexed 16-bit values at row[j0 ..), j0 a multiple of P: one vector store when
+// the P entries are all in range.
+template <int P>
+__device__ __forceinline__ void store_u16(uint16_t* row, int j0, int M, const int (&v)[P]) {
+    if constexpr (P == 2 || P == 4 || P == 8) {
+        if (j0 + P <= M) {
+            uint32_t w[P / 2];
+#pragma unroll
+            for (int q = 0; q < P / 2; ++q) w[q] = (uint32_t)(v[2 * q] & 0xffff) | ((uint32_t)v[2 * q + 1] << 16);
+            if constexpr (P == 2) *reinterpret_cast<uint32_t*>(row + j0) = w[0];
+            if constexpr (P == 4) *reinterpret_cast<uint2*>(row + j0) = make_uint2(w[0], w[1]);
+            if constexpr (P == 8) *reinterpret_cast<uint4*>(row + j0) = make_uint4(w[0], w[1], w[2], w[3]);
+            return;
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+        if (j0 + p < M) row[j0 + p] = (uint16_t)v[p];
+}
+
 // Systematic ancestors (App. B with tau_i = (i + nu)/M): a_i = min{j : c_j >= tau_i}.
 // Particle j is the ancestor of i in [n(c_{j-1}), n(c_j)) with n(c) = #{i : tau_i <= c}
 // = clamp(floor(c M - nu) + 1, 0, M); range starts are marked and a prefix-max fills
-// in every i.  Three __syncthreads.  anc[p] is the ancestor of particle i = j0 + p.
+// in every i.  A thread converts the exact fixed-point sums at the two ends of its range;
+// the bounds between them come from its FP32 local sums, clamped to stay monotone, so
+// neighbouring threads share their common bound exactly.  The parent whose range holds a
+// warp's first child is recorded for that warp (carry), which seeds the warp's prefix-max.
+// Two __syncthreads.  anc[p] is the ancestor of particle i = j0 + p.
 template <int P, int G>
 __device__ __forceinline__ void systematic_ancestors(const float (&lw)[P], bool lead, int j0, int M, float nu,
                                                      uint16_t* marks, unsigned long long* scanw,
-                                                     int* scanwi, int* maxoff, int (&anc)[P], int& max_offspring) {
+                                                     int* carry, int* maxoff, int (&anc)[P], int& max_offspring) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int p = 0; p < P; ++p)
-        if (lead && j0 + p < M) marks[j0 + p] = 0;
+    constexpr int C = (32 / G) * P;  // children (particles) per warp
+    if (lead) {
+        const int z[P] = {};
+        store_u16<P>(marks, j0, M, z);
+    }
     if (threadIdx.x == 0) *maxoff = 0;
     unsigned long long s[P], base, tot;
-    block_fixed_scan<P, G>(lw, lead, j0, M, scanw, s, base, tot);
+    float sf[P];
+    block_fixed_scan<P, G>(lw, lead, j0, M, scanw, s, sf, base, tot);
     const float scale = (float)M / u64_to_float_rz(tot);
-    auto count_le = [&](unsigned long long S) {
-        const float cm = u64_to_float_rz(S) * scale - nu;
-        const int n = (int)floorf(cm) + 1;
-        return min(max(n, 0), M);
-    };
-    int lo = count_le(base), off = 0;
+    const float c0 = u64_to_float_rz(base) * scale - nu;
+    const float sc40 = scale * 0x1p40f;
+    int lo = count_below(c0, M), off = 0;
+    const int hiP = count_below(u64_to_float_rz(base + s[P - 1]) * scale - nu, M);
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         const int j = j0 + p;
-        const int hi = (j == M - 1) ? M : count_le(base + s[p]);
-        if (lead && j < M && hi > lo) marks[lo] = (uint16_t)(j + 1);
+        const int hi = (j == M - 1) ? M : (p == P - 1) ? hiP : min(count_below(fmaf(sf[p], sc40, c0), M), hiP);
+        if (lead && j < M && hi > lo) {
+            marks[lo] = (uint16_t)(j + 1);
+            for (int w = max((lo + C - 1) / C, 1); w * C < hi; ++w) carry[w] = j + 1;
+        }
         off = max(off, hi - lo);
         lo = hi;
     }
     off = __reduce_max_sync(kFull, off);
     if (lane == 0) atomicMax(maxoff, off);
     __syncthreads();
-    max_offspring = *maxoff;  // read before the barrier below; rewritten only at the next call
+    max_offspring = *maxoff;  // rewritten only by the next call, after the next step's barriers
     int r = 0, rr[P];
 #pragma unroll
     for (int p = 0; p < P; ++p) {
@@ -231,20 +268,12 @@ __device__ __forceinline__ void systematic_ancestors(const float (&lw)[P], bool 
         const int v = __shfl_up_sync(kFull, inc, o);
         if (lane >= o) inc = max(inc, v);
     }
-    // exclusive prefix of the group: the inclusive value of the lane before the group leader
+    // exclusive prefix of the group: the inclusive value of the lane before the group leader,
+    // and the warp's carry
     const int lead_lane = lane & ~(G - 1);
     int excl = __shfl_sync(kFull, inc, (lead_lane + 31) & 31);
     if (lead_lane == 0) excl = 0;
-    if (lane == 31) scanwi[wid] = inc;
-    __syncthreads();
-    int v = (lane < (int)(blockDim.x >> 5)) ? scanwi[lane] : 0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int u = __shfl_up_sync(kFull, v, o);
-        if (lane >= o) v = max(v, u);
-    }
-    const int pre = (wid > 0) ? __shfl_sync(kFull, v, (wid + 31) & 31) : 0;
-    const int e = max(pre, excl);
+    const int e = max(excl, wid > 0 ? carry[wid] : 0);
 #pragma unroll
     for (int p = 0; p < P; ++p) anc[p] = max(e, rr[p]) - 1;
 }
@@ -256,7 +285,8 @@ __device__ __forceinline__ void multinomial_ancestors(const float (&lw)[P], bool
                                                       const PhiloxKey& key, uint32_t t, float* cs,
                                                       unsigned long long* scanw, int (&anc)[P]) {
     unsigned long long s[P], base, tot;
-    block_fixed_scan<P, G>(lw, lead, j0, M, scanw, s, base, tot);
+    float sf[P];
+    block_fixed_scan<P, G>(lw, lead, j0, M, scanw, s, sf, base, tot);
     const float inv = 1.0f / u64_to_float_rz(tot);
 #pragma unroll
     for (int p = 0; p < P; ++p) {
@@ -627,7 +657,7 @@ __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, cons
     uint16_t* marks = reinterpret_cast<uint16_t*>(smem + L.marks);
     float4* red = reinterpret_cast<float4*>(smem + L.red);
     unsigned long long* scanw = reinterpret_cast<unsigned long long*>(smem + L.scanw);
-    int* scanwi = reinterpret_cast<int*>(smem + L.scanwi);
+    int* carry = reinterpret_cast<int*>(smem + L.scanwi);  // per-warp prefix-max seeds
     int* maxoff = reinterpret_cast<int*>(smem + L.misc);
 
     if (tid == 0) Mdl::make_params(a.theta + (size_t)f * a.D, a.H, sprm);
@@ -660,24 +690,23 @@ __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, cons
             a.lstep[(size_t)f * (T + 1)] = Lprev;
         }
     }
+    float nu_lane = 0.f;  // systematic offset of step 32 k + 1 + lane, drawn for 32 steps at once
     for (int t = 1; t <= T; ++t) {
         int max_offspring = 0;
+        if (a.scheme == 0 && ((t - 1) & 31) == 0) {
+            const uint4 w = philox4x32_10(make_uint4((uint32_t)(t + (tid & 31)), 0u, kStreamResample, 0u), key);
+            nu_lane = u01_open(w.x);
+        }
         if (resample) {
             stage_x<P, DX, DL>(xstage, j0, gl, M, x);
             int anc[P];
             if (a.scheme == 0) {
-                const uint4 w = philox4x32_10(make_uint4((uint32_t)t, 0u, kStreamResample, 0u), key);
-                systematic_ancestors<P, G>(lw, lead, j0, M, u01_open(w.x), marks, scanw, scanwi, maxoff, anc,
-                                           max_offspring);
+                const float nu = __shfl_sync(kFull, nu_lane, (t - 1) & 31);
+                systematic_ancestors<P, G>(lw, lead, j0, M, nu, marks, scanw, carry, maxoff, anc, max_offspring);
             } else {
                 multinomial_ancestors<P, G>(lw, lead, j0, M, key, (uint32_t)t, cs, scanw, anc);
             }
-            if (a.anc && lead) {
-                uint16_t* row = tr.anc_row(t - 1);
-#pragma unroll
-                for (int p = 0; p < P; ++p)
-                    if (j0 + p < M) row[j0 + p] = (uint16_t)anc[p];
-            }
+            if (a.anc && lead) store_u16<P>(tr.anc_row(t - 1), j0, M, anc);
 #pragma unroll
             for (int p = 0; p < P; ++p) {
                 if (j0 + p < M) read_staged<DX, DL>(xstage, anc[p], gl, x[p]);
