@@ -140,14 +140,20 @@ def update(state, k, theta_new, ll_new, g_new, seed, gamma, proposal, m0, s0, hi
         # Eq. l_weights; a sample whose weight or posterior estimate (old or new) is zero
         # keeps weight zero (this also covers proposals outside a uniform prior's support)
         ok = (state.logw > -np.inf) & (lp_new > -np.inf) & (state.logpi > -np.inf)
-        with np.errstate(invalid="ignore"):
+        with np.errstate(invalid="ignore", over="ignore"):
             logw = np.where(ok, state.logw + lp_new - state.logpi + log_L - log_q, -np.inf)
+    # The Langevin kernels (the SMC1 proposal of Sec. III-D, the L-kernel of Sec. III-E) need
+    # grad log pi at the proposal.  Where it is not finite the sample can neither be
+    # weighted nor moved: it carries weight zero, as does any non-finite weight.
+    grad_ok = np.all(np.isfinite(gp_new), axis=1) if proposal == "langevin" else np.ones(N, bool)
+    logw = np.where(grad_ok & np.isfinite(logw), logw, -np.inf)
     theta, logpi, gradpi, loglik = theta_new, lp_new, gp_new, ll_new
 
-    # normalise, estimate, recycling statistic, ESS
+    # normalise, estimate (over the samples of positive weight), recycling statistic, ESS
     L = _lse(logw)
     wn = np.exp(logw - L)
-    mean = wn @ theta
+    pos = wn > 0.0
+    mean = wn[pos] @ theta[pos]
     ess = 1.0 / np.sum(wn * wn)
     l_k = np.exp(2.0 * _lse(logw) - _lse(2.0 * logw))        # (sum w)^2 / sum w^2
     rec = {"k": k, "ess": float(ess), "l_k": float(l_k), "mean": mean.copy(),

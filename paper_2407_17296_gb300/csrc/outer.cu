@@ -144,6 +144,12 @@ __global__ void outer_weight_kernel(OuterArgs a) {
     const double* thn = a.theta_new + (size_t)i * D;
     const double lln = a.ll_new[i];
     const double lpn = (lln > -INFINITY) ? log_prior_at(a, thn, pinv) + lln : -INFINITY;
+    // the Langevin kernels need grad log pi at the proposal: where the filter's gradient
+    // is not finite (e.g. FP32 overflow under explosive dynamics) the sample cannot be
+    // weighted or moved and carries weight zero, as does any non-finite weight
+    bool grad_ok = true;
+    if (a.langevin)
+        for (int d = 0; d < D; ++d) grad_ok = grad_ok && isfinite(a.grad_new[(size_t)i * D + d]);
     double lw;
     if (k == 1u) {
         lw = lln;  // pi / q_1 with q_1 the prior
@@ -171,6 +177,7 @@ __global__ void outer_weight_kernel(OuterArgs a) {
             lw = -INFINITY;
         }
     }
+    if (!grad_ok || !isfinite(lw)) lw = -INFINITY;
     a.logw[i] = lw;
     a.logpi[i] = lpn;
     a.loglik[i] = lln;
@@ -210,7 +217,8 @@ __global__ void __launch_bounds__(kOuterThreads) outer_stats_kernel(OuterArgs a)
         const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
         for (int d = wid; d < D; d += nw) {
             double acc = 0.0;
-            for (int i = lane; i < N; i += 32) acc += csum[i] * a.theta[(size_t)i * D + d];
+            for (int i = lane; i < N; i += 32)  // samples of weight zero do not enter
+                if (csum[i] > 0.0) acc += csum[i] * a.theta[(size_t)i * D + d];
             acc = warp_sum_d(acc);
             if (lane == 0) {
                 const double md = (s1 > 0.0) ? acc / s1 : 0.0;

@@ -182,8 +182,7 @@ __device__ __forceinline__ void block_fixed_scan(const float (&lw)[P], bool lead
     if (lane == 31) scanw[wid] = inc;
     __syncthreads();
     unsigned long long v = (lane < nw) ? scanw[lane] : 0ull;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
+    for (int o = 1; o < nw; o <<= 1) {  // nw is uniform: log2(warps) steps
         const unsigned long long u = __shfl_up_sync(kFull, v, o);
         if (lane >= o) v += u;
     }
@@ -213,6 +212,37 @@ __device__ __forceinline__ void store_u16(uint16_t* row, int j0, int M, const in
         if (j0 + p < M) row[j0 + p] = (uint16_t)v[p];
 }
 
+// The loading counterpart of store_u16 (entries at or beyond M read as zero).
+template <int P>
+__device__ __forceinline__ void load_u16(const uint16_t* row, int j0, int M, int (&v)[P]) {
+    if constexpr (P == 2 || P == 4 || P == 8) {
+        if (j0 + P <= M) {
+            uint32_t w[P / 2];
+            if constexpr (P == 2) w[0] = *reinterpret_cast<const uint32_t*>(row + j0);
+            if constexpr (P == 4) {
+                const uint2 u = *reinterpret_cast<const uint2*>(row + j0);
+                w[0] = u.x;
+                w[1] = u.y;
+            }
+            if constexpr (P == 8) {
+                const uint4 u = *reinterpret_cast<const uint4*>(row + j0);
+                w[0] = u.x;
+                w[1] = u.y;
+                w[2] = u.z;
+                w[3] = u.w;
+            }
+#pragma unroll
+            for (int q = 0; q < P / 2; ++q) {
+                v[2 * q] = (int)(w[q] & 0xffffu);
+                v[2 * q + 1] = (int)(w[q] >> 16);
+            }
+            return;
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p) v[p] = (j0 + p < M) ? (int)row[j0 + p] : 0;
+}
+
 // Systematic ancestors (App. B with tau_i = (i + nu)/M): a_i = min{j : c_j >= tau_i}.
 // Particle j is the ancestor of i in [n(c_{j-1}), n(c_j)) with n(c) = #{i : tau_i <= c}
 // = clamp(floor(c M - nu) + 1, 0, M); range starts are marked and a prefix-max fills
@@ -235,7 +265,7 @@ __device__ __forceinline__ void systematic_ancestors(const float (&lw)[P], bool 
     unsigned long long s[P], base, tot;
     float sf[P];
     block_fixed_scan<P, G>(lw, lead, j0, M, scanw, s, sf, base, tot);
-    const float scale = (float)M / u64_to_float_rz(tot);
+    const float scale = __fdividef((float)M, u64_to_float_rz(tot));  // the same value in every thread
     const float c0 = u64_to_float_rz(base) * scale - nu;
     const float sc40 = scale * 0x1p40f;
     int lo = count_below(c0, M), off = 0;
@@ -256,10 +286,10 @@ __device__ __forceinline__ void systematic_ancestors(const float (&lw)[P], bool 
     __syncthreads();
     max_offspring = *maxoff;  // rewritten only by the next call, after the next step's barriers
     int r = 0, rr[P];
+    load_u16<P>(marks, j0, M, rr);
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-        const int i = j0 + p;
-        r = max(r, (i < M) ? (int)marks[i] : 0);
+        r = max(r, rr[p]);
         rr[p] = r;
     }
     int inc = r;
@@ -418,6 +448,10 @@ __device__ __forceinline__ float group_sum(float v) {
 // data-dependent loop costs more in the steps that do not resample than it saves).
 template <int G, int DX>
 constexpr bool kGatherWalk = (G == 1 && DX == 4);
+
+// slices the adjoint's ring producer moves into L2 ahead of the ring (beyond its R slots),
+// so that the copies into shared memory do not wait on memory latency
+constexpr int kL2Ahead = 4;
 
 // Adjoint of the gather x'_i = x_{a_i} for sorted ancestors (systematic resampling):
 // xbar_new[j] = sum of xbar'[i] over the offspring i of j, which form the run of entries
@@ -889,6 +923,7 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
             if (tid == 0) {
                 fence_proxy_async();
                 for (int k = 0; k < R && k < Ls; ++k) ring.produce(g + k, Xp(t1 - k), a.status);
+                for (int k = R; k < R + kL2Ahead && k < Ls; ++k) ring.prefetch(Xp(t1 - k));
             }
         }
         // tape row and log w_{tt-1} of step tt (which resampled) into buffer b, by
@@ -990,7 +1025,10 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
             if (fl_next) prefetch(t - 1, nres & 1u);
             if constexpr (R > 0) {
                 ring.release(g + k);
-                if (tid == 0 && k + R < Ls) ring.produce(g + k + R, Xp(t1 - k - R), a.status);
+                if (tid == 0 && k + R < Ls) {
+                    ring.produce(g + k + R, Xp(t1 - k - R), a.status);
+                    if (k + R + kL2Ahead < Ls) ring.prefetch(Xp(t1 - k - R - kL2Ahead));
+                }
             }
         }
         if (s == 0) {

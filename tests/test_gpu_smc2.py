@@ -169,3 +169,19 @@ def test_run_equals_repeated_steps():
     np.testing.assert_array_equal(s0["recycled_mean"], s1["recycled_mean"])
     np.testing.assert_array_equal(th0, th1)
     np.testing.assert_array_equal(lw0, lw1)
+
+
+def test_sampler_survives_filters_with_overflowing_gradients():
+    """The full linear-Gaussian job from its N(0, I) prior: some proposals have explosive
+    dynamics whose FP32 adjoint overflows while the log-likelihood stays finite.  Such a
+    sample gets weight zero, so the population's ESS stays positive and its means finite
+    (a NaN weight would otherwise zero every weight for good)."""
+    from paper_2407_17296_gb300 import binding
+    w = W.lg4()
+    cfg = binding.config_for(w)
+    binding.set_launch(cfg, [4, 64, 2, 64, 1])
+    with binding.Handle(cfg) as h:
+        for _ in range(40):
+            st = h.step()
+            assert st["ess"] >= 1.0, st
+            assert np.all(np.isfinite(st["mean"])), st

@@ -145,3 +145,38 @@ def test_sampler_with_uniform_prior_finds_quadrature_posterior_mean():
     # every draw of iteration 1 lies inside the box
     th1 = recs[0]["theta"]
     assert np.all((th1 >= w.prior_mean) & (th1 <= w.prior_std))
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_nonfinite_gradient_or_weight_gets_zero_weight(k):
+    """A proposal whose filter gradient overflowed (finite log p-hat, non-finite gradient)
+    cannot be moved by the Langevin kernel or weighted by its L-kernel: it gets weight zero,
+    and neither it nor a NaN state of a zero-weight sample reaches the estimate."""
+    rng = np.random.default_rng(11)
+    N, D = 8, 3
+    st = smc2.State(N, D)
+    st.theta = rng.standard_normal((N, D))
+    st.gradpi = rng.standard_normal((N, D))
+    st.logpi = rng.standard_normal(N)
+    st.logw = np.zeros(N)
+    th_new = st.theta + 0.1 * rng.standard_normal((N, D))
+    th_new[5] = np.nan  # a zero-weight sample's state may be anything
+    ll_new = -np.abs(rng.standard_normal(N))
+    ll_new[5] = -np.inf
+    g_new = rng.standard_normal((N, D))
+    g_new[2, 1] = np.nan
+    g_new[6, 0] = np.inf
+    m0, s0 = np.zeros(D), np.ones(D)
+    rec = smc2.update(st, k, th_new, ll_new, g_new, 7, 0.2, "langevin", m0, s0)
+    lw = rec["logw"]
+    assert lw[2] == -np.inf and lw[6] == -np.inf and lw[5] == -np.inf
+    live = [0, 1, 3, 4, 7]
+    assert np.all(np.isfinite(lw[live]))
+    assert np.all(np.isfinite(rec["mean"])) and rec["ess"] > 1.0
+    w = np.exp(lw[live] - lw[live].max())
+    np.testing.assert_allclose(rec["mean"], w @ th_new[live] / w.sum(), rtol=1e-12)
+    # the random walk ignores the gradient
+    st2 = smc2.State(N, D)
+    st2.theta, st2.gradpi, st2.logpi, st2.logw = st.theta, st.gradpi, st.logpi, np.zeros(N)
+    rec2 = smc2.update(st2, k, th_new, ll_new, g_new, 7, 0.2, "rw", m0, s0)
+    assert np.isfinite(rec2["logw"][2]) and np.isfinite(rec2["logw"][6])
