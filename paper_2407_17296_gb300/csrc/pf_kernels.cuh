@@ -449,10 +449,6 @@ __device__ __forceinline__ float group_sum(float v) {
 template <int G, int DX>
 constexpr bool kGatherWalk = (G == 1 && DX == 4);
 
-// slices the adjoint's ring producer moves into L2 ahead of the ring (beyond its R slots),
-// so that the copies into shared memory do not wait on memory latency
-constexpr int kL2Ahead = 4;
-
 // Adjoint of the gather x'_i = x_{a_i} for sorted ancestors (systematic resampling):
 // xbar_new[j] = sum of xbar'[i] over the offspring i of j, which form the run of entries
 // equal to j in the sorted tape row (empty for parents without offspring).  Every child
@@ -923,7 +919,6 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
             if (tid == 0) {
                 fence_proxy_async();
                 for (int k = 0; k < R && k < Ls; ++k) ring.produce(g + k, Xp(t1 - k), a.status);
-                for (int k = R; k < R + kL2Ahead && k < Ls; ++k) ring.prefetch(Xp(t1 - k));
             }
         }
         // tape row and log w_{tt-1} of step tt (which resampled) into buffer b, by
@@ -1025,10 +1020,7 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
             if (fl_next) prefetch(t - 1, nres & 1u);
             if constexpr (R > 0) {
                 ring.release(g + k);
-                if (tid == 0 && k + R < Ls) {
-                    ring.produce(g + k + R, Xp(t1 - k - R), a.status);
-                    if (k + R + kL2Ahead < Ls) ring.prefetch(Xp(t1 - k - R - kL2Ahead));
-                }
+                if (tid == 0 && k + R < Ls) ring.produce(g + k + R, Xp(t1 - k - R), a.status);
             }
         }
         if (s == 0) {

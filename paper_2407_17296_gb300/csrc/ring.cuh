@@ -71,11 +71,6 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32
         : "memory");
 }
 
-// hint: bring `bytes` of global memory at src into L2 (16-byte aligned, a multiple of 16)
-__device__ __forceinline__ void prefetch_l2(const void* src, uint32_t bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
-}
-
 // order this thread's earlier generic-proxy global writes before later async-proxy reads
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
 
@@ -107,11 +102,6 @@ struct SliceRing {
         const uint32_t bytes = (uint32_t)(sizeof(float) * padded_particles(M) * DX);
         mbar_arrive_expect_tx(&full[s], bytes);
         bulk_copy_g2s(slot(g), src, bytes, &full[s]);
-    }
-
-    // thread 0 only: start moving slice src (to be copied in later) from memory into L2
-    __device__ void prefetch(const float* src) const {
-        prefetch_l2(src, (uint32_t)(sizeof(float) * padded_particles(M) * DX));
     }
 
     // every thread: wait until slice g has landed
