@@ -232,11 +232,13 @@ void smc2::plan_sizes(const smc2_config* c, int D, int kc, Sizes* s) {
     s->xseg = (kc > 1) ? N * kc * Mp * DX * sizeof(float) + 256 : 0;
     s->lwseg = (kc > 1) ? N * kc * Mp * sizeof(float) : 0;
     s->anc = N * T * (size_t)tape_stride(c->M) * sizeof(uint16_t);
+    // first-offspring rows, read by the run-walk adjoint of sorted (systematic) resampling
+    s->offs = (c->pf_resample == SMC2_SYSTEMATIC && gather_walk(model_lanes(c, false), c->d_x)) ? s->anc : 0;
     s->flag = N * T;
     s->steps = 2 * N * (T + 1) * sizeof(float);
     s->state = sizeof(double) * (N * D * 5 + N * 6 + 2 * D + kStatsHead + 2 * D) + sizeof(int) * N + 64;
     s->obs = sizeof(float) * (T * c->d_y + c->d_y * DX);
-    s->total = s->xck + s->lwck + s->xseg + s->lwseg + s->anc + s->flag + s->steps + s->state + s->obs;
+    s->total = s->xck + s->lwck + s->xseg + s->lwseg + s->anc + s->offs + s->flag + s->steps + s->state + s->obs;
 }
 
 extern "C" int smc2_footprint(const smc2_config* cfg, size_t* bytes) {
@@ -256,7 +258,7 @@ extern "C" int smc2_footprint(const smc2_config* cfg, size_t* bytes) {
 static void free_handle_memory(smc2_handle* h) {
     void* ptrs[] = {h->y, h->H, h->prior_m, h->prior_s, h->theta, h->theta_new, h->logw, h->logpi,
                     h->gradpi, h->loglik, h->ll_new, h->grad_new, h->tmp, h->stats, h->outer_anc,
-                    h->k_dev, h->status, h->xck, h->lwck, h->xseg, h->lwseg, h->anc, h->flag, h->mstep, h->lstep};
+                    h->k_dev, h->status, h->xck, h->lwck, h->xseg, h->lwseg, h->anc, h->offs, h->flag, h->mstep, h->lstep};
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, h->stream);
     delete[] h->h_stats;
@@ -329,6 +331,7 @@ extern "C" int smc2_create(const smc2_config* cfg, smc2_handle** out) {
         {(void**)&h->xseg, s.xseg},
         {(void**)&h->lwseg, s.lwseg},
         {(void**)&h->anc, s.anc},
+        {(void**)&h->offs, s.offs},
         {(void**)&h->flag, s.flag},
         {(void**)&h->mstep, s.steps / 2},
         {(void**)&h->lstep, s.steps / 2},
@@ -423,6 +426,7 @@ PFArgs smc2::make_pf_args(smc2_handle* h, const double* theta, int n, uint32_t i
     a.xseg = h->xseg;
     a.lwseg = h->lwseg;
     a.anc = h->anc;
+    a.offs = h->offs;
     a.flag = h->flag;
     a.mstep = h->mstep;
     a.lstep = h->lstep;

@@ -31,6 +31,8 @@ struct PFArgs {
     float* xseg;            // [n][kc][Mp][DX]  (kc > 1)
     float* lwseg;           // [n][kc][Mp]      (kc > 1)
     uint16_t* anc;          // [n][T][Ma] ancestor tape (row t-1: before step t), Ma = tape_stride(M)
+    uint16_t* offs;         // [n][T][Ma] first offspring of each parent at the same steps (sorted
+                            // resampling with the run-walk adjoint), or nullptr
     uint8_t* flag;          // [n][T]   1 if the filter resampled before step t
     float* mstep;           // [n][T+1] recentring maximum of step t
     float* lstep;           // [n][T+1] log sum exp of the recentred log-weights after step t
@@ -51,6 +53,11 @@ SMC2_HD inline int tape_stride(int M) { return (M + 7) & ~7; }
 // static shared variables).
 constexpr size_t kSmemLimit = 227 * 1024 - 1024;
 
+// The adjoint of a gather with sorted ancestors walks each parent's run of offspring (whose
+// bounds the forward pass records) for the four-dimensional model with one lane per
+// particle; other model shapes use a segmented sum.
+SMC2_HD constexpr bool gather_walk(int G, int DX) { return G == 1 && DX == 4; }
+
 // Dynamic shared-memory plan (mirrored on the host to size the launch).
 struct SmemLayout {
     size_t xstage, cs, marks, starts, red, scanw, scanwi, misc, dred, bars, total;
@@ -70,8 +77,9 @@ struct SmemLayout {
                      : take(sizeof(float) * Mp * DX * (R > 0 ? R : 1));
         // fwd: multinomial cumulative weights; bwd: two log-weight buffers
         cs = fwd ? take(sizeof(float) * (size_t)M) : take(sizeof(float) * 2 * Mp);
-        // fwd: range marks; bwd: two tape-row buffers
-        marks = fwd ? take(sizeof(uint16_t) * (size_t)M) : take(sizeof(uint16_t) * 2 * (size_t)tape_stride(M));
+        // fwd: range marks; bwd: two tape-row buffers, then (run walk) two first-offspring rows
+        marks = fwd ? take(sizeof(uint16_t) * (size_t)M)
+                    : take(sizeof(uint16_t) * (gather_walk(G, DX) ? 4 : 2) * (size_t)tape_stride(M));
         starts = fwd ? o : take(sizeof(float) * 32 * G * (DX / G + 1));  // segmented-sum scratch
         red = take(sizeof(float4) * (2 * 32 + 2));  // two buffers of per-warp partials + results
         scanw = take(sizeof(unsigned long long) * 32);

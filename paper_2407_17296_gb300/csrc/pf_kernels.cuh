@@ -250,11 +250,13 @@ __device__ __forceinline__ void load_u16(const uint16_t* row, int j0, int M, int
 // the bounds between them come from its FP32 local sums, clamped to stay monotone, so
 // neighbouring threads share their common bound exactly.  The parent whose range holds a
 // warp's first child is recorded for that warp (carry), which seeds the warp's prefix-max.
-// Two __syncthreads.  anc[p] is the ancestor of particle i = j0 + p.
+// Two __syncthreads.  anc[p] is the ancestor of particle i = j0 + p, first[p] the first
+// offspring of parent j0 + p (its offspring are first[p] .. first of parent j0 + p + 1, or M).
 template <int P, int G>
 __device__ __forceinline__ void systematic_ancestors(const float (&lw)[P], bool lead, int j0, int M, float nu,
                                                      uint16_t* marks, unsigned long long* scanw,
-                                                     int* carry, int* maxoff, int (&anc)[P], int& max_offspring) {
+                                                     int* carry, int* maxoff, int (&anc)[P], int (&first)[P],
+                                                     int& max_offspring) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     constexpr int C = (32 / G) * P;  // children (particles) per warp
     if (lead) {
@@ -274,6 +276,7 @@ __device__ __forceinline__ void systematic_ancestors(const float (&lw)[P], bool 
     for (int p = 0; p < P; ++p) {
         const int j = j0 + p;
         const int hi = (j == M - 1) ? M : (p == P - 1) ? hiP : min(count_below(fmaf(sf[p], sc40, c0), M), hiP);
+        first[p] = lo;
         if (lead && j < M && hi > lo) {
             marks[lo] = (uint16_t)(j + 1);
             for (int w = max((lo + C - 1) / C, 1); w * C < hi; ++w) carry[w] = j + 1;
@@ -447,18 +450,18 @@ __device__ __forceinline__ float group_sum(float v) {
 // counts, where a long run serialises the walk; for one-dimensional states the walk's
 // data-dependent loop costs more in the steps that do not resample than it saves).
 template <int G, int DX>
-constexpr bool kGatherWalk = (G == 1 && DX == 4);
+constexpr bool kGatherWalk = gather_walk(G, DX);
 
 // Adjoint of the gather x'_i = x_{a_i} for sorted ancestors (systematic resampling):
-// xbar_new[j] = sum of xbar'[i] over the offspring i of j, which form the run of entries
-// equal to j in the sorted tape row (empty for parents without offspring).  Every child
-// stages its cotangent in its own row of `stage` (a ring slot whose states have been
-// consumed); after one barrier the thread owning parents j0 .. j0+P-1 finds the first
-// offspring of j0 by binary search in the tape row and sums its parents' runs in order
-// (deterministic; the work of a thread is its parents' offspring count).
+// xbar_new[j] = sum of xbar'[i] over the offspring i of j, the children first[j] ..
+// first[j+1] - 1 (first[M] = M) recorded by the forward pass (empty for parents without
+// offspring).  Every child stages its cotangent in its own row of `stage` (a ring slot
+// whose states have been consumed); after one barrier the thread owning parents
+// j0 .. j0+P-1 sums its parents' runs in order (deterministic; the work of a thread is
+// its parents' offspring count).
 template <int P, int DX, int DL, int G>
 __device__ __forceinline__ void gather_adjoint_runs(float (&xbar)[P][DL], int j0, int gl, int M,
-                                                    const uint16_t* ancs, float* stage) {
+                                                    const uint16_t* first, float* stage) {
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         const int i = j0 + p;
@@ -475,25 +478,20 @@ __device__ __forceinline__ void gather_adjoint_runs(float (&xbar)[P][DL], int j0
             }
         }
     }
+    int b[P + 1];
+#pragma unroll
+    for (int p = 0; p <= P; ++p) b[p] = (j0 + p < M) ? (int)first[j0 + p] : M;
     __syncthreads();
-    int lo = 0, hi = M;  // lower_bound(ancs[0 .. M), j0)
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if ((int)ancs[mid] < j0) lo = mid + 1;
-        else hi = mid;
-    }
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-        const int j = j0 + p;
         float acc[DL];
 #pragma unroll
         for (int k = 0; k < DL; ++k) acc[k] = 0.f;
-        while (lo < M && (int)ancs[lo] == j) {
+        for (int c = b[p]; c < b[p + 1]; ++c) {
             float v[DL];
-            read_staged<DX, DL>(stage, lo, gl, v);
+            read_staged<DX, DL>(stage, c, gl, v);
 #pragma unroll
             for (int k = 0; k < DL; ++k) acc[k] += v[k];
-            ++lo;
         }
 #pragma unroll
         for (int k = 0; k < DL; ++k) xbar[p][k] = acc[k];
@@ -670,6 +668,9 @@ struct Traj {
     __device__ uint16_t* anc_row(int t) const {
         return a.anc + ((size_t)f * a.T + t) * (size_t)tape_stride(a.M);
     }
+    __device__ uint16_t* offs_row(int t) const {
+        return a.offs + ((size_t)f * a.T + t) * (size_t)tape_stride(a.M);
+    }
 };
 
 // ---------------------------------------------------------------- forward pass
@@ -732,7 +733,10 @@ __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, cons
             int anc[P];
             if (a.scheme == 0) {
                 const float nu = __shfl_sync(kFull, nu_lane, (t - 1) & 31);
-                systematic_ancestors<P, G>(lw, lead, j0, M, nu, marks, scanw, carry, maxoff, anc, max_offspring);
+                int first[P];
+                systematic_ancestors<P, G>(lw, lead, j0, M, nu, marks, scanw, carry, maxoff, anc, first,
+                                           max_offspring);
+                if (a.offs && lead) store_u16<P>(tr.offs_row(t - 1), j0, M, first);
             } else {
                 multinomial_ancestors<P, G>(lw, lead, j0, M, key, (uint32_t)t, cs, scanw, anc);
             }
@@ -823,6 +827,7 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
     float* xstage = reinterpret_cast<float*>(smem + L.xstage);
     float* segw = reinterpret_cast<float*>(smem + L.starts);
     uint16_t* ancbuf = reinterpret_cast<uint16_t*>(smem + L.marks);  // two tape-row buffers
+    uint16_t* offbuf = ancbuf + 2 * (uint32_t)tape_stride(M);          // run walk: two first-offspring rows
     float* lwbuf = reinterpret_cast<float*>(smem + L.cs);             // two log-weight buffers
     double* dred = reinterpret_cast<double*>(smem + L.dred);
 
@@ -921,10 +926,10 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
                 for (int k = 0; k < R && k < Ls; ++k) ring.produce(g + k, Xp(t1 - k), a.status);
             }
         }
-        // tape row and log w_{tt-1} of step tt (which resampled) into buffer b, by
-        // asynchronous copies of 16-byte chunks issued by all threads one step ahead of use
-        // (a block has at least M/8 threads: one tape chunk and at most two log-weight
-        // chunks per thread)
+        // tape row (and first-offspring row) and log w_{tt-1} of step tt (which resampled)
+        // into buffer b, by asynchronous copies of 16-byte chunks issued by all threads one
+        // step ahead of use (a block has at least M/8 threads: one chunk of each 16-bit row
+        // and at most two log-weight chunks per thread)
         auto prefetch = [&](int tt, uint32_t b) {
             const char* ra = reinterpret_cast<const char*>(tr.anc_row(tt - 1));
             const char* rl = reinterpret_cast<const char*>(LWp(tt - 1));
@@ -932,6 +937,9 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
             char* dl = reinterpret_cast<char*>(lwbuf + b * (uint32_t)padded_particles(M));
             const int nt = blockDim.x, na = tape_stride(M) / 8, nl = padded_particles(M) / 4;
             if (tid < na) cp_async16(da + 16 * tid, ra + 16 * tid);
+            if (kGatherWalk<G, DX> && a.offs && tid < na)
+                cp_async16(reinterpret_cast<char*>(offbuf + b * (uint32_t)tape_stride(M)) + 16 * tid,
+                           reinterpret_cast<const char*>(tr.offs_row(tt - 1)) + 16 * tid);
             if (tid < nl) cp_async16(dl + 16 * tid, rl + 16 * tid);
             if (tid + nt < nl) cp_async16(dl + 16 * (tid + nt), rl + 16 * (tid + nt));
             cp_async_commit();
@@ -1003,8 +1011,9 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
                 // offspring, staged in the rows of x_t (each thread has read its own)
                 if (a.scheme != 0)
                     gather_adjoint_scatter<P, DX, DL, G>(xbar, ai, j0, gl, M, st);
-                else if (kGatherWalk<G, DX> && !(fb & 2))
-                    gather_adjoint_runs<P, DX, DL, G>(xbar, j0, gl, M, ancs, st);
+                else if (kGatherWalk<G, DX> && a.offs && !(fb & 2))
+                    gather_adjoint_runs<P, DX, DL, G>(xbar, j0, gl, M, offbuf + (nres & 1u) * (uint32_t)tape_stride(M),
+                                                      st);
                 else
                     gather_adjoint_segmented<P, DX, DL, G>(xbar, ai, j0, gl, M, ancs, st, segw);
                 // the staged cotangents (generic-proxy writes) precede the bulk copy that

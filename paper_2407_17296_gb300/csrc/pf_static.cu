@@ -53,7 +53,7 @@ size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 size_t static_need(const smc2_config& c, int D, int kc, Sizes* s) {
     plan_sizes(&c, D, kc, s);
     return align256(sizeof(float) * 256) + align256(sizeof(int)) + align256(s->xck) + align256(s->lwck) + align256(s->xseg) +
-           align256(s->lwseg) + align256(s->anc) + align256(s->flag) + 2 * align256(s->steps / 2);
+           align256(s->lwseg) + align256(s->anc) + align256(s->offs) + align256(s->flag) + 2 * align256(s->steps / 2);
 }
 
 }  // namespace
@@ -137,6 +137,7 @@ extern "C" int pf_loglik_grad_static(const smc2_config* cfg, const double* theta
     a.xseg = s.xseg ? reinterpret_cast<float*>(take(s.xseg)) : nullptr;
     a.lwseg = s.lwseg ? reinterpret_cast<float*>(take(s.lwseg)) : nullptr;
     a.anc = reinterpret_cast<uint16_t*>(take(s.anc));
+    a.offs = s.offs ? reinterpret_cast<uint16_t*>(take(s.offs)) : nullptr;
     a.flag = reinterpret_cast<uint8_t*>(take(s.flag));
     a.mstep = reinterpret_cast<float*>(take(s.steps / 2));
     a.lstep = reinterpret_cast<float*>(take(s.steps / 2));

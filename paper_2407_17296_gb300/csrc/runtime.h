@@ -20,7 +20,7 @@ constexpr double kTrajectoryBudget = 48.0e9;
 
 struct Sizes {
     int n_slots = 0;
-    size_t xck = 0, lwck = 0, xseg = 0, lwseg = 0, anc = 0, flag = 0, steps = 0, state = 0, obs = 0, total = 0;
+    size_t xck = 0, lwck = 0, xseg = 0, lwseg = 0, anc = 0, offs = 0, flag = 0, steps = 0, state = 0, obs = 0, total = 0;
 };
 
 int fail(int code, const std::string& msg);
@@ -62,6 +62,7 @@ struct smc2_handle {
     int* h_status = nullptr;    // host copy of the status word
     float *xck = nullptr, *lwck = nullptr, *xseg = nullptr, *lwseg = nullptr, *mstep = nullptr, *lstep = nullptr;
     uint16_t* anc = nullptr;
+    uint16_t* offs = nullptr;
     uint8_t* flag = nullptr;
     double* h_stats = nullptr;  // host copy of the outer statistics
     uint32_t k = 0;             // iterations enqueued
