@@ -47,7 +47,7 @@ ALG_OPS_STRICT = {"lg1": 33 + 14, "lg4": 94 + 47, "sv": 36 + 15, "lg16": 333 + 1
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per filter of the forward +
 # adjoint pair, measured with ncu on a launch of 304 filters of the 4-d workload's shape
 # (M = 1024, T = 250, every step stored); a launch of N filters moves N times this.
-TRAFFIC_PER_FILTER = {("lg4", 1024, 250): (1401.364e6 + 1457.115e6) / 304}
+TRAFFIC_PER_FILTER = {("lg4", 1024, 250): (1484.644e6 + 1542.551e6) / 304}
 
 
 def _args():
@@ -163,7 +163,9 @@ def cpu_oracle_rate(w, budget_s, procs=None):
     t0 = time.perf_counter()
     _oracle_filter((w.family, w.dx, w.dy, H, theta[0], w.y, w.M, w.seed, 2, 0))
     one = time.perf_counter() - t0
-    n = int(max(procs, min(w.N, budget_s * procs / max(one, 1e-6))))
+    # enough filter runs for the budget, cycling over the iteration's filters when they
+    # are fewer (small workloads would otherwise time milliseconds of pool overhead)
+    n = int(max(procs, min(64 * w.N, budget_s * procs / max(one, 1e-6))))
     n = max(procs, (n // procs) * procs)
     jobs = [(w.family, w.dx, w.dy, H, theta[i % w.N], w.y, w.M, w.seed, 2, i % w.N) for i in range(n)]
     ctx = mp.get_context("spawn")
@@ -327,8 +329,8 @@ def run_gpu(a, rank, world, local):
     if not a.no_cpu_baseline:
         rate, cores, info = cpu_oracle_rate(w, a.cpu_seconds, a.cpu_procs or None)
         out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                               "sample": f"{info['filters']} of {info['of']} filters of one iteration "
-                                         f"(forward + forward-mode gradient, FP64), spawn pool, "
+                               "sample": f"{info['filters']} filter runs over the {info['of']} filters of one "
+                                         f"iteration (forward + forward-mode gradient, FP64), spawn pool, "
                                          f"{info['seconds']:.1f} s"}
     if world > 1:
         import torch.distributed as dist
