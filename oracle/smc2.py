@@ -18,6 +18,15 @@ Readings where the paper is silent or inconsistent:
     importance weight with no accept/reject;
   * log pi-hat and its gradient travel with each sample through resampling;
   * the prior is N(prior_mean, diag(prior_std^2)).
+
+The HMC proposal (the extension Sec. V names, "hmc"): L leapfrog steps of Hamiltonian
+dynamics whose single step is the SMC1 move above (Sec. III-D notes that Langevin is HMC
+with one step).  In displacement form the momentum is v ~ N(0, gamma^2 I) with kinetic
+energy |v|^2 / (2 gamma^2), and each step is v += F(theta); theta += v; v += F(theta).
+The L-kernel that reverses the momentum weights the end point by
+pi(theta_L) N(v_L; 0, gamma^2 I) / (pi(theta_0) N(v_0; 0, gamma^2 I)); with L = 1 this is
+the Langevin weight above.  Every leapfrog point runs the particle filters with the
+iteration's CRN keys.
 """
 import math
 
@@ -104,6 +113,29 @@ class State:
         self.loglik = np.zeros(N)
 
 
+def leapfrog(theta, v, gradpi, L, gamma, grad_fn):
+    """L leapfrog steps from (theta, v) with grad log pi(theta) = gradpi, in displacement
+    form (force F = 0.5 gamma^2 grad log pi): v += F; theta += v; v += F.  grad_fn(theta, l)
+    returns (log pi, grad log pi) at the l-th new point (l = 0 .. L-1).  Returns the end
+    point, its momentum, log pi and gradient, and the log pi of every point visited."""
+    half = 0.5 * gamma * gamma
+    lps = []
+    lp = None
+    for l in range(L):
+        v = v + half * gradpi
+        theta = theta + v
+        lp, gradpi = grad_fn(theta, l)
+        lps.append(lp)
+        v = v + half * gradpi
+    return theta, v, lp, gradpi, lps
+
+
+def hmc_xi(state, k, seed):
+    """The momentum normals of iteration k (Philox stream 3, as the SMC0/SMC1 moves)."""
+    N, D = state.theta.shape
+    return np.stack([_normals(seed, k, i, 0, STREAM_OUTER_XI, D) for i in range(N)])
+
+
 def propose(state, k, seed, gamma, proposal, m0, s0, prior_kind=GAUSSIAN_PRIOR):
     """theta' for iteration k: a prior draw at k = 1 (Eq. init_sample; a uniform prior maps the
     normal xi through its CDF), else the random-walk (SMC0) or Langevin (SMC1) move of
@@ -119,15 +151,23 @@ def propose(state, k, seed, gamma, proposal, m0, s0, prior_kind=GAUSSIAN_PRIOR):
 
 
 def update(state, k, theta_new, ll_new, g_new, seed, gamma, proposal, m0, s0, hint=None,
-           outer_band=1e-4, outer_flag_band=1e-3, prior_kind=GAUSSIAN_PRIOR):
+           outer_band=1e-4, outer_flag_band=1e-3, prior_kind=GAUSSIAN_PRIOR, kinetic=None):
     """Complete iteration k from the filter outputs at theta_new: weight, normalise,
-    estimate, recycling statistic, ESS, resampling.  Updates state; returns the record."""
+    estimate, recycling statistic, ESS, resampling.  Updates state; returns the record.
+    kinetic (HMC): (|v_0|^2, |v_L|^2) / (2 gamma^2) per sample, NaN where a leapfrog point
+    failed."""
     N = state.logw.shape[0]
     lp_new = log_prior(theta_new, m0, s0, prior_kind) + ll_new
     gp_new = grad_log_prior(theta_new, m0, s0, prior_kind) + g_new
     if k == 1:
         # w_1 = pi/q_1 = p-hat(y|theta) (Eq. init_weights)
         logw = ll_new.copy()
+    elif proposal == "hmc":
+        # momentum-reversal L-kernel: pi(theta_L) N(v_L) / (pi(theta_0) N(v_0))
+        ke0, keL = kinetic
+        ok = (state.logw > -np.inf) & (lp_new > -np.inf) & (state.logpi > -np.inf)
+        with np.errstate(invalid="ignore", over="ignore"):
+            logw = np.where(ok, state.logw + lp_new - state.logpi + ke0 - keL, -np.inf)
     else:
         if proposal == "langevin":
             drift = 0.5 * gamma * gamma * state.gradpi
@@ -145,7 +185,7 @@ def update(state, k, theta_new, ll_new, g_new, seed, gamma, proposal, m0, s0, hi
     # The Langevin kernels (the SMC1 proposal of Sec. III-D, the L-kernel of Sec. III-E) need
     # grad log pi at the proposal.  Where it is not finite the sample can neither be
     # weighted nor moved: it carries weight zero, as does any non-finite weight.
-    grad_ok = np.all(np.isfinite(gp_new), axis=1) if proposal == "langevin" else np.ones(N, bool)
+    grad_ok = np.all(np.isfinite(gp_new), axis=1) if proposal in ("langevin", "hmc") else np.ones(N, bool)
     logw = np.where(grad_ok & np.isfinite(logw), logw, -np.inf)
     theta, logpi, gradpi, loglik = theta_new, lp_new, gp_new, ll_new
 
@@ -188,10 +228,11 @@ def recycled_mean(records):
 def run(family, dx, dy, H, y, N, M, K, gamma, proposal, seed, prior_mean=None, prior_std=None,
         scheme=SYSTEMATIC, ess_frac=0.5, hints=None, band=1e-6, flag_band=1e-6,
         outer_band=1e-4, D=None, loglik_grad_fn=None, band_rel=0.0, outer_flag_band=1e-3,
-        prior_kind=GAUSSIAN_PRIOR):
+        prior_kind=GAUSSIAN_PRIOR, hmc_steps=1):
     """Run K iterations; returns (list of per-iteration records, recycled mean).
 
-    proposal: "rw" (SMC0) or "langevin" (SMC1).
+    proposal: "rw" (SMC0), "langevin" (SMC1) or "hmc" (hmc_steps leapfrog steps; the hints,
+      when given, apply to the filters at the last leapfrog point).
     hints: optional list, per iteration, of dicts with keys pf_anc (N,T,M), pf_flag (N,T),
       outer_anc (N,), outer_flag (bool): decisions taken elsewhere, followed at near-ties
       (PF level: |c - tau| < band; outer level: |c - tau| < outer_band, and the resampling
@@ -208,12 +249,38 @@ def run(family, dx, dy, H, y, N, M, K, gamma, proposal, seed, prior_mean=None, p
     state = State(N, D)
     for k in range(1, K + 1):
         hint = hints[k - 1] if hints is not None else None
-        theta_new = propose(state, k, seed, gamma, proposal, m0, s0, prior_kind)
-        ll_new, g_new, pfstats, pfrows = run_filters(family, dx, dy, H, y, M, seed, k, theta_new,
-                                                     range(N), scheme, ess_frac, hint, band, flag_band,
-                                                     band_rel, loglik_grad_fn)
+        kinetic = None
+        if proposal == "hmc" and k > 1:
+            L = int(hmc_steps)
+            last = {}
+
+            def grad_fn(th, l):
+                ll, g, st, rows = run_filters(family, dx, dy, H, y, M, seed, k, th, range(N), scheme,
+                                              ess_frac, hint if l == L - 1 else None, band, flag_band,
+                                              band_rel, loglik_grad_fn)
+                last.update(ll=ll, g=g, st=st, rows=rows)
+                lp = log_prior(th, m0, s0, prior_kind) + ll
+                gp = grad_log_prior(th, m0, s0, prior_kind) + g
+                # a point whose estimate or gradient is not finite breaks the trajectory
+                bad = ~(np.isfinite(lp) & np.all(np.isfinite(gp), axis=1))
+                last["bad"] = last.get("bad", np.zeros(N, bool)) | bad
+                return lp, gp
+
+            xi = hmc_xi(state, k, seed)
+            theta_new, vL, _, _, _ = leapfrog(state.theta, gamma * xi, state.gradpi, L, gamma, grad_fn)
+            ll_new, g_new, pfstats, pfrows = last["ll"], last["g"], last["st"], last["rows"]
+            ke0 = 0.5 * np.sum(xi * xi, axis=1)
+            with np.errstate(invalid="ignore", over="ignore"):
+                keL = 0.5 * np.sum(vL * vL, axis=1) / (gamma * gamma)
+            keL = np.where(last["bad"], np.nan, keL)
+            kinetic = (ke0, keL)
+        else:
+            theta_new = propose(state, k, seed, gamma, proposal, m0, s0, prior_kind)
+            ll_new, g_new, pfstats, pfrows = run_filters(family, dx, dy, H, y, M, seed, k, theta_new,
+                                                         range(N), scheme, ess_frac, hint, band, flag_band,
+                                                         band_rel, loglik_grad_fn)
         rec = update(state, k, theta_new, ll_new, g_new, seed, gamma, proposal, m0, s0, hint,
-                     outer_band, outer_flag_band, prior_kind)
+                     outer_band, outer_flag_band, prior_kind, kinetic)
         rec["pf_stats"] = pfstats
         rec["pf_stats_rows"] = pfrows
         records.append(rec)
