@@ -62,6 +62,9 @@ def _args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--N", type=int, default=0, help="override the number of samples (profiling runs)")
     p.add_argument("--no-autotune", action="store_true", help="use the default launch configuration")
+    p.add_argument("--hmc-steps", type=int, default=0,
+                   help="run the workload with the HMC proposal of this many leapfrog steps "
+                        "(step gamma / sqrt(L); every step runs the N filters)")
     p.add_argument("--launch", default=None,
                    help="pin the launch instead of tuning: fwd_ppt,fwd_regs,adj_ppt,adj_regs,ckpt")
     p.add_argument("--experiment", default=None, choices=["lgssm"],
@@ -194,6 +197,11 @@ def run_gpu(a, rank, world, local):
     w = workloads.ALL[a.workload]()
     if a.N:
         w = w.with_sizes(N=a.N)
+    if a.hmc_steps:
+        # leapfrog step gamma / sqrt(L): Langevin-sized steps over several points leave the
+        # outer weights degenerate on these workloads
+        from dataclasses import replace
+        w = replace(w, proposal="hmc", hmc_steps=a.hmc_steps, gamma=w.gamma / math.sqrt(a.hmc_steps))
     # weak scaling: every rank runs its own independent job (own seed), no data-path collective
     w.seed = w.seed + 1000 * rank
     binding.load()
@@ -206,7 +214,8 @@ def run_gpu(a, rank, world, local):
         binding.autotune(cfg, workloads.thetas_near(w, w.N, 0.05, seed=5))
     h = binding.Handle(cfg)
     launch = h.launch()
-    ps_per_step = w.N * w.M * w.T
+    ps_launch = w.N * w.M * w.T  # particle-steps of one filter launch (one leapfrog point)
+    ps_per_step = ps_launch * (w.hmc_steps if w.proposal == "hmc" else 1)
 
     def barrier():
         if world > 1:
@@ -287,8 +296,8 @@ def run_gpu(a, rank, world, local):
     sm_count = props.multi_processor_count
     max_mhz = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
     peak_tops = sm_count * 128 * max_mhz * 1e6 / 1e12
-    achieved_tops = ALG_OPS.get(w.name, 0) * ps_per_step / (pf_ms / 1e3) / 1e12
-    strict_tops = ALG_OPS_STRICT.get(w.name, 0) * ps_per_step / (pf_ms / 1e3) / 1e12
+    achieved_tops = ALG_OPS.get(w.name, 0) * ps_launch / (pf_ms / 1e3) / 1e12
+    strict_tops = ALG_OPS_STRICT.get(w.name, 0) * ps_launch / (pf_ms / 1e3) / 1e12
     per_filter = TRAFFIC_PER_FILTER.get((w.name, w.M, w.T))
     traffic = per_filter * w.N if per_filter else None
     out = {
@@ -308,7 +317,10 @@ def run_gpu(a, rank, world, local):
                    "N": w.N, "M": w.M, "T": w.T, "D": w.D, "proposal": w.proposal, "gamma": w.gamma,
                    "launch": {"forward_ppt": launch[0], "forward_regs": launch[1], "adjoint_ppt": launch[2],
                               "adjoint_regs": launch[3], "ckpt_every": launch[4]},
-                   "step": "one SMC2 iteration: propose, N filters fwd+adjoint, L-kernel weights, resample",
+                   "step": ("one SMC2 iteration: propose, N filters fwd+adjoint, L-kernel weights, resample"
+                            if w.proposal != "hmc" else
+                            f"one SMC2 iteration: HMC move of {w.hmc_steps} leapfrog steps (N filters "
+                            f"fwd+adjoint at each point), L-kernel weights, resample"),
                    "dead_samples": dead,
                    "l2": "inputs larger than L2 (particle trajectory of several GB written and read per step)",
                    "parallelism": f"replicas x{world} (independent jobs)"},

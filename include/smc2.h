@@ -49,8 +49,12 @@ extern "C" {
  *    1/rho^2 = 1/phi^2 + 1/sigma^2, and weights p(y_t | x_{t-1}) = N(y_t; mu x_{t-1},
  *    phi^2 + sigma^2). */
 enum { SMC2_LG_DIAG = 0, SMC2_SV = 1, SMC2_LG_OPT = 2 };
-/* Outer proposals (Sec. III-D): SMC0 random walk, SMC1 Langevin. */
-enum { SMC2_RW = 0, SMC2_LANGEVIN = 1 };
+/* Outer proposals (Sec. III-D): SMC0 random walk, SMC1 Langevin, and HMC (the extension
+ * Sec. V names): hmc_steps leapfrog steps whose single step is the SMC1 move, with
+ * momentum v ~ N(0, gamma^2 I) and the momentum-reversal L-kernel, i.e. the weight
+ * pi(theta_L) N(v_L; 0, gamma^2 I) / (pi(theta_0) N(v_0; 0, gamma^2 I)).  Every leapfrog
+ * point runs the N particle filters (forward + adjoint) with the iteration's CRN keys. */
+enum { SMC2_RW = 0, SMC2_LANGEVIN = 1, SMC2_HMC = 2 };
 /* Particle-filter resampler (Sec. II-B, App. B). */
 enum { SMC2_SYSTEMATIC = 0, SMC2_MULTINOMIAL = 1 };
 /* Prior on theta: Gaussian N(prior_mean, diag(prior_std^2)), or uniform on the box
@@ -68,7 +72,7 @@ typedef struct smc2_config {
     int32_t T, N, M, D;         /* D must equal the family's parameter count */
     const double* prior_mean;   /* host [D] or NULL (zeros); prior N(mean, diag(std^2)) */
     const double* prior_std;    /* host [D] or NULL (ones) */
-    int32_t proposal;           /* SMC2_RW or SMC2_LANGEVIN */
+    int32_t proposal;           /* SMC2_RW, SMC2_LANGEVIN or SMC2_HMC */
     double gamma;               /* step size, Gamma = gamma^2 I */
     int32_t K_iters;            /* iterations for a served job (smc2_submit) */
     int32_t pf_resample;        /* SMC2_SYSTEMATIC or SMC2_MULTINOMIAL */
@@ -78,9 +82,11 @@ typedef struct smc2_config {
     int32_t particles_per_thread; /* 0 = automatic (autotuned), else 1, 2, 4 or 8 */
     void* stream;               /* cudaStream_t for all work of the handle; NULL = a private stream */
     int32_t prior_kind;         /* SMC2_PRIOR_GAUSSIAN (default) or SMC2_PRIOR_UNIFORM */
+    int32_t hmc_steps;          /* SMC2_HMC: leapfrog steps per move, 1..64 (1 = the SMC1 move) */
 } smc2_config;
 
-/* Fill defaults: struct_size, ess_frac 0.5, K_iters 10, systematic, Langevin, gamma 0.1. */
+/* Fill defaults: struct_size, ess_frac 0.5, K_iters 10, systematic, Langevin, gamma 0.1,
+ * hmc_steps 1. */
 void smc2_config_init(smc2_config* cfg);
 
 typedef struct smc2_handle smc2_handle;
@@ -133,7 +139,8 @@ int pf_loglik_grad_host(smc2_handle* h, const double* theta_host, int n, uint32_
  * smc2_step: one SMC^2 iteration k (k counts from 1 per handle).
  *  k = 1: theta ~ prior (Eq. init_sample), PF, w = pi/q_1 (Eq. init_weights).
  *  k > 1: Langevin or random-walk move (Sec. III-D), PF at the new theta, weight with
- *         the L-kernel (Eq. l_weights, Sec. III-E).
+ *         the L-kernel (Eq. l_weights, Sec. III-E); with SMC2_HMC, hmc_steps leapfrog steps
+ *         (a PF forward + adjoint at every point) and the momentum-reversal weight.
  *  then normalise, estimate, recycling statistic, ESS and, if N_eff < N/2,
  *  systematic resampling (Sec. III-A..C).  Fills *out (may be NULL) on the host:
  *  this call synchronises the handle's stream.
@@ -175,7 +182,8 @@ int smc2_get_step_timing(smc2_handle* h, float* ms);
  * Replicas that pass the same N rows to smc2_step_update stay identical, and equal to one
  * handle running smc2_step.  The two calls must alternate; smc2_step_update without a
  * preceding smc2_step_filters, or n < 0, row0 < 0, row0 + n > N, or NULL buffers with n > 0:
- * SMC2_E_INVAL.  Launch failures: SMC2_E_CUDA.
+ * SMC2_E_INVAL; so is a handle with the SMC2_HMC proposal (its leapfrog needs every
+ * sample's filters at each point).  Launch failures: SMC2_E_CUDA.
  */
 int smc2_step_filters(smc2_handle* h, int row0, int n, double* loglik_dev, double* grad_dev);
 int smc2_step_update(smc2_handle* h, const double* loglik_all_dev, const double* grad_all_dev,

@@ -17,7 +17,8 @@ ERRORS = {-1: "SMC2_E_INVAL", -2: "SMC2_E_NOMEM", -3: "SMC2_E_CUDA", -4: "SMC2_E
           -5: "SMC2_E_NOTFOUND", -6: "SMC2_E_BUSY"}
 LG_DIAG, SV, LG_OPT = 0, 1, 2
 PRIOR_GAUSSIAN, PRIOR_UNIFORM = 0, 1
-RW, LANGEVIN = 0, 1
+RW, LANGEVIN, HMC = 0, 1, 2
+PROPOSALS = {"rw": RW, "langevin": LANGEVIN, "hmc": HMC}
 SYSTEMATIC, MULTINOMIAL = 0, 1
 
 # every symbol include/smc2.h declares
@@ -54,6 +55,7 @@ class Config(ctypes.Structure):
         ("particles_per_thread", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
         ("prior_kind", ctypes.c_int32),
+        ("hmc_steps", ctypes.c_int32),
     ]
 
 
@@ -169,7 +171,7 @@ def _ptr(t):
 def make_config(family, dx, dy, T, N, M, D, y, H=None, prior_mean=None, prior_std=None,
                 proposal=LANGEVIN, gamma=0.1, K_iters=10, pf_resample=SYSTEMATIC, ess_frac=0.5,
                 seed=777, ckpt_every=0, particles_per_thread=0, stream=None, y_on_device=False,
-                prior_kind=PRIOR_GAUSSIAN):
+                prior_kind=PRIOR_GAUSSIAN, hmc_steps=1):
     """Build a Config; numpy arrays referenced by it are kept alive on the returned object."""
     import numpy as np
     lib = load()
@@ -205,6 +207,7 @@ def make_config(family, dx, dy, T, N, M, D, y, H=None, prior_mean=None, prior_st
     c.particles_per_thread = int(particles_per_thread)
     c.stream = stream
     c.prior_kind = int(prior_kind)
+    c.hmc_steps = int(hmc_steps)
     c._keep = keep
     return c
 
@@ -430,10 +433,10 @@ def footprint(cfg: Config) -> int:
 
 def config_for(workload, **kw):
     """Config for a workloads.Workload (sizes, data and step size taken from it)."""
-    prop = LANGEVIN if workload.proposal == "langevin" else RW
-    args = dict(proposal=prop, gamma=workload.gamma, K_iters=workload.K, seed=workload.seed,
-                prior_mean=workload.prior_mean, prior_std=workload.prior_std,
-                prior_kind=getattr(workload, "prior_kind", PRIOR_GAUSSIAN))
+    args = dict(proposal=PROPOSALS[workload.proposal], gamma=workload.gamma, K_iters=workload.K,
+                seed=workload.seed, prior_mean=workload.prior_mean, prior_std=workload.prior_std,
+                prior_kind=getattr(workload, "prior_kind", PRIOR_GAUSSIAN),
+                hmc_steps=getattr(workload, "hmc_steps", 1))
     args.update(kw)
     return make_config(workload.family, workload.dx, workload.dy, workload.T, workload.N, workload.M,
                        workload.D, workload.y, workload.H, **args)

@@ -67,6 +67,7 @@ extern "C" void smc2_config_init(smc2_config* c) {
     c->d_x = 1;
     c->d_y = 1;
     c->proposal = SMC2_LANGEVIN;
+    c->hmc_steps = 1;
     c->gamma = 0.1;
     c->K_iters = 10;
     c->pf_resample = SMC2_SYSTEMATIC;
@@ -193,7 +194,10 @@ int smc2::validate(const smc2_config* c, int* D) {
     if (!(c->ess_frac >= 0.f && c->ess_frac <= 1.f)) return fail(SMC2_E_INVAL, "ess_frac must be in [0, 1]");
     if (c->pf_resample != SMC2_SYSTEMATIC && c->pf_resample != SMC2_MULTINOMIAL)
         return fail(SMC2_E_INVAL, "unknown pf_resample");
-    if (c->proposal != SMC2_RW && c->proposal != SMC2_LANGEVIN) return fail(SMC2_E_INVAL, "unknown proposal");
+    if (c->proposal != SMC2_RW && c->proposal != SMC2_LANGEVIN && c->proposal != SMC2_HMC)
+        return fail(SMC2_E_INVAL, "unknown proposal");
+    if (c->proposal == SMC2_HMC && (c->hmc_steps < 1 || c->hmc_steps > 64))
+        return fail(SMC2_E_INVAL, "hmc_steps must be in [1, 64]");
     if (!(c->gamma > 0.0)) return fail(SMC2_E_INVAL, "gamma must be positive");
     if (c->ckpt_every < 0) return fail(SMC2_E_INVAL, "ckpt_every must be >= 0");
     const int P = c->particles_per_thread;
@@ -236,7 +240,7 @@ void smc2::plan_sizes(const smc2_config* c, int D, int kc, Sizes* s) {
     s->offs = (c->pf_resample == SMC2_SYSTEMATIC && gather_walk(model_lanes(c, false), c->d_x)) ? s->anc : 0;
     s->flag = N * T;
     s->steps = 2 * N * (T + 1) * sizeof(float);
-    s->state = sizeof(double) * (N * D * 5 + N * 6 + 2 * D + kStatsHead + 2 * D) + sizeof(int) * N + 64;
+    s->state = sizeof(double) * (N * D * 6 + N * 7 + 2 * D + kStatsHead + 2 * D) + sizeof(int) * N + 64;
     s->obs = sizeof(float) * (T * c->d_y + c->d_y * DX);
     s->total = s->xck + s->lwck + s->xseg + s->lwseg + s->anc + s->offs + s->flag + s->steps + s->state + s->obs;
 }
@@ -257,7 +261,7 @@ extern "C" int smc2_footprint(const smc2_config* cfg, size_t* bytes) {
 
 static void free_handle_memory(smc2_handle* h) {
     void* ptrs[] = {h->y, h->H, h->prior_m, h->prior_s, h->theta, h->theta_new, h->logw, h->logpi,
-                    h->gradpi, h->loglik, h->ll_new, h->grad_new, h->tmp, h->stats, h->outer_anc,
+                    h->gradpi, h->loglik, h->ll_new, h->grad_new, h->tmp, h->mom, h->ke, h->stats, h->outer_anc,
                     h->k_dev, h->status, h->xck, h->lwck, h->xseg, h->lwseg, h->anc, h->offs, h->flag, h->mstep, h->lstep};
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, h->stream);
@@ -322,6 +326,8 @@ extern "C" int smc2_create(const smc2_config* cfg, smc2_handle** out) {
         {(void**)&h->ll_new, sizeof(double) * N},
         {(void**)&h->grad_new, sizeof(double) * N * D},
         {(void**)&h->tmp, sizeof(double) * N * D},
+        {(void**)&h->mom, sizeof(double) * N * D},
+        {(void**)&h->ke, sizeof(double) * N},
         {(void**)&h->stats, sizeof(double) * (kStatsHead + 2 * D)},
         {(void**)&h->outer_anc, sizeof(int) * N},
         {(void**)&h->k_dev, sizeof(uint32_t)},
@@ -523,19 +529,37 @@ OuterArgs smc2::make_outer_args(smc2_handle* h) {
     o.ll_new = h->ll_new;
     o.grad_new = h->grad_new;
     o.tmp = h->tmp;
+    o.hmc = h->cfg.proposal == SMC2_HMC;
+    o.mom = h->mom;
+    o.ke = h->ke;
     o.stats = h->stats;
     o.outer_anc = h->outer_anc;
     return o;
 }
 
+// Kernel launches of one iteration after the first: propose, the filter passes of every
+// leapfrog point (one point for RW and Langevin), the leapfrog kicks between them, update.
+static int launches_per_step(const smc2_handle* h) {
+    const int L = h->cfg.proposal == SMC2_HMC ? h->cfg.hmc_steps : 1;
+    return 1 + 2 * L + (L - 1) + kOuterUpdateLaunches;
+}
+
 int smc2::enqueue_step(smc2_handle* h) {
     const OuterArgs o = make_outer_args(h);
-    if (launch_outer_propose(o, h->stream)) return fail(SMC2_E_CUDA, "outer propose launch failed");
+    // iteration 1 draws from the prior: every proposal takes the same path there
+    const bool hmc = o.hmc && h->k >= 1;
+    const int L = hmc ? h->cfg.hmc_steps : 1;
+    if ((hmc ? launch_hmc_start(o, h->stream) : launch_outer_propose(o, h->stream)))
+        return fail(SMC2_E_CUDA, "outer propose launch failed");
     const PFArgs a = make_pf_args(h, h->theta_new, h->cfg.N, 0u, 0u, h->k_dev, h->ll_new, h->grad_new);
-    int rc = launch_filters(h, a, h->timing);
-    if (rc) return rc;
+    for (int l = 0; l < L; ++l) {
+        // timing mode times the filter passes at the last leapfrog point (one launch each)
+        int rc = launch_filters(h, a, h->timing && l == L - 1);
+        if (rc) return rc;
+        if (l < L - 1 && launch_hmc_leap(o, h->stream)) return fail(SMC2_E_CUDA, "leapfrog launch failed");
+    }
     if (launch_outer_update(o, h->stream)) return fail(SMC2_E_CUDA, "outer update launch failed");
-    count_launches(1 + kOuterUpdateLaunches);
+    count_launches(1 + (L - 1) + kOuterUpdateLaunches);
     return SMC2_OK;
 }
 
@@ -565,7 +589,7 @@ int smc2::step_async(smc2_handle* h) {
     }
     if (h->graph_exec && !h->timing) {
         CUDA_TRY(cudaGraphLaunch(h->graph_exec, h->stream));
-        count_launches(3 + kOuterUpdateLaunches);
+        count_launches(launches_per_step(h));
     } else {
         int rc = enqueue_step(h);
         if (rc) return rc;
@@ -656,6 +680,9 @@ extern "C" int smc2_step(smc2_handle* h, smc2_stats* out) {
 extern "C" int smc2_step_filters(smc2_handle* h, int row0, int n, double* loglik_dev, double* grad_dev) {
     if (!h) return fail(SMC2_E_INVAL, "handle is NULL");
     if (h->split_pending) return fail(SMC2_E_INVAL, "smc2_step_update must follow smc2_step_filters");
+    if (h->cfg.proposal == SMC2_HMC)
+        return fail(SMC2_E_INVAL, "the split step supports the random-walk and Langevin proposals "
+                                  "(an HMC move needs every sample's filters at each leapfrog point)");
     if (row0 < 0 || n < 0 || row0 + n > h->cfg.N) return fail(SMC2_E_INVAL, "rows must lie in [0, N)");
     if (n > 0 && (!loglik_dev || !grad_dev)) return fail(SMC2_E_INVAL, "loglik and grad must not be NULL");
     const OuterArgs o = make_outer_args(h);

@@ -8,6 +8,10 @@
 //   log w += log pi(theta') - log pi(theta) + log L(theta|theta') - log q(theta'|theta).
 // Iteration 1 draws theta from the prior (Eq. init_sample) and weights by
 // pi/q_1 = p-hat(y|theta) (Eq. init_weights).
+// HMC (the extension Sec. V names): hmc_steps leapfrog steps in displacement form, momentum
+// v ~ N(0, gamma^2 I), each step v += F(theta); theta += v; v += F(theta) (one step is the
+// SMC1 move), the filters run at every new point; the momentum-reversal L-kernel gives
+//   log w += log pi(theta_L) - log pi(theta_0) + |v_0|^2/(2 gamma^2) - |v_L|^2/(2 gamma^2).
 // Then: normalise (Eq. normalise_smc2), estimate f~_k = sum w~ theta (Eq. realised_estimates),
 // l_k = (sum w)^2 / sum w^2 (Eq. recycling_I), ESS (Eq. ess_smc2) and, if ESS < N/2,
 // systematic resampling with one uniform per iteration (Philox stream 4), ancestors
@@ -131,6 +135,52 @@ __device__ double log_prior_at(const OuterArgs& a, const double* th, const doubl
     return log_prior(th, a.prior_mean, pinv, pinv[64], a.D);
 }
 
+// HMC start (iteration k > 1), one thread a sample: v_0 = gamma xi (kinetic energy
+// |xi|^2 / 2), first half kick with the sample's stored grad log pi, first drift.
+__global__ void hmc_start_kernel(OuterArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.N) return;
+    const uint32_t k = *a.k_dev + 1u;
+    const PhiloxKey key = philox_key(a.seed_lo, a.seed_hi, k, (uint32_t)i);
+    const double half = 0.5 * a.gamma * a.gamma;
+    double ke = 0.0;
+    for (int d = 0; d < a.D; ++d) {
+        const size_t idx = (size_t)i * a.D + d;
+        const double xi = outer_normal(key, d);
+        ke += 0.5 * xi * xi;
+        const double v = a.gamma * xi + half * a.gradpi[idx];
+        a.mom[idx] = v;
+        a.theta_new[idx] = a.theta[idx] + v;
+    }
+    a.ke[i] = ke;
+}
+
+// Between leapfrog points, one thread a sample: grad log pi at theta_l (prior term plus the
+// filter's gradient), the two half kicks v += gamma^2 grad log pi, the next drift.  A point
+// whose posterior estimate or gradient is not finite breaks the trajectory: the start
+// kinetic energy becomes NaN, so the sample's weight is zero.
+__global__ void hmc_leap_kernel(OuterArgs a) {
+    __shared__ double pinv[65];
+    prior_constants(a, pinv);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.N) return;
+    const int D = a.D;
+    double* th = a.theta_new + (size_t)i * D;
+    const double lln = a.ll_new[i];
+    const double lp = (lln > -INFINITY) ? log_prior_at(a, th, pinv) + lln : -INFINITY;
+    bool ok = isfinite(lp);
+    const double g2 = a.gamma * a.gamma;
+    for (int d = 0; d < D; ++d) {
+        const size_t idx = (size_t)i * D + d;
+        const double gp = -(th[d] - a.prior_mean[d]) * pinv[d] * pinv[d] + a.grad_new[idx];
+        ok = ok && isfinite(gp);
+        const double v = a.mom[idx] + g2 * gp;
+        a.mom[idx] = v;
+        th[d] = th[d] + v;
+    }
+    if (!ok) a.ke[i] = __longlong_as_double(0x7ff8000000000000ll);
+}
+
 // 1. pseudo-marginal update of every sample with its particle-filter result (one thread a
 //    sample, any number of blocks)
 __global__ void outer_weight_kernel(OuterArgs a) {
@@ -148,7 +198,7 @@ __global__ void outer_weight_kernel(OuterArgs a) {
     // is not finite (e.g. FP32 overflow under explosive dynamics) the sample cannot be
     // weighted or moved and carries weight zero, as does any non-finite weight
     bool grad_ok = true;
-    if (a.langevin)
+    if (a.langevin || a.hmc)
         for (int d = 0; d < D; ++d) grad_ok = grad_ok && isfinite(a.grad_new[(size_t)i * D + d]);
     double lw;
     if (k == 1u) {
@@ -171,6 +221,15 @@ __global__ void outer_weight_kernel(OuterArgs a) {
                     lf += bwd * bwd;
                 }
                 corr = -0.5 * (lf - qf) / g2;
+            } else if (a.hmc) {
+                // momentum at the end point v_L = v + F(theta_L); momentum-reversal L-kernel
+                double kl = 0.0;
+                for (int d = 0; d < D; ++d) {
+                    const double gpn = -(thn[d] - a.prior_mean[d]) * pinv[d] * pinv[d] + a.grad_new[(size_t)i * D + d];
+                    const double vl = a.mom[(size_t)i * D + d] + 0.5 * g2 * gpn;
+                    kl += vl * vl;
+                }
+                corr = a.ke[i] - 0.5 * kl / g2;  // NaN for a broken trajectory
             }
             lw = lw + (lpn - a.logpi[i]) + corr;
         } else {
@@ -336,6 +395,16 @@ int launch_outer_propose(const OuterArgs& a, void* stream) {
     const int threads = 256;
     const int blocks = (total + threads - 1) / threads;
     outer_propose_kernel<<<blocks, threads, 0, static_cast<cudaStream_t>(stream)>>>(a);
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+int launch_hmc_start(const OuterArgs& a, void* stream) {
+    hmc_start_kernel<<<(a.N + 127) / 128, 128, 0, static_cast<cudaStream_t>(stream)>>>(a);
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+int launch_hmc_leap(const OuterArgs& a, void* stream) {
+    hmc_leap_kernel<<<(a.N + 127) / 128, 128, 0, static_cast<cudaStream_t>(stream)>>>(a);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 

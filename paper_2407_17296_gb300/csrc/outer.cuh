@@ -24,6 +24,9 @@ struct OuterArgs {
     double* tmp;                  // [N][D] gather scratch
     double* stats;                // [kStatsHead + 2D]
     int* outer_anc;               // [N]
+    int hmc;                      // 1: HMC proposal (iterations k > 1)
+    double* mom;                  // [N][D] HMC leapfrog momentum (displacement form)
+    double* ke;                   // [N] HMC kinetic energy at the start, NaN if the trajectory broke
 };
 
 // stats layout (FP64 slots)
@@ -31,6 +34,11 @@ enum { kStEss = 0, kStLk = 1, kStResampled = 2, kStMaxLogw = 3, kStSumL = 4, kSt
 // then mean [D] at kStatsHead, recycled numerator sum_k l_k f~_k [D] at kStatsHead + D
 
 int launch_outer_propose(const OuterArgs& a, void* stream);
+// HMC move of iteration k > 1: momentum draw, first half kick and drift (replaces the
+// proposal launch); then, between the filter passes of consecutive leapfrog points, the
+// two half kicks and the next drift.
+int launch_hmc_start(const OuterArgs& a, void* stream);
+int launch_hmc_leap(const OuterArgs& a, void* stream);
 // Launches the update in kOuterUpdateLaunches kernels: per-sample weights (many blocks),
 // statistics and ancestors (one block), gather and commit of the resampled rows.
 constexpr int kOuterUpdateLaunches = 4;

@@ -56,6 +56,7 @@ struct smc2_handle {
     double *prior_m = nullptr, *prior_s = nullptr;
     double *theta = nullptr, *theta_new = nullptr, *logw = nullptr, *logpi = nullptr, *gradpi = nullptr;
     double *loglik = nullptr, *ll_new = nullptr, *grad_new = nullptr, *tmp = nullptr, *stats = nullptr;
+    double *mom = nullptr, *ke = nullptr;  // HMC: leapfrog momentum [N][D], start kinetic energy [N]
     int* outer_anc = nullptr;
     uint32_t* k_dev = nullptr;
     int* status = nullptr;      // device status word of the handle's kernels

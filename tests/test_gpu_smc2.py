@@ -185,3 +185,39 @@ def test_sampler_survives_filters_with_overflowing_gradients():
             st = h.step()
             assert st["ess"] >= 1.0, st
             assert np.all(np.isfinite(st["mean"])), st
+
+
+def test_smc2_hmc_matches_oracle():
+    """HMC moves with three leapfrog steps (a filter forward + adjoint at every point, the
+    momentum-reversal weight) against the oracle's HMC sampler: the small linear-Gaussian
+    job with filter resampling off, so that every filter decision is fixed and the three
+    filter runs of a move leave no near-tie to follow.  The leapfrog step is 0.1: with the
+    Langevin step (0.245 at T = 60) three steps leave one sample carrying all the weight
+    at every iteration, and the population's path is then chaotic (FP32 and FP64 runs
+    drift apart geometrically over the iterations, although each move agrees)."""
+    from dataclasses import replace
+    w = replace(W.lg1(N=64, M=128, T=60, K=6, proposal="hmc"), hmc_steps=3, gamma=0.1)
+    recs, hints = _run_gpu(w, w.K, ess_frac=0.0)
+    ref, rec_ref = osmc2.run(w.family, 1, 1, None, w.y, w.N, w.M, w.K, w.gamma, "hmc", w.seed,
+                             ess_frac=0.0, hints=hints, band=BAND, flag_band=BAND, band_rel=BAND_REL,
+                             hmc_steps=3)
+    _compare(recs, ref, rec_ref, stable=_stable_lg(1))
+
+
+def test_hmc_with_one_step_equals_langevin():
+    """One leapfrog step is the SMC1 move and its weight the Langevin L-kernel weight: the
+    two proposals give the same population up to FP64 rounding."""
+    from dataclasses import replace
+    from paper_2407_17296_gb300 import binding
+    out = []
+    for prop in ("langevin", "hmc"):
+        w = replace(W.lg1(N=64, M=128, T=60, K=5, proposal=prop), hmc_steps=1)
+        with binding.Handle(binding.config_for(w, ess_frac=0.0)) as h:
+            st = h.run(5)
+            out.append((st, h.samples()))
+    (sa, (tha, lwa)), (sb, (thb, lwb)) = out
+    assert sa["resampled"] == sb["resampled"]
+    np.testing.assert_allclose(thb, tha, rtol=0, atol=1e-9)
+    fin = np.isfinite(lwa)
+    assert np.array_equal(fin, np.isfinite(lwb))
+    np.testing.assert_allclose(lwb[fin], lwa[fin], rtol=0, atol=1e-6)
