@@ -12,9 +12,11 @@ pytestmark = pytest.mark.gpu
 
 
 def _jobs():
+    from dataclasses import replace
     return [W.lg1(T=50, N=64, M=128, K=3), W.lg4(T=40, N=32, M=256, K=3),
             W.sv(T=60, N=48, M=128, K=4), W.lg16(T=20, N=16, M=128, K=2),
-            W.lg4(T=30, N=64, M=100, K=2, proposal="rw")]
+            W.lg4(T=30, N=64, M=100, K=2, proposal="rw"),
+            replace(W.lg1(T=50, N=64, M=128, K=3, proposal="hmc"), hmc_steps=2, gamma=0.1)]
 
 
 def _alone(w):

@@ -221,3 +221,17 @@ def test_hmc_with_one_step_equals_langevin():
     fin = np.isfinite(lwa)
     assert np.array_equal(fin, np.isfinite(lwb))
     np.testing.assert_allclose(lwb[fin], lwa[fin], rtol=0, atol=1e-6)
+
+
+def test_smc2_hmc_lgssm_uniform_prior_matches_oracle():
+    """HMC moves (two leapfrog steps) on Sec. IV-A's model with the optimal proposal and its
+    uniform priors: a trajectory that leaves the box ends with weight zero on both sides."""
+    from dataclasses import replace
+    w = replace(W.lgssm(T=100, N=32, M=128, K=5, proposal="hmc"), hmc_steps=2, gamma=0.05)
+    recs, hints = _run_gpu(w, w.K, ess_frac=0.0)
+    ref, rec_ref = osmc2.run(w.family, 1, 1, None, w.y, w.N, w.M, w.K, w.gamma, "hmc", w.seed,
+                             prior_mean=w.prior_mean, prior_std=w.prior_std, D=3,
+                             prior_kind=osmc2.UNIFORM_PRIOR, ess_frac=0.0,
+                             hints=hints, band=BAND, flag_band=BAND, band_rel=BAND_REL, hmc_steps=2)
+    inside = lambda th: bool(np.all(th >= w.prior_mean) and np.all(th <= w.prior_std))
+    _compare(recs, ref, rec_ref, stable=inside)
