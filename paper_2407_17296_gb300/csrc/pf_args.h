@@ -73,7 +73,7 @@ struct SmemLayout {
             return r;
         };
         const size_t Mp = (size_t)padded_particles(M);
-        xstage = fwd ? take(sizeof(float) * (size_t)M * DX)
+        xstage = fwd ? take(sizeof(float) * (size_t)((M + 7) & ~7) * DX)  // gather slots: M rounded up to 8
                      : take(sizeof(float) * Mp * DX * (R > 0 ? R : 1));
         // fwd: multinomial cumulative weights; bwd: two log-weight buffers
         cs = fwd ? take(sizeof(float) * (size_t)M) : take(sizeof(float) * 2 * Mp);

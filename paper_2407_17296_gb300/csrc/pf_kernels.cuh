@@ -270,20 +270,29 @@ __device__ __forceinline__ void systematic_ancestors(const float (&lw)[P], bool 
     const float scale = __fdividef((float)M, u64_to_float_rz(tot));  // the same value in every thread
     const float c0 = u64_to_float_rz(base) * scale - nu;
     const float sc40 = scale * 0x1p40f;
-    int lo = count_below(c0, M), off = 0;
+    const int lo0 = count_below(c0, M);
+    int lo = lo0, off = 0;
     const int hiP = count_below(u64_to_float_rz(base + s[P - 1]) * scale - nu, M);
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         const int j = j0 + p;
         const int hi = (j == M - 1) ? M : (p == P - 1) ? hiP : min(count_below(fmaf(sf[p], sc40, c0), M), hiP);
         first[p] = lo;
-        if (lead && j < M && hi > lo) {
-            marks[lo] = (uint16_t)(j + 1);
-            for (int w = max((lo + C - 1) / C, 1); w * C < hi; ++w) carry[w] = j + 1;
-        }
+        if (lead && j < M && hi > lo) marks[lo] = (uint16_t)(j + 1);
         off = max(off, hi - lo);
         lo = hi;
     }
+    // warp carries: the parent whose range holds warp w's first child w*C, for the warp
+    // boundaries inside this thread's children lo0 .. lo-1 (the last parent starting at or
+    // before the boundary; padding parents start at M)
+    if (lead)
+        for (int w = max((lo0 + C - 1) / C, 1); w * C < lo; ++w) {
+            int q = 0;
+#pragma unroll
+            for (int p = 1; p < P; ++p)
+                if (first[p] <= w * C) q = p;
+            carry[w] = j0 + q + 1;
+        }
     off = __reduce_max_sync(kFull, off);
     if (lane == 0) atomicMax(maxoff, off);
     __syncthreads();
@@ -420,6 +429,18 @@ __device__ __forceinline__ void read_staged(const float* xstage, int j, int gl, 
 #pragma unroll
         for (int k = 0; k < DL; ++k) x[k] = src[k];
     }
+}
+
+// Forward gather staging: particle j's state sits in slot j XOR (a few higher bits of j),
+// which spreads the stores of a warp (consecutive threads own P consecutive particles) over
+// all shared-memory banks.  4-d states (one float4 per particle, eight per 128 bytes) and
+// 1-d states (one word, 32 per 128 bytes) with one lane per particle; identity otherwise.
+// Slots stay below M rounded up to a multiple of 8.
+template <int P, int DX, int G>
+__device__ __forceinline__ int gather_slot(int j) {
+    if constexpr (G == 1 && DX == 4) return j ^ ((j >> 3) & 7);
+    else if constexpr (G == 1 && DX == 1) return j ^ ((j >> 5) & (P - 1));
+    else return j;
 }
 
 // Normals of the lane's dimensions of its P particles: normal index n = j*DX + k.
@@ -729,7 +750,20 @@ __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, cons
             nu_lane = u01_open(w.x);
         }
         if (resample) {
-            stage_x<P, DX, DL>(xstage, j0, gl, M, x);
+#pragma unroll
+            for (int p = 0; p < P; ++p)
+                if (j0 + p < M) {
+                    float* dst = xstage + gather_slot<P, DX, G>(j0 + p) * DX + gl * DL;
+                    if constexpr (DL % 4 == 0) {
+#pragma unroll
+                        for (int k = 0; k < DL; k += 4)
+                            *reinterpret_cast<float4*>(dst + k) =
+                                make_float4(x[p][k], x[p][k + 1], x[p][k + 2], x[p][k + 3]);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < DL; ++k) dst[k] = x[p][k];
+                    }
+                }
             int anc[P];
             if (a.scheme == 0) {
                 const float nu = __shfl_sync(kFull, nu_lane, (t - 1) & 31);
@@ -743,7 +777,7 @@ __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, cons
             if (a.anc && lead) store_u16<P>(tr.anc_row(t - 1), j0, M, anc);
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                if (j0 + p < M) read_staged<DX, DL>(xstage, anc[p], gl, x[p]);
+                if (j0 + p < M) read_staged<DX, DL>(xstage, gather_slot<P, DX, G>(anc[p]), gl, x[p]);
                 lw[p] = (j0 + p < M) ? 0.f : -INFINITY;
             }
             Lprev = logM;
