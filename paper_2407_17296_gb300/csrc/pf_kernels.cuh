@@ -987,6 +987,10 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
             for (int p = 0; p < P; ++p) lwbar[p] = (j0 + p < M) ? __expf(lwT[j0 + p] - LT) : 0.f;
         }
         if constexpr (R > 0) ring.acquire(g, a.status);
+        // ring cursor: slot of slice g+k, advanced with the sweep (no division per step)
+        const uint32_t slot_elems = (uint32_t)(padded_particles(M) * DX);
+        const uint32_t full_u32 = smem_u32(ring.full);
+        uint32_t sc = g % (uint32_t)(R > 0 ? R : 1);
         uint8_t fb_next = t1 > t0 ? flags[t1 - 1] : (uint8_t)0;
         for (int k = 0; k < Ls - 1; ++k) {
             const int t = t1 - k;
@@ -999,11 +1003,13 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
             const float* sx;
             const float* sp;
             float* st;
+            uint32_t sn = 0;
             if constexpr (R > 0) {
-                ring.acquire(g + k + 1, a.status);
-                st = ring.slot(g + k);
+                sn = (sc + 1u == (uint32_t)R) ? 0u : sc + 1u;  // slot of slice g+k+1
+                ring.acquire_slot(sn, full_u32, a.status);
+                st = ring.slot_at(sc, slot_elems);
                 sx = st;
-                sp = ring.slot(g + k + 1);
+                sp = ring.slot_at(sn, slot_elems);
             } else {
                 st = xstage;
                 sx = Xp(t);
@@ -1062,8 +1068,9 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
             // the next resampling step's buffer was last read before this step's barrier
             if (fl_next) prefetch(t - 1, nres & 1u);
             if constexpr (R > 0) {
-                ring.release(g + k);
+                ring.release_slot(sc, full_u32);
                 if (tid == 0 && k + R < Ls) ring.produce(g + k + R, Xp(t1 - k - R), a.status);
+                sc = sn;
             }
         }
         if (s == 0) {

@@ -54,10 +54,29 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return done != 0;
 }
 
+__device__ __forceinline__ bool mbar_try_wait_u32(uint32_t bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
 // Bounded wait for the phase with the given parity to complete; false on expiry.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit = kWaitLimit) {
     for (uint32_t i = 0; i < limit; ++i)
         if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// The same for a barrier given by its shared-memory address.
+__device__ __forceinline__ bool mbar_wait_u32(uint32_t bar, uint32_t parity, uint32_t limit = kWaitLimit) {
+    for (uint32_t i = 0; i < limit; ++i)
+        if (mbar_try_wait_u32(bar, parity)) return true;
     return false;
 }
 
@@ -90,6 +109,19 @@ struct SliceRing {
     uint32_t filled = 0;       // producer only: slots that have ever been filled
 
     __device__ float* slot(uint32_t g) const { return slots + (size_t)(g % R) * padded_particles(M) * DX; }
+
+    // The same operations by slot index s (= g % R, which the sweep advances step by step),
+    // with the slot size and the barriers' shared-memory address computed once by the caller.
+    __device__ float* slot_at(uint32_t s, uint32_t slot_elems) const { return slots + s * slot_elems; }
+    __device__ void acquire_slot(uint32_t s, uint32_t full_u32, int* status) {
+        if (!mbar_wait_u32(full_u32 + 8u * s, (full_phase >> s) & 1u)) atomicOr(status, kStatusTimeout);
+        full_phase ^= 1u << s;
+    }
+    __device__ void release_slot(uint32_t s, uint32_t full_u32) const {
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0)
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(full_u32 + 8u * (R + s)) : "memory");
+    }
 
     // thread 0 only: copy slice src into the slot of slice g once every warp has released it
     __device__ void produce(uint32_t g, const float* src, int* status) {
