@@ -991,6 +991,14 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
         const uint32_t slot_elems = (uint32_t)(padded_particles(M) * DX);
         const uint32_t full_u32 = smem_u32(ring.full);
         uint32_t sc = g % (uint32_t)(R > 0 ? R : 1);
+        // per-step scalars read through running pointers; launch constants held in registers
+        int* const status = a.status;
+        const int scheme = a.scheme;
+        const bool walk_rows = kGatherWalk<G, DX> && a.offs != nullptr;
+        const float* yrow = a.y + (size_t)(t1 - 1) * DY + (G > 1 ? gl * DL : 0);
+        int jc[P];  // own rows, clamped (padding particles read the last row)
+#pragma unroll
+        for (int p = 0; p < P; ++p) jc[p] = min(j0 + p, M - 1);
         uint8_t fb_next = t1 > t0 ? flags[t1 - 1] : (uint8_t)0;
         for (int k = 0; k < Ls - 1; ++k) {
             const int t = t1 - k;
@@ -1006,7 +1014,7 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
             uint32_t sn = 0;
             if constexpr (R > 0) {
                 sn = (sc + 1u == (uint32_t)R) ? 0u : sc + 1u;  // slot of slice g+k+1
-                ring.acquire_slot(sn, full_u32, a.status);
+                ring.acquire_slot(sn, full_u32, status);
                 st = ring.slot_at(sc, slot_elems);
                 sx = st;
                 sp = ring.slot_at(sn, slot_elems);
@@ -1017,15 +1025,15 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
             }
             float xt[P][DL];
 #pragma unroll
-            for (int p = 0; p < P; ++p) read_staged<DX, DL>(sx, min(j0 + p, M - 1), gl, xt[p]);
-            const float* yt = a.y + (size_t)(t - 1) * DY + (G > 1 ? gl * DL : 0);
+            for (int p = 0; p < P; ++p) read_staged<DX, DL>(sx, jc[p], gl, xt[p]);
+            const float* yt = yrow;
+            yrow -= DY;
             // padding particles have zero cotangents and finite (clamped) states: no guards
 #pragma unroll
             for (int p = 0; p < P; ++p)
                 if constexpr (!Mdl::kFused) Mdl::bwd_obs(prm, xt[p], yt, lwbar[p], xbar[p], thb);
             int ai[P];
             const uint16_t* ancs = ancbuf + (nres & 1u) * (uint32_t)tape_stride(M);
-            const float* lwrow = lwbuf + (nres & 1u) * (uint32_t)padded_particles(M);
             if (fl) {
                 // the prefetched tape row and log-weights have landed (each thread waits for
                 // its own copies, the barrier for everyone's); every warp is also done with
@@ -1033,10 +1041,10 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
                 cp_async_wait_all();
                 __syncthreads();
 #pragma unroll
-                for (int p = 0; p < P; ++p) ai[p] = min((int)ancs[min(j0 + p, M - 1)], M - 1);
+                for (int p = 0; p < P; ++p) ai[p] = min((int)ancs[jc[p]], M - 1);
             } else {
 #pragma unroll
-                for (int p = 0; p < P; ++p) ai[p] = min(j0 + p, M - 1);
+                for (int p = 0; p < P; ++p) ai[p] = jc[p];
             }
             float xp[P][DL];
 #pragma unroll
@@ -1049,9 +1057,9 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
             if (fl) {
                 // adjoint of the gather x'_i = x_{a_i}: sum the cotangents of each parent's
                 // offspring, staged in the rows of x_t (each thread has read its own)
-                if (a.scheme != 0)
+                if (scheme != 0)
                     gather_adjoint_scatter<P, DX, DL, G>(xbar, ai, j0, gl, M, st);
-                else if (kGatherWalk<G, DX> && a.offs && !(fb & 2))
+                else if (walk_rows && !(fb & 2))
                     gather_adjoint_runs<P, DX, DL, G>(xbar, j0, gl, M, offbuf + (nres & 1u) * (uint32_t)tape_stride(M),
                                                       st);
                 else
@@ -1061,6 +1069,7 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
                 fence_proxy_async_shared();
                 // adjoint of the mean reset log w' = LSE(log w) - log M: cotangent becomes w~_{t-1}
                 const float Lp = lstep[t - 1];
+                const float* lwrow = lwbuf + (nres & 1u) * (uint32_t)padded_particles(M);
 #pragma unroll
                 for (int p = 0; p < P; ++p) lwbar[p] = (j0 + p < M) ? __expf(lwrow[j0 + p] - Lp) : 0.f;
                 ++nres;
@@ -1069,7 +1078,7 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
             if (fl_next) prefetch(t - 1, nres & 1u);
             if constexpr (R > 0) {
                 ring.release_slot(sc, full_u32);
-                if (tid == 0 && k + R < Ls) ring.produce(g + k + R, Xp(t1 - k - R), a.status);
+                if (tid == 0 && k + R < Ls) ring.produce(g + k + R, Xp(t1 - k - R), status);
                 sc = sn;
             }
         }
