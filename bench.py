@@ -49,7 +49,7 @@ ALG_OPS_STRICT = {"lg1": 33 + 14, "lg4": 94 + 47, "sv": 36 + 15, "lg16": 333 + 1
 # of 304 filters for the 4-d workload (M = 1024, T = 250), dram__bytes.sum.per_second times
 # the duration of 304 SV filters (M = 2048, T = 500) and of 152 16-d filters (M = 1024,
 # T = 200); a launch of N filters moves N times this.
-TRAFFIC_PER_FILTER = {("lg4", 1024, 250): (1484.644e6 + 1542.551e6) / 304,
+TRAFFIC_PER_FILTER = {("lg4", 1024, 250): (1485.484e6 + 1541.974e6) / 304,
                       ("sv", 2048, 500): (1466.4e6 + 1525.1e6) / 304,
                       ("lg16", 1024, 200): (2269.1e6 + 2196.7e6) / 152}
 
@@ -172,7 +172,7 @@ def cpu_oracle_rate(w, budget_s, procs=None):
     one = time.perf_counter() - t0
     # enough filter runs for the budget, cycling over the iteration's filters when they
     # are fewer (small workloads would otherwise time milliseconds of pool overhead)
-    n = int(max(procs, min(64 * w.N, budget_s * procs / max(one, 1e-6))))
+    n = int(max(procs, min(500000, budget_s * procs / max(one, 1e-6))))
     n = max(procs, (n // procs) * procs)
     jobs = [(w.family, w.dx, w.dy, H, theta[i % w.N], w.y, w.M, w.seed, 2, i % w.N) for i in range(n)]
     ctx = mp.get_context("spawn")
