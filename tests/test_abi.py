@@ -118,3 +118,14 @@ def test_set_launch_validates_without_device(lib):
     with pytest.raises(binding.Smc2Error):
         binding.set_launch(c, [2, 64, 2, 64, 0])    # checkpoint interval outside [1, T]
     binding.set_launch(c, [2, 64, 4, 128, 5])
+
+
+@pytest.mark.parametrize("steps,code", [(0, -1), (65, -1), (1, 0), (3, 0), (64, 0)])
+def test_hmc_steps_are_validated(lib, steps, code):
+    """The HMC proposal takes 1..64 leapfrog steps; other proposals ignore the field."""
+    from paper_2407_17296_gb300 import binding
+    c = _cfg(proposal=binding.HMC, hmc_steps=steps)
+    b = ctypes.c_size_t(0)
+    assert lib.smc2_footprint(ctypes.byref(c), ctypes.byref(b)) == code
+    c = _cfg(proposal=binding.LANGEVIN, hmc_steps=steps)
+    assert lib.smc2_footprint(ctypes.byref(c), ctypes.byref(b)) == 0
