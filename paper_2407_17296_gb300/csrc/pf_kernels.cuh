@@ -357,25 +357,56 @@ __device__ __forceinline__ void multinomial_ancestors(const float (&lw)[P], bool
 
 // Lane gl of a group stores/loads/stages dimensions gl*DL .. gl*DL+DL-1 of its particles;
 // rows are particle-major [M][DX], so a group writes DX contiguous floats per particle.
+// P consecutive floats v[p] at dst[j0 ..) (j0 a multiple of P, dst 16-byte aligned): vector
+// stores when all P entries are in range.
+template <int P>
+__device__ __forceinline__ void store_run(float* __restrict__ dst, int j0, int M, const float (&v)[P]) {
+    if constexpr (P % 4 == 0) {
+        if (j0 + P <= M) {
+#pragma unroll
+            for (int q = 0; q < P; q += 4)
+                *reinterpret_cast<float4*>(dst + j0 + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+            return;
+        }
+    } else if constexpr (P == 2) {
+        if (j0 + P <= M) {
+            *reinterpret_cast<float2*>(dst + j0) = make_float2(v[0], v[1]);
+            return;
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+        if (j0 + p < M) dst[j0 + p] = v[p];
+}
+
+// One particle's lane slice of a state row.
+template <int DX, int DL>
+__device__ __forceinline__ void store_row(float* __restrict__ xdst, int j, int gl, const float (&x)[DL]) {
+    float* dst = xdst + (size_t)j * DX + gl * DL;
+    if constexpr (DL % 4 == 0) {
+#pragma unroll
+        for (int k = 0; k < DL; k += 4)
+            *reinterpret_cast<float4*>(dst + k) = make_float4(x[k], x[k + 1], x[k + 2], x[k + 3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < DL; ++k) dst[k] = x[k];
+    }
+}
+
 template <int P, int DX, int DL>
 __device__ __forceinline__ void store_state(float* __restrict__ xdst, float* __restrict__ lwdst, int j0,
                                             int gl, int M, const float (&x)[P][DL], const float (&lw)[P]) {
+    if constexpr (DX == 1) {  // one word a particle: the thread's P rows are consecutive
+        float v[P];
 #pragma unroll
-    for (int p = 0; p < P; ++p) {
-        const int j = j0 + p;
-        if (j < M) {
-            float* dst = xdst + (size_t)j * DX + gl * DL;
-            if constexpr (DL % 4 == 0) {
+        for (int p = 0; p < P; ++p) v[p] = x[p][0];
+        store_run<P>(xdst, j0, M, v);
+    } else {
 #pragma unroll
-                for (int k = 0; k < DL; k += 4)
-                    *reinterpret_cast<float4*>(dst + k) = make_float4(x[p][k], x[p][k + 1], x[p][k + 2], x[p][k + 3]);
-            } else {
-#pragma unroll
-                for (int k = 0; k < DL; ++k) dst[k] = x[p][k];
-            }
-            if (lwdst && gl == 0) lwdst[j] = lw[p];
-        }
+        for (int p = 0; p < P; ++p)
+            if (j0 + p < M) store_row<DX, DL>(xdst, j0 + p, gl, x[p]);
     }
+    if (lwdst && gl == 0) store_run<P>(lwdst, j0, M, lw);
 }
 
 template <int P, int DX, int DL>
@@ -805,6 +836,12 @@ __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, cons
                 lw[p] += g;  // padding particles stay at -inf
             }
         }
+        // with kc = 1 every state slice is stored: issue the stores before the reduction's
+        // barriers so that they drain while the block synchronises
+        if (store && a.kc == 1) {
+            const float nolw[P] = {};
+            store_state<P, DX, DL>(tr.x_ck(t), nullptr, j0, gl, M, x, nolw);
+        }
         float m, s1, s2;
         block_lse3<P>(lw, lead, red + (t & 1) * 32, red + 64 + (t & 1), m, s1, s2);
         if (!(isfinite(m) && isfinite(s1) && s1 > 0.f)) {
@@ -822,9 +859,9 @@ __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, cons
         }
         if (store) {
             // with kc = 1 the adjoint reads log w only at steps followed by resampling and at T
-            if (a.kc == 1)
-                store_state<P, DX, DL>(tr.x_ck(t), (resample || t == T) ? tr.lw_ck(t) : nullptr, j0, gl, M, x, lw);
-            else if (t % a.kc == 0 && t < T)
+            if (a.kc == 1) {
+                if ((resample || t == T) && lead) store_run<P>(tr.lw_ck(t), j0, M, lw);
+            } else if (t % a.kc == 0 && t < T)
                 store_state<P, DX, DL>(tr.x_ck(t / a.kc), tr.lw_ck(t / a.kc), j0, gl, M, x, lw);
         }
     }
