@@ -54,9 +54,9 @@ SMC2_HD inline int tape_stride(int M) { return (M + 7) & ~7; }
 constexpr size_t kSmemLimit = 227 * 1024 - 1024;
 
 // The adjoint of a gather with sorted ancestors walks each parent's run of offspring (whose
-// bounds the forward pass records) for the four-dimensional model with one lane per
-// particle; other model shapes use a segmented sum.
-SMC2_HD constexpr bool gather_walk(int G, int DX) { return G == 1 && DX == 4; }
+// bounds the forward pass records) for 1-d and 4-d states with one lane per particle; the
+// 16-d model (several lanes per particle) uses a segmented sum.
+SMC2_HD constexpr bool gather_walk(int G, int DX) { return G == 1 && (DX == 4 || DX == 1); }
 
 // Dynamic shared-memory plan (mirrored on the host to size the launch).
 struct SmemLayout {

@@ -496,11 +496,11 @@ __device__ __forceinline__ float group_sum(float v) {
     return v;
 }
 
-// Sorted-ancestor gather adjoint used per model shape, as measured: the run walk for the
-// four-dimensional model (short runs; one barrier), the balanced segmented sum elsewhere
-// (the 16-dimensional model resamples at nearly every step with very uneven offspring
-// counts, where a long run serialises the walk; for one-dimensional states the walk's
-// data-dependent loop costs more in the steps that do not resample than it saves).
+// Sorted-ancestor gather adjoint used per model shape, as measured: the run walk over the
+// offspring ranges the forward pass records for one lane per particle (1-d and 4-d
+// states: short runs, one barrier), the balanced segmented sum for the 16-dimensional
+// model (it resamples at nearly every step with very uneven offspring counts, where a
+// long run serialises the walk).
 template <int G, int DX>
 constexpr bool kGatherWalk = gather_walk(G, DX);
 
