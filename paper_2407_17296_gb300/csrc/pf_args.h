@@ -94,7 +94,7 @@ struct SmemLayout {
 // Slots of the adjoint's shared-memory ring of trajectory slices: the model shape's
 // preferred count when the plan fits kSmemLimit, else its fallback (0: no ring, slices
 // read from memory).
-SMC2_HD constexpr int ring_preferred(int DX) { return DX >= 16 ? 2 : (DX == 4 ? 5 : 8); }
+SMC2_HD constexpr int ring_preferred(int DX) { return DX >= 16 ? 3 : (DX == 4 ? 5 : 8); }
 SMC2_HD constexpr int ring_fallback(int DX) { return DX >= 16 ? 0 : (DX >= 4 ? 2 : 4); }
 SMC2_HD inline int ring_slots(int M, int DX, int D, int G) {
     return SmemLayout(M, DX, D, false, G, ring_preferred(DX)).total <= kSmemLimit ? ring_preferred(DX)
