@@ -46,12 +46,12 @@ ALG_OPS_STRICT = {"lg1": 33 + 14, "lg4": 94 + 47, "sv": 36 + 15, "lg16": 333 + 1
 
 # DRAM bytes per filter of the forward + adjoint pair, measured with ncu on small launches
 # of each workload's shape (every step stored): dram__bytes_read.sum + dram__bytes_write.sum
-# of 304 filters for the 4-d workload (M = 1024, T = 250), dram__bytes.sum.per_second times
-# the duration of 304 SV filters (M = 2048, T = 500) and of 152 16-d filters (M = 1024,
-# T = 200); a launch of N filters moves N times this.
-TRAFFIC_PER_FILTER = {("lg4", 1024, 250): (1485.484e6 + 1541.974e6) / 304,
-                      ("sv", 2048, 500): (1466.4e6 + 1525.1e6) / 304,
-                      ("lg16", 1024, 200): (2269.1e6 + 2196.7e6) / 152}
+# of 304 filters for the 4-d workload (M = 1024, T = 250) and for SV (M = 2048, T = 500),
+# of 152 filters for the 16-d workload (M = 1024, T = 200); a launch of N filters moves N
+# times this.
+TRAFFIC_PER_FILTER = {("lg4", 1024, 250): (1482.490e6 + 1542.340e6) / 304,
+                      ("sv", 2048, 500): (1553.137e6 + 1620.408e6) / 304,
+                      ("lg16", 1024, 200): (2330.697e6 + 2196.141e6) / 152}
 
 
 def _args():
