@@ -462,6 +462,31 @@ __device__ __forceinline__ void read_staged(const float* xstage, int j, int gl, 
     }
 }
 
+// The thread's own P consecutive 1-d states (rows j0 .. j0+P-1 of a slice, j0 a multiple of
+// P): one vector load when all are in range (conflict-free across the warp), else rows
+// clamped to M - 1 one by one.
+template <int P, int DL>
+__device__ __forceinline__ void load_own_1d(const float* slice, int j0, int M, float (&x)[P][DL]) {
+    if constexpr (P % 4 == 0) {
+        if (j0 + P <= M) {
+#pragma unroll
+            for (int q = 0; q < P; q += 4) {
+                const float4 v = *reinterpret_cast<const float4*>(slice + j0 + q);
+                x[q][0] = v.x; x[q + 1][0] = v.y; x[q + 2][0] = v.z; x[q + 3][0] = v.w;
+            }
+            return;
+        }
+    } else if constexpr (P == 2) {
+        if (j0 + P <= M) {
+            const float2 v = *reinterpret_cast<const float2*>(slice + j0);
+            x[0][0] = v.x; x[1][0] = v.y;
+            return;
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p) x[p][0] = slice[min(j0 + p, M - 1)];
+}
+
 // Forward gather staging: particle j's state sits in slot j XOR (a few higher bits of j),
 // which spreads the stores of a warp (consecutive threads own P consecutive particles) over
 // all shared-memory banks.  4-d states (one float4 per particle, eight per 128 bytes) and
@@ -1061,8 +1086,12 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
                 sp = Xp(t - 1);
             }
             float xt[P][DL];
+            if constexpr (DX == 1 && G == 1) {
+                load_own_1d<P, DL>(sx, j0, M, xt);
+            } else {
 #pragma unroll
-            for (int p = 0; p < P; ++p) read_staged<DX, DL>(sx, jc[p], gl, xt[p]);
+                for (int p = 0; p < P; ++p) read_staged<DX, DL>(sx, jc[p], gl, xt[p]);
+            }
             const float* yt = yrow;
             yrow -= DY;
             // padding particles have zero cotangents and finite (clamped) states: no guards
@@ -1084,8 +1113,17 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
                 for (int p = 0; p < P; ++p) ai[p] = jc[p];
             }
             float xp[P][DL];
+            if constexpr (DX == 1 && G == 1) {
+                if (fl) {
 #pragma unroll
-            for (int p = 0; p < P; ++p) read_staged<DX, DL>(sp, ai[p], gl, xp[p]);
+                    for (int p = 0; p < P; ++p) read_staged<DX, DL>(sp, ai[p], gl, xp[p]);
+                } else {
+                    load_own_1d<P, DL>(sp, j0, M, xp);
+                }
+            } else {
+#pragma unroll
+                for (int p = 0; p < P; ++p) read_staged<DX, DL>(sp, ai[p], gl, xp[p]);
+            }
 #pragma unroll
             for (int p = 0; p < P; ++p) {
                 if constexpr (Mdl::kFused) Mdl::bwd_step(prm, xt[p], xp[p], yt, lwbar[p], xbar[p], thb);
