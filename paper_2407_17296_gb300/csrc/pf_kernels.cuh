@@ -379,6 +379,29 @@ __device__ __forceinline__ void store_run(float* __restrict__ dst, int j0, int M
         if (j0 + p < M) dst[j0 + p] = v[p];
 }
 
+// The loading counterpart of store_run (entries at or beyond M read as zero).
+template <int P>
+__device__ __forceinline__ void load_run(const float* __restrict__ src, int j0, int M, float (&v)[P]) {
+    if constexpr (P % 4 == 0) {
+        if (j0 + P <= M) {
+#pragma unroll
+            for (int q = 0; q < P; q += 4) {
+                const float4 u = *reinterpret_cast<const float4*>(src + j0 + q);
+                v[q] = u.x; v[q + 1] = u.y; v[q + 2] = u.z; v[q + 3] = u.w;
+            }
+            return;
+        }
+    } else if constexpr (P == 2) {
+        if (j0 + P <= M) {
+            const float2 u = *reinterpret_cast<const float2*>(src + j0);
+            v[0] = u.x; v[1] = u.y;
+            return;
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p) v[p] = (j0 + p < M) ? src[j0 + p] : 0.f;
+}
+
 // One particle's lane slice of a state row.
 template <int DX, int DL>
 __device__ __forceinline__ void store_row(float* __restrict__ xdst, int j, int gl, const float (&x)[DL]) {
@@ -539,6 +562,12 @@ constexpr bool kGatherWalk = gather_walk(G, DX);
 template <int P, int DX, int DL, int G>
 __device__ __forceinline__ void gather_adjoint_runs(float (&xbar)[P][DL], int j0, int gl, int M,
                                                     const uint16_t* first, float* stage) {
+    if constexpr (DX == 1 && G == 1) {  // the thread's P rows are consecutive words
+        float v[P];
+#pragma unroll
+        for (int p = 0; p < P; ++p) v[p] = xbar[p][0];
+        store_run<P>(stage, j0, M, v);
+    } else
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         const int i = j0 + p;
@@ -1107,7 +1136,15 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
                 cp_async_wait_all();
                 __syncthreads();
 #pragma unroll
-                for (int p = 0; p < P; ++p) ai[p] = min((int)ancs[jc[p]], M - 1);
+                for (int p = 0; p < P; ++p) ai[p] = jc[p];
+                if constexpr (G == 1) {
+                    load_u16<P>(ancs, j0, M, ai);  // padding particles read ancestor 0
+#pragma unroll
+                    for (int p = 0; p < P; ++p) ai[p] = min(ai[p], M - 1);
+                } else {
+#pragma unroll
+                    for (int p = 0; p < P; ++p) ai[p] = min((int)ancs[jc[p]], M - 1);
+                }
             } else {
 #pragma unroll
                 for (int p = 0; p < P; ++p) ai[p] = jc[p];
@@ -1146,7 +1183,12 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
                 const float Lp = lstep[t - 1];
                 const float* lwrow = lwbuf + (nres & 1u) * (uint32_t)padded_particles(M);
 #pragma unroll
-                for (int p = 0; p < P; ++p) lwbar[p] = (j0 + p < M) ? __expf(lwrow[j0 + p] - Lp) : 0.f;
+                {
+                    float lv[P];
+                    load_run<P>(lwrow, j0, M, lv);
+#pragma unroll
+                    for (int p = 0; p < P; ++p) lwbar[p] = (j0 + p < M) ? __expf(lv[p] - Lp) : 0.f;
+                }
                 ++nres;
             }
             // the next resampling step's buffer was last read before this step's barrier
