@@ -49,9 +49,9 @@ ALG_OPS_STRICT = {"lg1": 33 + 14, "lg4": 94 + 47, "sv": 36 + 15, "lg16": 333 + 1
 # of 304 filters for the 4-d workload (M = 1024, T = 250) and for SV (M = 2048, T = 500),
 # of 152 filters for the 16-d workload (M = 1024, T = 200); a launch of N filters moves N
 # times this.
-TRAFFIC_PER_FILTER = {("lg4", 1024, 250): (1482.490e6 + 1542.340e6) / 304,
-                      ("sv", 2048, 500): (1553.137e6 + 1620.408e6) / 304,
-                      ("lg16", 1024, 200): (2330.697e6 + 2196.141e6) / 152}
+TRAFFIC_PER_FILTER = {("lg4", 1024, 250): (1482.174e6 + 1542.289e6) / 304,
+                      ("sv", 2048, 500): (1552.733e6 + 1624.368e6) / 304,
+                      ("lg16", 1024, 200): (2319.920e6 + 2196.099e6) / 152}
 
 
 def _args():
