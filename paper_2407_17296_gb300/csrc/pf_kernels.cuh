@@ -522,6 +522,24 @@ __device__ __forceinline__ int gather_slot(int j) {
     else return j;
 }
 
+// The same for states spread over G lanes (d_x a multiple of 4, each lane DL = DX/G
+// dimensions in float4 pieces): float4 index of piece k of lane gl of particle j.  The
+// eight lanes of a quarter warp hold pieces of particles P apart; XOR-ing the index with
+// a function of j / P (an involution within each 128-byte row, identity for P = 1)
+// spreads their accesses over all eight 16-byte bank groups.
+template <int P, int DX, int DL, int G>
+__device__ __forceinline__ int gather_f4(int j, int gl, int k) {
+    const int idx = j * (DX / 4) + gl * (DL / 4) + k;
+    if constexpr (P >= 2 && G == 2 && DX / 4 == 4) {
+        const int m = (j / P) & 3;
+        return idx ^ ((m & 1) | ((m & 2) << 1));
+    } else if constexpr (P >= 2 && G == 4 && DX / 4 == 4) {
+        return idx ^ (((j / P) & 1) << 2);
+    } else {
+        return idx;
+    }
+}
+
 // Normals of the lane's dimensions of its P particles: normal index n = j*DX + k.
 template <int P, int DX, int DL>
 __device__ __forceinline__ void draw_normals(const PhiloxKey& key, uint32_t t, uint32_t stream, int j0, int gl,
@@ -838,15 +856,23 @@ __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, cons
 #pragma unroll
             for (int p = 0; p < P; ++p)
                 if (j0 + p < M) {
-                    float* dst = xstage + gather_slot<P, DX, G>(j0 + p) * DX + gl * DL;
-                    if constexpr (DL % 4 == 0) {
+                    if constexpr (G > 1 && DL % 4 == 0) {
+                        float4* st4 = reinterpret_cast<float4*>(xstage);
 #pragma unroll
                         for (int k = 0; k < DL; k += 4)
-                            *reinterpret_cast<float4*>(dst + k) =
+                            st4[gather_f4<P, DX, DL, G>(j0 + p, gl, k / 4)] =
                                 make_float4(x[p][k], x[p][k + 1], x[p][k + 2], x[p][k + 3]);
                     } else {
+                        float* dst = xstage + gather_slot<P, DX, G>(j0 + p) * DX + gl * DL;
+                        if constexpr (DL % 4 == 0) {
 #pragma unroll
-                        for (int k = 0; k < DL; ++k) dst[k] = x[p][k];
+                            for (int k = 0; k < DL; k += 4)
+                                *reinterpret_cast<float4*>(dst + k) =
+                                    make_float4(x[p][k], x[p][k + 1], x[p][k + 2], x[p][k + 3]);
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < DL; ++k) dst[k] = x[p][k];
+                        }
                     }
                 }
             int anc[P];
@@ -862,7 +888,18 @@ __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, cons
             if (a.anc && lead) store_u16<P>(tr.anc_row(t - 1), j0, M, anc);
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                if (j0 + p < M) read_staged<DX, DL>(xstage, gather_slot<P, DX, G>(anc[p]), gl, x[p]);
+                if (j0 + p < M) {
+                    if constexpr (G > 1 && DL % 4 == 0) {
+                        const float4* st4 = reinterpret_cast<const float4*>(xstage);
+#pragma unroll
+                        for (int k = 0; k < DL; k += 4) {
+                            const float4 v = st4[gather_f4<P, DX, DL, G>(anc[p], gl, k / 4)];
+                            x[p][k] = v.x; x[p][k + 1] = v.y; x[p][k + 2] = v.z; x[p][k + 3] = v.w;
+                        }
+                    } else {
+                        read_staged<DX, DL>(xstage, gather_slot<P, DX, G>(anc[p]), gl, x[p]);
+                    }
+                }
                 lw[p] = (j0 + p < M) ? 0.f : -INFINITY;
             }
             Lprev = logM;
