@@ -632,11 +632,20 @@ __device__ __forceinline__ void gather_adjoint_segmented(float (&xbar)[P][DL], c
                                                       int M, const uint16_t* ancs, float* xbstage,
                                                       float* segw) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    // lane-split states stage their float4 pieces at bank-spread positions (the staged
+    // sums are read back only through the same map)
+    constexpr bool kF4 = (G > 1 && DL == 4);
+    float4* st4 = reinterpret_cast<float4*>(xbstage);
 #pragma unroll
     for (int p = 0; p < P; ++p)
-        if (j0 + p < M)
+        if (j0 + p < M) {
+            if constexpr (kF4) {
+                st4[gather_f4<P, DX, DL, G>(j0 + p, gl, 0)] = make_float4(0.f, 0.f, 0.f, 0.f);
+            } else {
 #pragma unroll
-            for (int k = 0; k < DL; ++k) xbstage[(j0 + p) * DX + gl * DL + k] = 0.f;
+                for (int k = 0; k < DL; ++k) xbstage[(j0 + p) * DX + gl * DL + k] = 0.f;
+            }
+        }
     // thread aggregate: sum since the last run head in the thread's range (F: a head was seen)
     float acc[DL];
     bool F = false;
@@ -735,17 +744,28 @@ __device__ __forceinline__ void gather_adjoint_segmented(float (&xbar)[P][DL], c
                 for (int k = 0; k < DL; ++k) carry[k] = 0.f;
 #pragma unroll
             for (int k = 0; k < DL; ++k) carry[k] += xbar[p][k];
-            if (i == M - 1 || (int)ancs[i + 1] != ai[p])
+            if (i == M - 1 || (int)ancs[i + 1] != ai[p]) {
+                if constexpr (kF4) {
+                    st4[gather_f4<P, DX, DL, G>(ai[p], gl, 0)] = make_float4(carry[0], carry[1], carry[2], carry[3]);
+                } else {
 #pragma unroll
-                for (int k = 0; k < DL; ++k) xbstage[ai[p] * DX + gl * DL + k] = carry[k];
+                    for (int k = 0; k < DL; ++k) xbstage[ai[p] * DX + gl * DL + k] = carry[k];
+                }
+            }
         }
     }
     __syncthreads();
 #pragma unroll
     for (int p = 0; p < P; ++p)
-        if (j0 + p < M)
+        if (j0 + p < M) {
+            if constexpr (kF4) {
+                const float4 v = st4[gather_f4<P, DX, DL, G>(j0 + p, gl, 0)];
+                xbar[p][0] = v.x; xbar[p][1] = v.y; xbar[p][2] = v.z; xbar[p][3] = v.w;
+            } else {
 #pragma unroll
-            for (int k = 0; k < DL; ++k) xbar[p][k] = xbstage[(j0 + p) * DX + gl * DL + k];
+                for (int k = 0; k < DL; ++k) xbar[p][k] = xbstage[(j0 + p) * DX + gl * DL + k];
+            }
+        }
 }
 
 // Adjoint of the gather for unsorted ancestors (multinomial resampling): each thread clears
@@ -984,7 +1004,6 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
     constexpr int DX = Mdl::DX, DY = Mdl::DY, D = Mdl::D, G = Mdl::G, DL = Mdl::DL, DTH = Mdl::DTH;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     const int gl = (G > 1) ? (tid & (G - 1)) : 0;
-    const bool lead = gl == 0;
     const int M = a.M, T = a.T, kc = a.kc;
     float* xstage = reinterpret_cast<float*>(smem + L.xstage);
     float* segw = reinterpret_cast<float*>(smem + L.starts);
@@ -1219,7 +1238,6 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
                 // adjoint of the mean reset log w' = LSE(log w) - log M: cotangent becomes w~_{t-1}
                 const float Lp = lstep[t - 1];
                 const float* lwrow = lwbuf + (nres & 1u) * (uint32_t)padded_particles(M);
-#pragma unroll
                 {
                     float lv[P];
                     load_run<P>(lwrow, j0, M, lv);
