@@ -51,7 +51,7 @@ ALG_OPS_STRICT = {"lg1": 33 + 14, "lg4": 94 + 47, "sv": 36 + 15, "lg16": 333 + 1
 # times this.
 TRAFFIC_PER_FILTER = {("lg4", 1024, 250): (1482.174e6 + 1542.289e6) / 304,
                       ("sv", 2048, 500): (1552.733e6 + 1624.368e6) / 304,
-                      ("lg16", 1024, 200): (2319.920e6 + 2196.099e6) / 152}
+                      ("lg16", 1024, 200): (2322.950e6 + 2196.211e6) / 152}
 
 
 def _args():
