@@ -157,8 +157,10 @@ int smc2_run(smc2_handle* h, int K, smc2_stats* out);
  * the replayed step graph) and record CUDA events on the handle's stream around the
  * forward and adjoint passes; smc2_get_step_timing returns the mean device time of the
  * passes over the iterations run since timing was switched on or last queried (up to the
- * last 512): ms[0] forward, ms[1] adjoint (waits for them to finish).  SMC2_E_INVAL if no
- * timed iteration ran since then. */
+ * last 512): ms[0] forward, ms[1] adjoint (waits for them to finish).  A handle whose N
+ * filters exceed what the GPU holds at once runs them as two halves on two streams, the
+ * forward pass of one overlapping the adjoint of the other: then ms[0] is the time of both
+ * passes together and ms[1] is -1.  SMC2_E_INVAL if no timed iteration ran since then. */
 int smc2_set_step_timing(smc2_handle* h, int on);
 int smc2_get_step_timing(smc2_handle* h, float* ms);
 

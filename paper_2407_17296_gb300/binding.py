@@ -283,7 +283,8 @@ class Handle:
 
     def step_timing(self):
         """Mean (forward ms, adjoint ms) of the filter passes of the iterations run since the
-        last query (device events)."""
+        last query (device events); (both passes, -1) when the handle overlaps the passes of
+        two halves of its filters."""
         ms = (ctypes.c_float * 2)()
         check(self.lib.smc2_get_step_timing(self.h, ms), "smc2_get_step_timing")
         return float(ms[0]), float(ms[1])

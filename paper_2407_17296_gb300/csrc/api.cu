@@ -259,6 +259,28 @@ extern "C" int smc2_footprint(const smc2_config* cfg, size_t* bytes) {
 
 // ------------------------------------------------------------------ handle lifecycle
 
+// Filters per chunk of a filter launch (0: no chunks).  A pass over more filters than the
+// GPU holds at once runs in waves of blocks, and its last wave is partial.  Split in two
+// halves on two streams, the forward pass of one half overlaps the adjoint of the other, so
+// the SMs a partial wave leaves idle take blocks of the other stream (measured: +3.5% for
+// 1024 filters of 1024 4-d particles, +2.5% for 2048 of 1024 16-d particles, neutral for
+// 4096 of 2048 1-d particles; more chunks, whose passes queue behind each other on each
+// stream, measured slower).
+static int choose_chunk(const smc2_handle* h) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    PFArgs q{};
+    q.M = h->cfg.M;
+    const int nb = h->fwd(q, nullptr, 0);
+    if (nb <= 0) return 0;
+    const int N = h->cfg.N;
+    return N > nb * sms ? (N + 1) / 2 : 0;
+}
+
 static void free_handle_memory(smc2_handle* h) {
     void* ptrs[] = {h->y, h->H, h->prior_m, h->prior_s, h->theta, h->theta_new, h->logw, h->logpi,
                     h->gradpi, h->loglik, h->ll_new, h->grad_new, h->tmp, h->mom, h->ke, h->stats, h->outer_anc,
@@ -270,6 +292,9 @@ static void free_handle_memory(smc2_handle* h) {
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
     for (cudaEvent_t e : h->tev)
         if (e) cudaEventDestroy(e);
+    if (h->fork_ev) cudaEventDestroy(h->fork_ev);
+    if (h->join_ev) cudaEventDestroy(h->join_ev);
+    if (h->side) cudaStreamDestroy(h->side);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
@@ -309,6 +334,13 @@ extern "C" int smc2_create(const smc2_config* cfg, smc2_handle** out) {
         if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess)
             return cleanup(SMC2_E_CUDA, "cudaStreamCreate failed");
         h->own_stream = true;
+    }
+    h->chunk = choose_chunk(h);
+    if (h->chunk > 0) {
+        if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming) != cudaSuccess)
+            return cleanup(SMC2_E_CUDA, "cudaStreamCreate / cudaEventCreate failed");
     }
     const size_t N = cfg->N, T = cfg->T;
     struct Alloc { void** p; size_t bytes; };
@@ -442,22 +474,76 @@ PFArgs smc2::make_pf_args(smc2_handle* h, const double* theta, int n, uint32_t i
     return a;
 }
 
+// The launch arguments of filters f0 .. f0 + n - 1 of a (every per-filter array offset).
+static PFArgs chunk_args(const smc2_handle* h, const PFArgs& a, int f0, int n) {
+    PFArgs b = a;
+    const size_t f = (size_t)f0, D = (size_t)a.D, T = (size_t)a.T;
+    const size_t Mp = (size_t)padded_particles(a.M), Ma = (size_t)tape_stride(a.M), DX = (size_t)h->cfg.d_x;
+    b.n = n;
+    b.row0 = a.row0 + (uint32_t)f0;
+    b.theta = a.theta + f * D;
+    b.loglik = a.loglik + f;
+    if (a.grad) b.grad = a.grad + f * D;
+    if (a.xck) b.xck = a.xck + f * a.n_slots * Mp * DX;
+    if (a.lwck) b.lwck = a.lwck + f * a.n_slots * Mp;
+    if (a.xseg) b.xseg = a.xseg + f * a.kc * Mp * DX;
+    if (a.lwseg) b.lwseg = a.lwseg + f * a.kc * Mp;
+    if (a.anc) b.anc = a.anc + f * T * Ma;
+    if (a.offs) b.offs = a.offs + f * T * Ma;
+    b.flag = a.flag + f * T;
+    b.mstep = a.mstep + f * (T + 1);
+    b.lstep = a.lstep + f * (T + 1);
+    return b;
+}
+
+// Kernel launches of the filter passes over n filters.
+static int filter_launches(const smc2_handle* h, int n, bool grad) {
+    if (!grad) return 1;
+    return (h->chunk > 0 && n > h->chunk) ? 2 * ((n + h->chunk - 1) / h->chunk) : 2;
+}
+
 int smc2::launch_filters(smc2_handle* h, const PFArgs& a, bool timed) {
     // timed: bracket the passes with the events of the step's timing slot (eager launches only)
     cudaEvent_t* ev = timed ? &h->tev[3 * (h->tev_next % kTimingSlots)] : nullptr;
     if (timed) cudaEventRecord(ev[0], h->stream);
-    int rc = h->fwd(a, h->stream, a.n);
+    int rc = 0;
     const char* pass = "forward";
-    if (timed && !rc) cudaEventRecord(ev[1], h->stream);
-    if (!rc && a.want_grad) {
-        rc = h->bwd(a, h->stream, a.n);
-        pass = "adjoint";
+    if (a.want_grad && h->chunk > 0 && a.n > h->chunk) {
+        // chunks of filters, each forward then adjoint, alternating between two streams: the
+        // passes of neighbouring chunks overlap, so a pass's last partial wave of blocks
+        // shares the GPU with the other stream's work instead of leaving SMs idle
+        cudaEventRecord(h->fork_ev, h->stream);
+        cudaStreamWaitEvent(h->side, h->fork_ev, 0);
+        for (int c = 0, f0 = 0; f0 < a.n && !rc; ++c, f0 += h->chunk) {
+            const PFArgs b = chunk_args(h, a, f0, std::min(h->chunk, a.n - f0));
+            cudaStream_t s = (c & 1) ? h->side : h->stream;
+            pass = "forward";
+            rc = h->fwd(b, s, b.n);
+            if (!rc) {
+                pass = "adjoint";
+                rc = h->bwd(b, s, b.n);
+            }
+        }
+        cudaEventRecord(h->join_ev, h->side);
+        cudaStreamWaitEvent(h->stream, h->join_ev, 0);
+        // the passes overlap: the timing slot holds both together
+        if (timed && !rc) {
+            cudaEventRecord(ev[1], h->stream);
+            cudaEventRecord(ev[2], h->stream);
+        }
+    } else {
+        rc = h->fwd(a, h->stream, a.n);
+        if (timed && !rc) cudaEventRecord(ev[1], h->stream);
+        if (!rc && a.want_grad) {
+            rc = h->bwd(a, h->stream, a.n);
+            pass = "adjoint";
+        }
+        if (timed && !rc) cudaEventRecord(ev[2], h->stream);
     }
-    if (timed && !rc) cudaEventRecord(ev[2], h->stream);
     if (rc)
         return fail(SMC2_E_CUDA, std::string(pass) + " filter launch failed: " +
                                      (rc > 0 ? cudaGetErrorString((cudaError_t)rc) : "block too large"));
-    count_launches(a.want_grad ? 2 : 1);
+    count_launches(filter_launches(h, a.n, a.want_grad));
     return SMC2_OK;
 }
 
@@ -541,7 +627,7 @@ OuterArgs smc2::make_outer_args(smc2_handle* h) {
 // leapfrog point (one point for RW and Langevin), the leapfrog kicks between them, update.
 static int launches_per_step(const smc2_handle* h) {
     const int L = h->cfg.proposal == SMC2_HMC ? h->cfg.hmc_steps : 1;
-    return 1 + 2 * L + (L - 1) + kOuterUpdateLaunches;
+    return 1 + L * filter_launches(h, h->cfg.N, true) + (L - 1) + kOuterUpdateLaunches;
 }
 
 int smc2::enqueue_step(smc2_handle* h) {
@@ -628,7 +714,8 @@ extern "C" int smc2_get_step_timing(smc2_handle* h, float* ms) {
         b += c;
     }
     ms[0] = (float)(f / h->tev_pending);
-    ms[1] = (float)(b / h->tev_pending);
+    // an iteration's filters run in two overlapping halves: only the pair's time exists
+    ms[1] = (h->chunk > 0 && h->cfg.N > h->chunk) ? -1.f : (float)(b / h->tev_pending);
     h->tev_pending = 0;
     return SMC2_OK;
 }

@@ -107,7 +107,9 @@ SMC2_HD inline int pf_threads(int M, int P, int G = 1) {
     return ((lanes + 31) / 32) * 32;
 }
 
-// Host-side launcher of one compiled kernel variant (forward or adjoint pass).
+// Host-side launcher of one compiled kernel variant (forward or adjoint pass).  With grid 0
+// it launches nothing and returns how many blocks of the variant fit on one SM for a.M
+// particles (0 if none, -1 if the query failed).
 typedef int (*pf_kernel_fn)(const PFArgs& a, void* stream, int grid);
 
 // A launch choice: particles per thread and register cap of each pass, checkpoint interval.

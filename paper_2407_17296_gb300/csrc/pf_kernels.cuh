@@ -1338,18 +1338,35 @@ __global__ void __maxnreg__(REGS) pf_backward_kernel(PFArgs a) {
     }
 }
 
+// Blocks of `kernel` resident on one SM (the grid = 0 query of the launchers).
+template <class K>
+int blocks_per_sm(K kernel, int threads, size_t smem) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    return nb;
+}
+
 // Launch one pass for a.n filters (grid = a.n CTAs, or fewer for a grid-stride launch).
-// Returns 0, -1 when the block would exceed kMaxThreads, or the cudaError_t of the launch.
+// Returns 0, -1 when the block would exceed kMaxThreads, or the cudaError_t of the launch;
+// grid = 0 is the occupancy query described at pf_kernel_fn.
 template <class Mdl, int P, int REGS>
 int launch_forward(const PFArgs& a, void* stream, int grid) {
     const int threads = pf_threads(a.M, P, Mdl::G);
     const size_t smem = SmemLayout(a.M, Mdl::DX, Mdl::D, true, Mdl::G).total;
-    if (threads > kMaxThreads) return -1;
+    if (threads > kMaxThreads) return grid ? -1 : 0;
     if (smem + sizeof(typename Mdl::Params) > 48 * 1024) {
         const cudaError_t e = cudaFuncSetAttribute(pf_forward_kernel<Mdl, P, REGS>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return (int)e;
+        if (e != cudaSuccess) {
+            if (grid) return (int)e;
+            cudaGetLastError();
+            return -1;
+        }
     }
+    if (grid == 0) return blocks_per_sm(pf_forward_kernel<Mdl, P, REGS>, threads, smem);
     pf_forward_kernel<Mdl, P, REGS><<<grid, threads, smem, static_cast<cudaStream_t>(stream)>>>(a);
     return (int)cudaGetLastError();
 }
@@ -1359,12 +1376,17 @@ int launch_backward(const PFArgs& a, void* stream, int grid) {
     const int threads = pf_threads(a.M, P, Mdl::G);
     const int R = ring_slots(a.M, Mdl::DX, Mdl::D, Mdl::G);
     const size_t smem = SmemLayout(a.M, Mdl::DX, Mdl::D, false, Mdl::G, R).total;
-    if (threads > kMaxThreads) return -1;
+    if (threads > kMaxThreads) return grid ? -1 : 0;
     if (smem + sizeof(typename Mdl::Params) > 48 * 1024) {
         const cudaError_t e = cudaFuncSetAttribute(pf_backward_kernel<Mdl, P, REGS>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return (int)e;
+        if (e != cudaSuccess) {
+            if (grid) return (int)e;
+            cudaGetLastError();
+            return -1;
+        }
     }
+    if (grid == 0) return blocks_per_sm(pf_backward_kernel<Mdl, P, REGS>, threads, smem);
     pf_backward_kernel<Mdl, P, REGS><<<grid, threads, smem, static_cast<cudaStream_t>(stream)>>>(a);
     return (int)cudaGetLastError();
 }

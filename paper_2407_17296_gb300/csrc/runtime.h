@@ -51,6 +51,11 @@ struct smc2_handle {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     smc2::pf_kernel_fn fwd = nullptr, bwd = nullptr;
+    // filters per chunk of a launch (0: one forward launch, then one adjoint launch); chunks
+    // alternate between the handle's stream and `side`, forked and joined with the two events
+    int chunk = 0;
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     // device state
     float *y = nullptr, *H = nullptr;
     double *prior_m = nullptr, *prior_s = nullptr;

@@ -114,6 +114,24 @@ def test_deterministic_and_row_offset():
     np.testing.assert_array_equal(c[1], a[1][3:])
 
 
+def test_two_stream_halves_match_single_launches():
+    """A launch over more filters than the GPU holds at once (1024 filters of 1024 4-d
+    particles) runs as two halves on two streams; every filter's log-likelihood, gradient,
+    ancestors and resampling flags equal those of launches small enough to run whole."""
+    from paper_2407_17296_gb300 import binding
+    w = W.lg4(T=40, N=1024, M=1024)
+    theta = W.thetas_near(w, w.N, 0.05, seed=31)
+    n0 = binding.kernel_launches()
+    a = gpu_pf(w, theta, iteration=4)
+    assert binding.kernel_launches() - n0 == 4  # two halves x (forward, adjoint)
+    for r0 in range(0, w.N, 256):
+        n0 = binding.kernel_launches()
+        c = gpu_pf(w, theta[r0:r0 + 256], iteration=4, row0=r0)
+        assert binding.kernel_launches() - n0 == 2
+        for x, y in zip(c, a):
+            np.testing.assert_array_equal(x, y[r0:r0 + 256])
+
+
 def test_single_particle_closed_form():
     """M = 1: resampling is the identity and log p-hat is the path density."""
     w = W.lg4(T=50, N=2, M=1)
