@@ -120,8 +120,8 @@ int smc2_create(const smc2_config* cfg, smc2_handle** out);
  * adjoint) to grad_dev[i*D..] (FP64, device).  A filter whose weights all vanish
  * or overflow reports log p-hat = -inf and a zero gradient.
  * Caller owns all buffers; n <= N of the handle.  Asynchronous on the handle's
- * stream.  When the handle's N filters exceed what the GPU holds at once and n is above
- * half of N, the rows run as two halves, the second on a stream of the handle's own that
+ * stream.  When a gradient is requested, the handle's N filters exceed what the GPU holds
+ * at once and n is above half of N, the rows run as two halves, the second on a stream of the handle's own that
  * is forked from and joined back into the handle's stream (work queued on that stream
  * afterwards still waits for every row).  Errors: SMC2_E_INVAL, SMC2_E_CUDA.
  */
