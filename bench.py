@@ -186,6 +186,12 @@ def cpu_oracle_rate(w, budget_s, procs=None):
     return rate, procs, info
 
 
+def workload_config(w):
+    """The workload part of the JSON line's config, the same for both arms."""
+    return {"workload": f"{w.name}: LG-diag d_x={w.dx} d_y={w.dy}" if w.family == 0 else f"{w.name}: SV",
+            "N": w.N, "M": w.M, "T": w.T, "D": w.D, "proposal": w.proposal, "gamma": w.gamma}
+
+
 # ------------------------------------------------------------------ GPU arm
 
 def run_gpu(a, rank, world, local):
@@ -318,8 +324,7 @@ def run_gpu(a, rank, world, local):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic (seeded simulation of the model; no dataset)",
-        "config": {"workload": f"{w.name}: LG-diag d_x={w.dx} d_y={w.dy}" if w.family == 0 else f"{w.name}: SV",
-                   "N": w.N, "M": w.M, "T": w.T, "D": w.D, "proposal": w.proposal, "gamma": w.gamma,
+        "config": {**workload_config(w),
                    "launch": {"forward_ppt": launch[0], "forward_regs": launch[1], "adjoint_ppt": launch[2],
                               "adjoint_regs": launch[3], "ckpt_every": launch[4]},
                    "step": ("one SMC2 iteration: propose, N filters fwd+adjoint, L-kernel weights, resample"
@@ -380,13 +385,16 @@ def run_reference(a, rank, world):
     ms_step = 1e3 * w.N * w.M * w.T / value
     return {
         "impl": "reference",
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": a.steps,
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded simulation of the model; no dataset)",
-        "config": {"workload": w.name, "N": w.N, "M": w.M, "T": w.T, "D": w.D},
+        "config": {**workload_config(w),
+                   "step": "a bounded sample of the workload's filters (forward + forward-mode gradient) "
+                           "on the host cores; value scaled to the whole workload by particle-steps",
+                   "runs_on": "host CPU cores (rank 0 only); no GPU work"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"per step {infos[0]['filters']} of {w.N} filters (forward + gradient), "
-                                   f"{wall:.1f} s total"},
+                         "sample": f"per step {infos[0]['filters']} filter runs cycling over the {w.N} filters "
+                                   f"of one iteration (forward + gradient), {wall:.1f} s total"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
