@@ -186,6 +186,20 @@ def cpu_oracle_rate(w, budget_s, procs=None):
     return rate, procs, info
 
 
+def make_workload(a):
+    """The workload of the command line (both arms)."""
+    from paper_2407_17296_gb300 import workloads
+    w = workloads.ALL[a.workload]()
+    if a.N:
+        w = w.with_sizes(N=a.N)
+    if a.hmc_steps:
+        # leapfrog step gamma / sqrt(L): Langevin-sized steps over several points leave the
+        # outer weights degenerate on these workloads
+        from dataclasses import replace
+        w = replace(w, proposal="hmc", hmc_steps=a.hmc_steps, gamma=w.gamma / math.sqrt(a.hmc_steps))
+    return w
+
+
 def workload_config(w):
     """The workload part of the JSON line's config, the same for both arms."""
     return {"workload": f"{w.name}: LG-diag d_x={w.dx} d_y={w.dy}" if w.family == 0 else f"{w.name}: SV",
@@ -204,14 +218,7 @@ def run_gpu(a, rank, world, local):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    w = workloads.ALL[a.workload]()
-    if a.N:
-        w = w.with_sizes(N=a.N)
-    if a.hmc_steps:
-        # leapfrog step gamma / sqrt(L): Langevin-sized steps over several points leave the
-        # outer weights degenerate on these workloads
-        from dataclasses import replace
-        w = replace(w, proposal="hmc", hmc_steps=a.hmc_steps, gamma=w.gamma / math.sqrt(a.hmc_steps))
+    w = make_workload(a)
     # weak scaling: every rank runs its own independent job (own seed), no data-path collective
     w.seed = w.seed + 1000 * rank
     binding.load()
@@ -369,8 +376,7 @@ def run_reference(a, rank, world):
     """The CPU oracle as the reference arm: each step a bounded sample of the workload."""
     if rank != 0:
         return None
-    from paper_2407_17296_gb300 import workloads
-    w = workloads.ALL[a.workload]()
+    w = make_workload(a)
     per = max(2.0, a.cpu_seconds / max(1, a.steps + a.warmup))
     for _ in range(a.warmup):
         cpu_oracle_rate(w, per / 4, a.cpu_procs or None)
@@ -382,7 +388,8 @@ def run_reference(a, rank, world):
         infos.append(info)
     wall = time.perf_counter() - t0
     value = statistics.mean(rates)
-    ms_step = 1e3 * w.N * w.M * w.T / value
+    # a step is the GPU arm's step: N filters at each of the move's leapfrog points
+    ms_step = 1e3 * w.N * w.M * w.T * (w.hmc_steps if w.proposal == "hmc" else 1) / value
     return {
         "impl": "reference",
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
