@@ -512,8 +512,9 @@ int smc2::launch_filters(smc2_handle* h, const PFArgs& a, bool timed) {
         // chunks of filters, each forward then adjoint, alternating between two streams: the
         // passes of neighbouring chunks overlap, so a pass's last partial wave of blocks
         // shares the GPU with the other stream's work instead of leaving SMs idle
-        cudaEventRecord(h->fork_ev, h->stream);
-        cudaStreamWaitEvent(h->side, h->fork_ev, 0);
+        if (cudaEventRecord(h->fork_ev, h->stream) != cudaSuccess ||
+            cudaStreamWaitEvent(h->side, h->fork_ev, 0) != cudaSuccess)
+            return fail(SMC2_E_CUDA, "filter launch: fork to the second stream failed");
         for (int c = 0, f0 = 0; f0 < a.n && !rc; ++c, f0 += h->chunk) {
             const PFArgs b = chunk_args(h, a, f0, std::min(h->chunk, a.n - f0));
             cudaStream_t s = (c & 1) ? h->side : h->stream;
@@ -524,8 +525,10 @@ int smc2::launch_filters(smc2_handle* h, const PFArgs& a, bool timed) {
                 rc = h->bwd(b, s, b.n);
             }
         }
-        cudaEventRecord(h->join_ev, h->side);
-        cudaStreamWaitEvent(h->stream, h->join_ev, 0);
+        // the join is issued whatever happened above, so no work is left unordered
+        const bool joined = cudaEventRecord(h->join_ev, h->side) == cudaSuccess &&
+                            cudaStreamWaitEvent(h->stream, h->join_ev, 0) == cudaSuccess;
+        if (!rc && !joined) return fail(SMC2_E_CUDA, "filter launch: join of the second stream failed");
         // the passes overlap: the timing slot holds both together
         if (timed && !rc) {
             cudaEventRecord(ev[1], h->stream);
