@@ -156,9 +156,10 @@ def _oracle_filter(args):
     return r["loglik"]
 
 
-def cpu_oracle_rate(w, budget_s, procs=None):
+def cpu_oracle_rate(w, budget_s, procs=None, pool=None):
     """Time the oracle's filter forward + forward-mode gradient on a bounded sample of the
-    workload's filters with a spawn pool over all host cores; returns (rate, info)."""
+    workload's filters: procs = 1 in this process, else a spawn pool over procs host cores (or
+    the given pool of that size); returns (rate, threads, info)."""
     import multiprocessing as mp
 
     import numpy as np
@@ -175,15 +176,39 @@ def cpu_oracle_rate(w, budget_s, procs=None):
     n = int(max(procs, min(500000, budget_s * procs / max(one, 1e-6))))
     n = max(procs, (n // procs) * procs)
     jobs = [(w.family, w.dx, w.dy, H, theta[i % w.N], w.y, w.M, w.seed, 2, i % w.N) for i in range(n)]
-    ctx = mp.get_context("spawn")
-    with ctx.Pool(procs) as pool:
-        pool.map(_oracle_filter, jobs[:procs])  # start-up outside the timing
+    if procs == 1:
         t0 = time.perf_counter()
-        pool.map(_oracle_filter, jobs, chunksize=1)
+        for j in jobs:
+            _oracle_filter(j)
         dt = time.perf_counter() - t0
+    else:
+        own = pool is None
+        if own:
+            pool = mp.get_context("spawn").Pool(procs)
+        try:
+            pool.map(_oracle_filter, jobs[:procs])  # start-up outside the timing
+            t0 = time.perf_counter()
+            pool.map(_oracle_filter, jobs, chunksize=1)
+            dt = time.perf_counter() - t0
+        finally:
+            if own:
+                pool.close()
+                pool.join()
     rate = n * w.M * w.T / dt
     info = {"filters": n, "of": w.N, "seconds": dt, "single_filter_s": one}
     return rate, procs, info
+
+
+def cpu_baseline_line(w, budget_s, procs=None):
+    """The oracle on the host: one thread, then all cores (a third and two thirds of the budget)."""
+    r1, _, i1 = cpu_oracle_rate(w, budget_s / 3.0, 1)
+    rn, cores, info = cpu_oracle_rate(w, 2.0 * budget_s / 3.0, procs)
+    return {"value": rn, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{info['filters']} filter runs over the {info['of']} filters of one iteration "
+                      f"(forward + forward-mode gradient, FP64), spawn pool of {cores} processes, "
+                      f"{info['seconds']:.1f} s; one thread: {i1['filters']} filter runs, {i1['seconds']:.1f} s",
+            "threads_all": {"value": rn, "threads": cores},
+            "threads_1": {"value": r1, "threads": 1}}
 
 
 def make_workload(a):
@@ -248,8 +273,8 @@ def run_gpu(a, rank, world, local):
     barrier()
     torch.cuda.synchronize()
     launches0 = binding.kernel_launches()
-    # steps launch their kernels one by one with events around the filter passes (the
-    # replayed step graph holds the same four kernels; its launch saving is ~10 us a step)
+    # steps replay the captured step graph with event-record nodes around the filter passes
+    # (the production launch path, timed on the device)
     h.set_step_timing(True)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
@@ -361,11 +386,7 @@ def run_gpu(a, rank, world, local):
         "gpu_launches": int(launches),
     }
     if not a.no_cpu_baseline:
-        rate, cores, info = cpu_oracle_rate(w, a.cpu_seconds, a.cpu_procs or None)
-        out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                               "sample": f"{info['filters']} filter runs over the {info['of']} filters of one "
-                                         f"iteration (forward + forward-mode gradient, FP64), spawn pool, "
-                                         f"{info['seconds']:.1f} s"}
+        out["cpu_baseline"] = cpu_baseline_line(w, a.cpu_seconds, a.cpu_procs or None)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -373,35 +394,48 @@ def run_gpu(a, rank, world, local):
 
 
 def run_reference(a, rank, world):
-    """The CPU oracle as the reference arm: each step a bounded sample of the workload."""
+    """The CPU oracle as the reference arm: each step a bounded sample of the workload's filters
+    on all host cores (one spawn pool for the whole run)."""
     if rank != 0:
         return None
+    import multiprocessing as mp
     w = make_workload(a)
-    per = max(2.0, a.cpu_seconds / max(1, a.steps + a.warmup))
-    for _ in range(a.warmup):
-        cpu_oracle_rate(w, per / 4, a.cpu_procs or None)
-    rates, infos = [], []
-    t0 = time.perf_counter()
-    for _ in range(a.steps):
-        r, cores, info = cpu_oracle_rate(w, per, a.cpu_procs or None)
-        rates.append(r)
-        infos.append(info)
-    wall = time.perf_counter() - t0
+    procs = a.cpu_procs or os.cpu_count() or 1
+    per = max(1.0, a.cpu_seconds / max(1, a.steps + a.warmup))
+    rates, infos, walls = [], [], []
+    with mp.get_context("spawn").Pool(procs) as pool:
+        for _ in range(a.warmup):
+            cpu_oracle_rate(w, per / 4, procs, pool)
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            s0 = time.perf_counter()
+            r, cores, info = cpu_oracle_rate(w, per, procs, pool)
+            walls.append(time.perf_counter() - s0)
+            rates.append(r)
+            infos.append(info)
+        wall = time.perf_counter() - t0
     value = statistics.mean(rates)
-    # a step is the GPU arm's step: N filters at each of the move's leapfrog points
-    ms_step = 1e3 * w.N * w.M * w.T * (w.hmc_steps if w.proposal == "hmc" else 1) / value
+    # what one whole iteration of the GPU arm's step (N filters at each of the move's leapfrog
+    # points) would take at this rate: extrapolated, not timed
+    ms_iter = 1e3 * w.N * w.M * w.T * (w.hmc_steps if w.proposal == "hmc" else 1) / value
+    r1, _, i1 = cpu_oracle_rate(w, max(2.0, per), 1)
     return {
         "impl": "reference",
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
-        "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "warmup": a.warmup, "ms_per_step": 1e3 * wall / a.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded simulation of the model; no dataset)",
         "config": {**workload_config(w),
                    "step": "a bounded sample of the workload's filters (forward + forward-mode gradient) "
-                           "on the host cores; value scaled to the whole workload by particle-steps",
+                           "on the host cores; ms_per_step is its measured wall time, value the rate "
+                           "in particle-steps/s",
+                   "extrapolated_ms_per_iteration": ms_iter,
                    "runs_on": "host CPU cores (rank 0 only); no GPU work"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"per step {infos[0]['filters']} filter runs cycling over the {w.N} filters "
-                                   f"of one iteration (forward + gradient), {wall:.1f} s total"},
+                                   f"of one iteration (forward + gradient), {wall:.1f} s over {a.steps} steps; "
+                                   f"one thread: {i1['filters']} filter runs, {i1['seconds']:.1f} s",
+                         "threads_all": {"value": value, "threads": cores},
+                         "threads_1": {"value": r1, "threads": 1}},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 

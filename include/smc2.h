@@ -100,6 +100,17 @@ typedef struct smc2_stats {
     double max_logw;          /* largest outer log-weight (diagnostic) */
     double* mean;             /* caller host storage [D] or NULL: f~_k = sum_i w~_i theta_i (Eq. realised_estimates) */
     double* recycled_mean;    /* caller host storage [D] or NULL: sum_k c_k f~_k over iterations so far (Sec. III-C) */
+    /* Near-ties of iteration k (App. B: the ancestor index counts the cumulative weights below a
+     * threshold, so a weight within rounding of a threshold decides it only up to rounding).
+     * pf_near_ties: over the N filters, systematic resampling counts the cumulative weights
+     * c_j (j < M-1) within 1e-6 of a threshold (i + nu)/M, multinomial the thresholds nu_i
+     * within 1e-6 of the cumulative weights next to their index; evaluated in FP32.
+     * pf_resample_steps: filter steps that resampled (the decisions those ties come from).
+     * outer_near_ties: outer resampling thresholds within 1e-6 of a cumulative weight (FP64),
+     * 0 when the outer sampler did not resample. */
+    int64_t pf_near_ties;
+    int64_t pf_resample_steps;
+    int64_t outer_near_ties;
 } smc2_stats;
 
 /*
@@ -156,9 +167,11 @@ int smc2_step(smc2_handle* h, smc2_stats* out);
  * one, synchronising once.  Equivalent to K calls of smc2_step.  Errors as smc2_step. */
 int smc2_run(smc2_handle* h, int K, smc2_stats* out);
 
-/* Filter-pass timing.  With timing on, iterations launch their kernels one by one (not as
- * the replayed step graph) and record CUDA events on the handle's stream around the
- * forward and adjoint passes; smc2_get_step_timing returns the mean device time of the
+/* Filter-pass timing.  With timing on, iterations record CUDA events on the handle's stream
+ * around the forward and adjoint passes (iterations after the first replay the captured step
+ * graph with three event-record nodes, re-targeted to a ring of events before each launch, so
+ * the timed iterations run as production ones do); smc2_get_step_timing returns the mean
+ * device time of the
  * passes over the iterations run since timing was switched on or last queried (up to the
  * last 512): ms[0] forward, ms[1] adjoint (waits for them to finish).  A handle whose N
  * filters exceed what the GPU holds at once runs them as two halves on two streams, the
@@ -221,7 +234,8 @@ int smc2_get_trace(smc2_handle* h, uint16_t* pf_anc, uint8_t* pf_flag, int32_t* 
  * No handle and no allocation: cfg describes the model and sizes (model_family, d_x,
  * d_y, H (host, copied), y (DEVICE pointer, y_on_device must be 1), T, M, D,
  * pf_resample, ess_frac, seed, ckpt_every, particles_per_thread, stream); cfg->N is
- * ignored and n rows of theta_dev ([n][D] FP64, device) are filtered with Philox rows
+ * ignored (the size checks use n) and n rows of theta_dev ([n][D] FP64, device, n <= 4096)
+ * are filtered with Philox rows
  * row0..row0+n-1 and iteration iter.  Outputs as for pf_loglik_grad (loglik_dev [n],
  * grad_dev [n][D] or NULL), caller-owned device buffers.  Work is enqueued on
  * cfg->stream (NULL: the legacy default stream).
@@ -233,13 +247,29 @@ int smc2_get_trace(smc2_handle* h, uint16_t* pf_anc, uint8_t* pf_flag, int32_t* 
  * SMC2_E_INVAL and a message giving the bytes it needs.  The first call on each device
  * looks up the array's device address (cudaGetSymbolAddress); make that first call
  * before any stream capture.  All calls share the one array and it keeps the last
- * call's contents (nothing in it needs to start at zero): calls whose work overlaps on
+ * call's contents (each call clears the status word it uses; nothing else needs to start at
+ * zero): calls whose work overlaps on
  * the GPU race with each other, so serialise them (one stream, or events).
  * This entry point calls no cudaMalloc, cudaFree or other allocating routine.
- * Errors: SMC2_E_INVAL, SMC2_E_CUDA.
+ * Errors: SMC2_E_INVAL, SMC2_E_CUDA.  The call is asynchronous: a bounded wait that expires
+ * inside its kernels is reported by pf_static_get_status afterwards (SMC2_E_TIMEOUT).
  */
 int pf_loglik_grad_static(const smc2_config* cfg, const double* theta_dev, int n, uint32_t iter,
                           uint32_t row0, double* loglik_dev, double* grad_dev);
+
+/* Status word of the last pf_loglik_grad_static call on the current device (it lives in the
+ * same static array; each call clears it before its kernels run): 0, or kernel error bits
+ * (1: a bounded wait inside a filter kernel expired, so that call's outputs are invalid and
+ * the call should be treated as failed with SMC2_E_TIMEOUT).  Copies the word with
+ * cudaMemcpyAsync on `stream` (the stream the call used; NULL: the legacy default stream) and
+ * synchronises that stream; clear != 0 resets a nonzero word.  Allocates nothing.
+ * Errors: SMC2_E_INVAL (status NULL), SMC2_E_CUDA. */
+int pf_static_get_status(void* stream, int* status, int clear);
+
+/* The cudaStream_t (as void*) on which the handle enqueues its work: cfg->stream, or the
+ * handle's private stream.  Callers that mix the handle's work with work on other streams
+ * (e.g. a framework's current stream) order the two with events on this stream. */
+int smc2_get_stream(const smc2_handle* h, void** stream);
 
 /* Read the handle's device status word (synchronises its stream): 0, or kernel error bits
  * (1: a bounded wait inside a filter kernel expired; that launch's results are invalid).
@@ -254,6 +284,18 @@ int smc2_get_status(smc2_handle* h, int* status, int clear);
  * counterpart in the paper.  Errors: SMC2_E_INVAL (polls < 1, NULL), SMC2_E_NOMEM,
  * SMC2_E_CUDA. */
 int smc2_selftest_bounded_wait(int polls, int* timed_out);
+
+/* The common random numbers of the filter kernels, for verification against an independent
+ * implementation of the same generator (Philox4x32-10, Salmon et al., SC'11; Sec. I and
+ * Sec. II-A use one fixed stream of numbers per sample and iteration).  For i = 0..n-1 (device
+ * buffers): key_dev[i] = (seed_lo, seed_hi, iter, row) gives the kernels' key
+ * (seed_lo ^ iter, seed_hi ^ row); ctr_dev[i] = the 4 counter words (the kernels use
+ * (t, call, stream, 0)).  Writes words_dev[i][4] (the block's 4 output words), u_dev[i][4]
+ * (the map to (0,1]: ((w >> 8) + 1) 2^-24) and z_dev[i][4] (Box-Muller normals of the word
+ * pairs (0,1) and (2,3)); any output may be NULL.  Runs on `stream` (NULL: the legacy default
+ * stream) and synchronises it.  No counterpart in the paper.  Errors: SMC2_E_INVAL, SMC2_E_CUDA. */
+int smc2_selftest_crn(const uint32_t* ctr_dev, const uint32_t* key_dev, int n, uint32_t* words_dev, float* u_dev,
+                      float* z_dev, void* stream);
 
 /* Replace the observations (T x d_y FP32, host) of an existing handle; the copy is
  * stream-ordered on the handle's stream. */

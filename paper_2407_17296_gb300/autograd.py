@@ -6,6 +6,12 @@ forward  = one fused launch of the filter forward pass and its reverse-time
 backward = grad_out[:, None] * gradient (no further device work).
 The gradient is the one of App. A/B (common random numbers and ancestors held
 fixed), so it is exact for the estimator, as the paper's autograd gradient is.
+
+Stream order: the handle enqueues on its own stream.  forward makes that stream
+wait for torch's current stream (so theta is ready), makes the current stream
+wait for the handle's work (so the outputs are ready for the ops that follow),
+and marks the tensors the kernels touch as used on the handle's stream (so the
+caching allocator does not hand their memory out while the kernels run).
 """
 import torch
 
@@ -22,7 +28,18 @@ class CRNPFLogLik(torch.autograd.Function):
         ll = torch.empty(n, dtype=torch.float64, device=th.device)
         grad = torch.empty_like(th) if theta.requires_grad else None
         with torch.cuda.device(th.device):
-            handle.pf_loglik_grad(th, iteration, ll, grad)
+            cur = torch.cuda.current_stream(th.device)
+            hs_ptr = handle.stream_ptr()
+            if hs_ptr == cur.cuda_stream:
+                handle.pf_loglik_grad(th, iteration, ll, grad)
+            else:
+                hs = torch.cuda.ExternalStream(hs_ptr, device=th.device)
+                hs.wait_stream(cur)  # theta (and its contiguous copy) written first
+                handle.pf_loglik_grad(th, iteration, ll, grad)
+                cur.wait_stream(hs)  # later ops on the current stream see ll and grad
+                for t in (th, ll, grad):
+                    if t is not None:
+                        t.record_stream(hs)
         ctx.save_for_backward(grad if grad is not None else th.new_zeros(0))
         return ll
 

@@ -27,7 +27,7 @@ EXPORTS = ("smc2_config_init", "smc2_create", "pf_loglik_grad", "pf_loglik_grad_
            "smc2_get_trace", "smc2_set_observations", "smc2_footprint", "smc2_destroy",
            "smc2_autotune", "smc2_get_launch", "smc2_set_launch", "smc2_get_status", "smc2_selftest_bounded_wait", "smc2_kernel_launches", "smc2_last_error", "smc2_server_create",
            "smc2_submit", "smc2_poll", "smc2_cancel", "smc2_server_destroy",
-           "pf_loglik_grad_static")
+           "pf_loglik_grad_static", "pf_static_get_status", "smc2_get_stream", "smc2_selftest_crn")
 
 
 class Config(ctypes.Structure):
@@ -68,7 +68,17 @@ class Stats(ctypes.Structure):
         ("max_logw", ctypes.c_double),
         ("mean", ctypes.c_void_p),
         ("recycled_mean", ctypes.c_void_p),
+        ("pf_near_ties", ctypes.c_int64),
+        ("pf_resample_steps", ctypes.c_int64),
+        ("outer_near_ties", ctypes.c_int64),
     ]
+
+
+def _stats_dict(st, mean, rec):
+    return {"k": st.k, "resampled": bool(st.resampled), "ess": st.ess, "l_k": st.l_k,
+            "max_logw": st.max_logw, "mean": mean, "recycled_mean": rec,
+            "pf_near_ties": int(st.pf_near_ties), "pf_resample_steps": int(st.pf_resample_steps),
+            "outer_near_ties": int(st.outer_near_ties)}
 
 
 class Result(ctypes.Structure):
@@ -132,6 +142,9 @@ def load(path: str = LIB_PATH):
         "smc2_server_destroy": (ctypes.c_int, [vp]),
         "pf_loglik_grad_static": (ctypes.c_int, [ctypes.POINTER(Config), dp, ctypes.c_int, u32, u32,
                                                  dp, dp]),
+        "pf_static_get_status": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
+        "smc2_get_stream": (ctypes.c_int, [vp, ctypes.POINTER(vp)]),
+        "smc2_selftest_crn": (ctypes.c_int, [vp, vp, ctypes.c_int, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -262,8 +275,7 @@ class Handle:
             st.mean = mean.ctypes.data
             st.recycled_mean = rec.ctypes.data
         check(self.lib.smc2_step(self.h, ctypes.byref(st)), "smc2_step")
-        return {"k": st.k, "resampled": bool(st.resampled), "ess": st.ess, "l_k": st.l_k,
-                "max_logw": st.max_logw, "mean": mean, "recycled_mean": rec}
+        return _stats_dict(st, mean, rec)
 
     def run(self, K, want_means=True):
         """K iterations back to back; statistics of the last one."""
@@ -275,8 +287,7 @@ class Handle:
             st.mean = mean.ctypes.data
             st.recycled_mean = rec.ctypes.data
         check(self.lib.smc2_run(self.h, int(K), ctypes.byref(st)), "smc2_run")
-        return {"k": st.k, "resampled": bool(st.resampled), "ess": st.ess, "l_k": st.l_k,
-                "max_logw": st.max_logw, "mean": mean, "recycled_mean": rec}
+        return _stats_dict(st, mean, rec)
 
     def set_step_timing(self, on=True):
         check(self.lib.smc2_set_step_timing(self.h, 1 if on else 0), "smc2_set_step_timing")
@@ -306,8 +317,7 @@ class Handle:
             st.recycled_mean = rec.ctypes.data
         check(self.lib.smc2_step_update(self.h, _ptr(loglik_all), _ptr(grad_all), ctypes.byref(st)),
               "smc2_step_update")
-        return {"k": st.k, "resampled": bool(st.resampled), "ess": st.ess, "l_k": st.l_k,
-                "max_logw": st.max_logw, "mean": mean, "recycled_mean": rec}
+        return _stats_dict(st, mean, rec)
 
     def samples(self):
         import numpy as np
@@ -332,6 +342,12 @@ class Handle:
         check(self.lib.smc2_get_trace(self.h, _ptr(anc), _ptr(flag), _ptr(oanc), ctypes.byref(ores)),
               "smc2_get_trace")
         return anc, flag, oanc, bool(ores.value)
+
+    def stream_ptr(self):
+        """The cudaStream_t (an int) on which the handle enqueues its work."""
+        p = ctypes.c_void_p()
+        check(self.lib.smc2_get_stream(self.h, ctypes.byref(p)), "smc2_get_stream")
+        return int(p.value or 0)
 
     def status(self, clear=False):
         """Device status word of the handle's kernels (0 = fine)."""
@@ -424,6 +440,39 @@ def selftest_bounded_wait(polls=1000) -> bool:
     out = ctypes.c_int(0)
     check(load().smc2_selftest_bounded_wait(int(polls), ctypes.byref(out)), "smc2_selftest_bounded_wait")
     return bool(out.value)
+
+
+def selftest_crn(ctr, key, want=("words", "u", "z")):
+    """The filter kernels' Philox4x32-10 words, (0,1] uniforms and Box-Muller normals for the
+    counters ctr [n][4] and keys key [n][4] = (seed_lo, seed_hi, iter, row) (uint32 numpy
+    arrays, copied to the device); returns numpy arrays [n][4]."""
+    import numpy as np
+    import torch
+    c = torch.as_tensor(np.ascontiguousarray(ctr, dtype=np.uint32).view(np.int32), device="cuda")
+    k = torch.as_tensor(np.ascontiguousarray(key, dtype=np.uint32).view(np.int32), device="cuda")
+    n = int(c.shape[0])
+    words = torch.zeros((n, 4), dtype=torch.int32, device="cuda") if "words" in want else None
+    u = torch.zeros((n, 4), dtype=torch.float32, device="cuda") if "u" in want else None
+    z = torch.zeros((n, 4), dtype=torch.float32, device="cuda") if "z" in want else None
+    stream = torch.cuda.current_stream().cuda_stream
+    check(load().smc2_selftest_crn(_ptr(c), _ptr(k), n, _ptr(words), _ptr(u), _ptr(z),
+                                   ctypes.c_void_p(stream)), "smc2_selftest_crn")
+    out = {}
+    if words is not None:
+        out["words"] = words.cpu().numpy().view(np.uint32)
+    if u is not None:
+        out["u"] = u.cpu().numpy()
+    if z is not None:
+        out["z"] = z.cpu().numpy()
+    return out
+
+
+def static_status(stream=None, clear=False) -> int:
+    """Status word of the last pf_loglik_grad_static call on the current device (0 = fine)."""
+    st = ctypes.c_int(0)
+    check(load().pf_static_get_status(None if stream is None else ctypes.c_void_p(int(stream)),
+                                      ctypes.byref(st), int(bool(clear))), "pf_static_get_status")
+    return st.value
 
 
 def footprint(cfg: Config) -> int:

@@ -17,6 +17,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/smc2.h"
 #include "outer.cuh"
@@ -284,12 +285,15 @@ static int choose_chunk(const smc2_handle* h) {
 static void free_handle_memory(smc2_handle* h) {
     void* ptrs[] = {h->y, h->H, h->prior_m, h->prior_s, h->theta, h->theta_new, h->logw, h->logpi,
                     h->gradpi, h->loglik, h->ll_new, h->grad_new, h->tmp, h->mom, h->ke, h->stats, h->outer_anc,
-                    h->k_dev, h->status, h->xck, h->lwck, h->xseg, h->lwseg, h->anc, h->offs, h->flag, h->mstep, h->lstep};
+                    h->k_dev, h->status, h->ties, h->xck, h->lwck, h->xseg, h->lwseg, h->anc, h->offs, h->flag, h->mstep, h->lstep};
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, h->stream);
     delete[] h->h_stats;
     delete[] h->h_status;
+    delete[] h->h_ties;
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    if (h->graph_timed) cudaGraphExecDestroy(h->graph_timed);
+    if (h->graph_timed_tmpl) cudaGraphDestroy(h->graph_timed_tmpl);
     for (cudaEvent_t e : h->tev)
         if (e) cudaEventDestroy(e);
     if (h->fork_ev) cudaEventDestroy(h->fork_ev);
@@ -364,6 +368,7 @@ extern "C" int smc2_create(const smc2_config* cfg, smc2_handle** out) {
         {(void**)&h->outer_anc, sizeof(int) * N},
         {(void**)&h->k_dev, sizeof(uint32_t)},
         {(void**)&h->status, sizeof(int)},
+        {(void**)&h->ties, 2 * sizeof(unsigned long long)},
         {(void**)&h->xck, s.xck},
         {(void**)&h->lwck, s.lwck},
         {(void**)&h->xseg, s.xseg},
@@ -387,7 +392,8 @@ extern "C" int smc2_create(const smc2_config* cfg, smc2_handle** out) {
     }
     h->h_stats = new (std::nothrow) double[kStatsHead + 2 * D];
     h->h_status = new (std::nothrow) int[1];
-    if (!h->h_stats || !h->h_status) return cleanup(SMC2_E_NOMEM, "host allocation failed");
+    h->h_ties = new (std::nothrow) unsigned long long[2];
+    if (!h->h_stats || !h->h_status || !h->h_ties) return cleanup(SMC2_E_NOMEM, "host allocation failed");
     // inputs
     const cudaMemcpyKind ykind = cfg->y_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     bool ok = cudaMemcpyAsync(h->y, cfg->y, sizeof(float) * T * cfg->d_y, ykind, h->stream) == cudaSuccess;
@@ -410,6 +416,7 @@ extern "C" int smc2_create(const smc2_config* cfg, smc2_handle** out) {
     }
     ok = ok && cudaMemsetAsync(h->k_dev, 0, sizeof(uint32_t), h->stream) == cudaSuccess;
     ok = ok && cudaMemsetAsync(h->status, 0, sizeof(int), h->stream) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(h->ties, 0, 2 * sizeof(unsigned long long), h->stream) == cudaSuccess;
     ok = ok && cudaMemsetAsync(h->stats, 0, sizeof(double) * (kStatsHead + 2 * D), h->stream) == cudaSuccess;
     ok = ok && cudaMemsetAsync(h->gradpi, 0, sizeof(double) * N * D, h->stream) == cudaSuccess;
     ok = ok && cudaMemsetAsync(h->flag, 0, s.flag, h->stream) == cudaSuccess;
@@ -471,6 +478,7 @@ PFArgs smc2::make_pf_args(smc2_handle* h, const double* theta, int n, uint32_t i
     a.loglik = loglik;
     a.grad = grad;
     a.status = h->status;
+    a.ties = h->ties;
     return a;
 }
 
@@ -502,10 +510,17 @@ static int filter_launches(const smc2_handle* h, int n, bool grad) {
     return (h->chunk > 0 && n > h->chunk) ? 2 * ((n + h->chunk - 1) / h->chunk) : 2;
 }
 
+// Record a timing event on the handle's stream; inside a capture it becomes an event-record
+// node of the graph (the timed step graph re-targets those nodes before every replay).
+static void record_timing_event(const smc2_handle* h, cudaEvent_t ev) {
+    if (h->capturing) cudaEventRecordWithFlags(ev, h->stream, cudaEventRecordExternal);
+    else cudaEventRecord(ev, h->stream);
+}
+
 int smc2::launch_filters(smc2_handle* h, const PFArgs& a, bool timed) {
-    // timed: bracket the passes with the events of the step's timing slot (eager launches only)
-    cudaEvent_t* ev = timed ? &h->tev[3 * (h->tev_next % kTimingSlots)] : nullptr;
-    if (timed) cudaEventRecord(ev[0], h->stream);
+    // timed: bracket the passes with the events of the step's timing slot (slot 0 while capturing)
+    cudaEvent_t* ev = timed ? &h->tev[h->capturing ? 0 : 3 * (h->tev_next % kTimingSlots)] : nullptr;
+    if (timed) record_timing_event(h, ev[0]);
     int rc = 0;
     const char* pass = "forward";
     if (a.want_grad && h->chunk > 0 && a.n > h->chunk) {
@@ -531,17 +546,17 @@ int smc2::launch_filters(smc2_handle* h, const PFArgs& a, bool timed) {
         if (!rc && !joined) return fail(SMC2_E_CUDA, "filter launch: join of the second stream failed");
         // the passes overlap: the timing slot holds both together
         if (timed && !rc) {
-            cudaEventRecord(ev[1], h->stream);
-            cudaEventRecord(ev[2], h->stream);
+            record_timing_event(h, ev[1]);
+            record_timing_event(h, ev[2]);
         }
     } else {
         rc = h->fwd(a, h->stream, a.n);
-        if (timed && !rc) cudaEventRecord(ev[1], h->stream);
+        if (timed && !rc) record_timing_event(h, ev[1]);
         if (!rc && a.want_grad) {
             rc = h->bwd(a, h->stream, a.n);
             pass = "adjoint";
         }
-        if (timed && !rc) cudaEventRecord(ev[2], h->stream);
+        if (timed && !rc) record_timing_event(h, ev[2]);
     }
     if (rc)
         return fail(SMC2_E_CUDA, std::string(pass) + " filter launch failed: " +
@@ -584,6 +599,12 @@ extern "C" int pf_loglik_grad_host(smc2_handle* h, const double* theta_host, int
     int rc2 = read_status(h, &st);
     if (rc2) return rc2;
     if (st) return fail(SMC2_E_TIMEOUT, "a bounded wait in a device kernel expired");
+    return SMC2_OK;
+}
+
+extern "C" int smc2_get_stream(const smc2_handle* h, void** stream) {
+    if (!h || !stream) return fail(SMC2_E_INVAL, "NULL argument");
+    *stream = static_cast<void*>(h->stream);
     return SMC2_OK;
 }
 
@@ -635,6 +656,8 @@ static int launches_per_step(const smc2_handle* h) {
 
 int smc2::enqueue_step(smc2_handle* h) {
     const OuterArgs o = make_outer_args(h);
+    // the iteration's resampling diagnostics start from zero (a memset node in the step graph)
+    CUDA_TRY(cudaMemsetAsync(h->ties, 0, 2 * sizeof(unsigned long long), h->stream));
     // iteration 1 draws from the prior: every proposal takes the same path there
     const bool hmc = o.hmc && h->k >= 1;
     const int L = hmc ? h->cfg.hmc_steps : 1;
@@ -652,32 +675,80 @@ int smc2::enqueue_step(smc2_handle* h) {
     return SMC2_OK;
 }
 
-int smc2::step_async(smc2_handle* h) {
-    // first iteration eagerly (sets kernel attributes); later ones replay a captured graph
-    if (h->k >= 1 && !h->graph_exec && !h->no_graph && !h->timing) {
-        cudaGraph_t g = nullptr;
-        CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-        const uint64_t before = g_launches.load();
-        int rc = enqueue_step(h);
-        cudaError_t e = cudaStreamEndCapture(h->stream, &g);
-        g_launches = before;  // captured, not launched
-        h->launches_per_step = 0;
-        if (rc || e != cudaSuccess) {
-            if (g) cudaGraphDestroy(g);
-            cudaGetLastError();
-            h->no_graph = true;
-        } else {
-            e = cudaGraphInstantiate(&h->graph_exec, g, 0);
-            cudaGraphDestroy(g);
-            if (e != cudaSuccess) {
-                cudaGetLastError();
-                h->graph_exec = nullptr;
-                h->no_graph = true;
-            }
-        }
+// Capture one iteration into a graph (timed: with the filter passes' event-record nodes).
+// On failure the handle falls back to eager launches for good.
+static void capture_step(smc2_handle* h, bool timed) {
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        h->no_graph = true;
+        return;
     }
-    if (h->graph_exec && !h->timing) {
-        CUDA_TRY(cudaGraphLaunch(h->graph_exec, h->stream));
+    const uint64_t before = g_launches.load();
+    h->capturing = true;
+    int rc = enqueue_step(h);
+    h->capturing = false;
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    g_launches = before;  // captured, not launched
+    h->launches_per_step = 0;
+    cudaGraphExec_t ge = nullptr;
+    if (!rc && e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+    if (rc || e != cudaSuccess || !ge) {
+        if (ge) cudaGraphExecDestroy(ge);
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        h->no_graph = true;
+        return;
+    }
+    if (!timed) {
+        cudaGraphDestroy(g);
+        h->graph_exec = ge;
+        return;
+    }
+    // the three event-record nodes, told apart by the slot-0 event each records
+    size_t n = 0;
+    bool ok = cudaGraphGetNodes(g, nullptr, &n) == cudaSuccess;
+    std::vector<cudaGraphNode_t> nodes(n);
+    ok = ok && cudaGraphGetNodes(g, nodes.data(), &n) == cudaSuccess;
+    int found = 0;
+    for (size_t i = 0; ok && i < n; ++i) {
+        cudaGraphNodeType ty;
+        if (cudaGraphNodeGetType(nodes[i], &ty) != cudaSuccess || ty != cudaGraphNodeTypeEventRecord) continue;
+        cudaEvent_t ev = nullptr;
+        if (cudaGraphEventRecordNodeGetEvent(nodes[i], &ev) != cudaSuccess) continue;
+        for (int k = 0; k < 3; ++k)
+            if (ev == h->tev[k] && !h->ev_nodes[k]) {
+                h->ev_nodes[k] = nodes[i];
+                ++found;
+            }
+    }
+    if (!ok || found != 3) {
+        cudaGetLastError();
+        cudaGraphExecDestroy(ge);
+        cudaGraphDestroy(g);
+        h->ev_nodes[0] = h->ev_nodes[1] = h->ev_nodes[2] = nullptr;
+        h->no_graph = true;
+        return;
+    }
+    h->graph_timed_tmpl = g;  // the node handles refer to it: kept while the graph exists
+    h->graph_timed = ge;
+}
+
+int smc2::step_async(smc2_handle* h) {
+    // first iteration eagerly (sets kernel attributes); later ones replay a captured graph,
+    // with timing on the same graph plus the event-record nodes of the filter passes
+    if (h->k >= 1 && !h->no_graph) {
+        if (!h->timing && !h->graph_exec) capture_step(h, false);
+        if (h->timing && !h->graph_timed) capture_step(h, true);
+    }
+    cudaGraphExec_t ge = h->timing ? h->graph_timed : h->graph_exec;
+    if (h->k >= 1 && ge) {
+        if (h->timing) {
+            cudaEvent_t* ev = &h->tev[3 * (h->tev_next % kTimingSlots)];
+            for (int k = 0; k < 3; ++k)
+                CUDA_TRY(cudaGraphExecEventRecordNodeSetEvent(ge, h->ev_nodes[k], ev[k]));
+        }
+        CUDA_TRY(cudaGraphLaunch(ge, h->stream));
         count_launches(launches_per_step(h));
     } else {
         int rc = enqueue_step(h);
@@ -744,9 +815,14 @@ int smc2::read_stats(smc2_handle* h, smc2_stats* out) {
     CUDA_TRY(cudaMemcpyAsync(h->h_stats, h->stats, sizeof(double) * (kStatsHead + 2 * D), cudaMemcpyDeviceToHost,
                              h->stream));
     CUDA_TRY(cudaMemcpyAsync(h->h_status, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(h->h_ties, h->ties, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                             h->stream));
     CUDA_TRY(cudaStreamSynchronize(h->stream));
     if (*h->h_status) return fail(SMC2_E_TIMEOUT, "a bounded wait in a device kernel expired");
     if (!out) return SMC2_OK;
+    out->pf_near_ties = (int64_t)h->h_ties[0];
+    out->pf_resample_steps = (int64_t)h->h_ties[1];
+    out->outer_near_ties = (int64_t)h->h_stats[kStOuterTies];
     const double* s = h->h_stats;
     out->k = (int32_t)s[kStK];
     out->resampled = s[kStResampled] != 0.0;
@@ -776,6 +852,7 @@ extern "C" int smc2_step_filters(smc2_handle* h, int row0, int n, double* loglik
     if (row0 < 0 || n < 0 || row0 + n > h->cfg.N) return fail(SMC2_E_INVAL, "rows must lie in [0, N)");
     if (n > 0 && (!loglik_dev || !grad_dev)) return fail(SMC2_E_INVAL, "loglik and grad must not be NULL");
     const OuterArgs o = make_outer_args(h);
+    CUDA_TRY(cudaMemsetAsync(h->ties, 0, 2 * sizeof(unsigned long long), h->stream));
     if (launch_outer_propose(o, h->stream)) return fail(SMC2_E_CUDA, "outer propose launch failed");
     count_launches(1);
     if (n > 0) {

@@ -296,6 +296,7 @@ __global__ void __launch_bounds__(kOuterThreads) outer_stats_kernel(OuterArgs a)
         a.stats[kStSumL] = ((k == 1u) ? 0.0 : a.stats[kStSumL]) + ess;
         a.stats[kStK] = (double)k;
         a.stats[kStLwNew] = lmax + log(s1) - log((double)N);  // log w of every sample after resampling
+        a.stats[kStOuterTies] = 0.0;
     }
     if (!resample) return;
 
@@ -335,6 +336,7 @@ __global__ void __launch_bounds__(kOuterThreads) outer_stats_kernel(OuterArgs a)
     const PhiloxKey key = philox_key(a.seed_lo, a.seed_hi, k, 0u);
     const uint4 w = philox4x32_10(make_uint4(0u, 0u, kStreamOuterNu, 0u), key);
     const double nu = u01_open_d(w.x);
+    double nties = 0.0;
     for (int i = tid; i < N; i += nt) {
         const double tau = ((double)i + nu) / (double)N;
         int lo = 0, hi = N - 1;
@@ -344,7 +346,11 @@ __global__ void __launch_bounds__(kOuterThreads) outer_stats_kernel(OuterArgs a)
             else lo = mid + 1;
         }
         a.outer_anc[i] = lo;
+        // near-tie: another index is admissible within the band (App. B's count form)
+        if (csum[lo] - tau < kOuterTieBand || (lo > 0 && tau - csum[lo - 1] <= kOuterTieBand)) nties += 1.0;
     }
+    nties = block_sum_d(nties, red);
+    if (tid == 0) a.stats[kStOuterTies] = nties;
 }
 
 // 3. after resampling: gather the ancestors' rows (theta, grad log pi into the scratch rows

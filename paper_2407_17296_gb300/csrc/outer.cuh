@@ -30,8 +30,12 @@ struct OuterArgs {
 };
 
 // stats layout (FP64 slots)
-enum { kStEss = 0, kStLk = 1, kStResampled = 2, kStMaxLogw = 3, kStSumL = 4, kStK = 5, kStLwNew = 6, kStatsHead = 7 };
+enum { kStEss = 0, kStLk = 1, kStResampled = 2, kStMaxLogw = 3, kStSumL = 4, kStK = 5, kStLwNew = 6,
+       kStOuterTies = 7, kStatsHead = 8 };
+// kStOuterTies: outer resampling thresholds within kOuterTieBand of a neighbouring cumulative weight
 // then mean [D] at kStatsHead, recycled numerator sum_k l_k f~_k [D] at kStatsHead + D
+
+constexpr double kOuterTieBand = 1e-6;
 
 int launch_outer_propose(const OuterArgs& a, void* stream);
 // HMC move of iteration k > 1: momentum draw, first half kick and drift (replaces the

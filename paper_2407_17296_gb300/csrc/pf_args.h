@@ -40,7 +40,14 @@ struct PFArgs {
     double* loglik;         // [n]
     double* grad;           // [n][D]
     int* status;            // device status word: bit kStatusTimeout when a bounded wait expired
+    // resampling diagnostics, or nullptr: [0] += cumulative-weight boundaries that lie within
+    // kNearTieBand of a resampling threshold (near-ties), [1] += filter-steps that resampled
+    unsigned long long* ties;
 };
+
+// Half-width of the near-tie band on normalised cumulative weights (App. B's ancestor index
+// is decided within this distance of a threshold only up to rounding).
+constexpr float kNearTieBand = 1e-6f;
 
 // Particle rows of stored state slices are padded to a multiple of 4 so that every slice
 // starts on a 16-byte boundary (bulk asynchronous copies need it).

@@ -252,11 +252,14 @@ __device__ __forceinline__ void load_u16(const uint16_t* row, int j0, int M, int
 // warp's first child is recorded for that warp (carry), which seeds the warp's prefix-max.
 // Two __syncthreads.  anc[p] is the ancestor of particle i = j0 + p, first[p] the first
 // offspring of parent j0 + p (its offspring are first[p] .. first of parent j0 + p + 1, or M).
-template <int P, int G>
+// With COUNT, nties grows by the parents j < M - 1 of this thread whose cumulative weight
+// c_j lies within kNearTieBand of a threshold: |c_j M - nu - i| < kNearTieBand M for the
+// nearest i in 0..M-1 (scaled units; a diagnostic, evaluated in FP32).
+template <int P, int G, bool COUNT>
 __device__ __forceinline__ void systematic_ancestors(const float (&lw)[P], bool lead, int j0, int M, float nu,
                                                      uint16_t* marks, unsigned long long* scanw,
                                                      int* carry, int* maxoff, int (&anc)[P], int (&first)[P],
-                                                     int& max_offspring) {
+                                                     int& max_offspring, int& nties) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     constexpr int C = (32 / G) * P;  // children (particles) per warp
     if (lead) {
@@ -272,11 +275,18 @@ __device__ __forceinline__ void systematic_ancestors(const float (&lw)[P], bool 
     const float sc40 = scale * 0x1p40f;
     const int lo0 = count_below(c0, M);
     int lo = lo0, off = 0;
-    const int hiP = count_below(u64_to_float_rz(base + s[P - 1]) * scale - nu, M);
+    const float vP = u64_to_float_rz(base + s[P - 1]) * scale - nu;
+    const int hiP = count_below(vP, M);
+    const float bandM = kNearTieBand * (float)M;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         const int j = j0 + p;
-        const int hi = (j == M - 1) ? M : (p == P - 1) ? hiP : min(count_below(fmaf(sf[p], sc40, c0), M), hiP);
+        const float v = (p == P - 1) ? vP : fmaf(sf[p], sc40, c0);
+        if constexpr (COUNT) {
+            const float r = rintf(v);
+            if (lead && j < M - 1 && r >= 0.f && r <= (float)(M - 1) && fabsf(v - r) < bandM) ++nties;
+        }
+        const int hi = (j == M - 1) ? M : (p == P - 1) ? hiP : min(count_below(v, M), hiP);
         first[p] = lo;
         if (lead && j < M && hi > lo) marks[lo] = (uint16_t)(j + 1);
         off = max(off, hi - lo);
@@ -322,10 +332,12 @@ __device__ __forceinline__ void systematic_ancestors(const float (&lw)[P], bool 
 
 // Multinomial ancestors (the paper's scheme, App. B): one uniform nu_i per particle,
 // a_i = min{j : c_j >= nu_i} by binary search over the cumulative weights.  Two __syncthreads.
-template <int P, int G>
+// With COUNT, nties grows by the thresholds nu_i of this thread that lie within kNearTieBand
+// of a cumulative weight next to the chosen index (c_a - nu_i < band or nu_i - c_{a-1} <= band).
+template <int P, int G, bool COUNT>
 __device__ __forceinline__ void multinomial_ancestors(const float (&lw)[P], bool lead, int j0, int M,
                                                       const PhiloxKey& key, uint32_t t, float* cs,
-                                                      unsigned long long* scanw, int (&anc)[P]) {
+                                                      unsigned long long* scanw, int (&anc)[P], int& nties) {
     unsigned long long s[P], base, tot;
     float sf[P];
     block_fixed_scan<P, G>(lw, lead, j0, M, scanw, s, sf, base, tot);
@@ -350,6 +362,11 @@ __device__ __forceinline__ void multinomial_ancestors(const float (&lw)[P], bool
             else lo = mid + 1;
         }
         anc[p] = lo;
+        if constexpr (COUNT) {
+            if (lead && i < M &&
+                (cs[lo] - nu < kNearTieBand || (lo > 0 && nu - cs[lo - 1] <= kNearTieBand)))
+                ++nties;
+        }
     }
 }
 
@@ -865,6 +882,8 @@ __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, cons
             a.lstep[(size_t)f * (T + 1)] = Lprev;
         }
     }
+    const bool count_ties = a.ties != nullptr;
+    int nties = 0, nresampled = 0;  // resampling diagnostics of this thread (see PFArgs::ties)
     float nu_lane = 0.f;  // systematic offset of step 32 k + 1 + lane, drawn for 32 steps at once
     for (int t = 1; t <= T; ++t) {
         int max_offspring = 0;
@@ -899,12 +918,13 @@ __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, cons
             if (a.scheme == 0) {
                 const float nu = __shfl_sync(kFull, nu_lane, (t - 1) & 31);
                 int first[P];
-                systematic_ancestors<P, G>(lw, lead, j0, M, nu, marks, scanw, carry, maxoff, anc, first,
-                                           max_offspring);
+                systematic_ancestors<P, G, true>(lw, lead, j0, M, nu, marks, scanw, carry, maxoff, anc, first,
+                                                 max_offspring, nties);
                 if (a.offs && lead) store_u16<P>(tr.offs_row(t - 1), j0, M, first);
             } else {
-                multinomial_ancestors<P, G>(lw, lead, j0, M, key, (uint32_t)t, cs, scanw, anc);
+                multinomial_ancestors<P, G, true>(lw, lead, j0, M, key, (uint32_t)t, cs, scanw, anc, nties);
             }
+            ++nresampled;
             if (a.anc && lead) store_u16<P>(tr.anc_row(t - 1), j0, M, anc);
 #pragma unroll
             for (int p = 0; p < P; ++p) {
@@ -992,6 +1012,11 @@ __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, cons
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
         if (tid == 0) a.loglik[f] = dead ? -INFINITY : acc;
+    }
+    if (count_ties) {
+        const int nw = __reduce_add_sync(kFull, nties);
+        if ((tid & 31) == 0 && nw) atomicAdd(&a.ties[0], (unsigned long long)nw);
+        if (tid == 0 && nresampled) atomicAdd(&a.ties[1], (unsigned long long)nresampled);
     }
 }
 

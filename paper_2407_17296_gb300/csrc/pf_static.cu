@@ -58,18 +58,23 @@ size_t static_need(const smc2_config& c, int D, int kc, Sizes* s) {
 
 }  // namespace
 
+// Offset of the status word in the array (after the copy of H).
+constexpr size_t kStatusOffset = (sizeof(float) * 256 + 255) & ~size_t(255);
+
 extern "C" int pf_loglik_grad_static(const smc2_config* cfg, const double* theta_dev, int n, uint32_t iter,
                                      uint32_t row0, double* loglik_dev, double* grad_dev) {
-    int D = 0;
-    int rc = validate(cfg, &D);
-    if (rc) return rc;
-    if (!cfg->y_on_device) return fail(SMC2_E_INVAL, "pf_loglik_grad_static needs y on the device (y_on_device = 1)");
+    if (!cfg) return fail(SMC2_E_INVAL, "config is NULL");
     if (n < 0 || n > 4096) return fail(SMC2_E_INVAL, "n must be in [0, 4096]");
     if (n == 0) return SMC2_OK;
-    if (!theta_dev || !loglik_dev) return fail(SMC2_E_INVAL, "theta and loglik must not be NULL");
-
+    // cfg->N plays no part: the sizes are checked for the n rows of this call
     smc2_config c = *cfg;
     c.N = n;
+    int D = 0;
+    int rc = validate(&c, &D);
+    if (rc) return rc;
+    if (!cfg->y_on_device) return fail(SMC2_E_INVAL, "pf_loglik_grad_static needs y on the device (y_on_device = 1)");
+    if (!theta_dev || !loglik_dev) return fail(SMC2_E_INVAL, "theta and loglik must not be NULL");
+
     // checkpoint interval: the caller's, else the smallest power of two whose scratch fits
     int kc = cfg->ckpt_every;
     Sizes s;
@@ -108,7 +113,7 @@ extern "C" int pf_loglik_grad_static(const smc2_config* cfg, const double* theta
         return r;
     };
     float* Hs = reinterpret_cast<float*>(take(sizeof(float) * 256));
-    int* status = reinterpret_cast<int*>(take(sizeof(int)));
+    int* status = reinterpret_cast<int*>(take(sizeof(int)));  // at kStatusOffset
     PFArgs a{};
     a.theta = theta_dev;
     a.y = cfg->y;
@@ -155,5 +160,22 @@ extern "C" int pf_loglik_grad_static(const smc2_config* cfg, const double* theta
         return fail(SMC2_E_CUDA, std::string("filter launch failed: ") +
                                      (lrc > 0 ? cudaGetErrorString((cudaError_t)lrc) : "block too large"));
     count_launches(a.want_grad ? 2 : 1);
+    return SMC2_OK;
+}
+
+extern "C" int pf_static_get_status(void* stream, int* status, int clear) {
+    if (!status) return fail(SMC2_E_INVAL, "status is NULL");
+    void* base = nullptr;
+    int rc = scratch_address(&base);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int* word = reinterpret_cast<int*>(static_cast<unsigned char*>(base) + kStatusOffset);
+    int host = 0;
+    if (cudaMemcpyAsync(&host, word, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return fail(SMC2_E_CUDA, std::string("reading the status word: ") + cudaGetErrorString(cudaGetLastError()));
+    *status = host;
+    if (clear && host && cudaMemsetAsync(word, 0, sizeof(int), st) != cudaSuccess)
+        return fail(SMC2_E_CUDA, "clearing the status word failed");
     return SMC2_OK;
 }

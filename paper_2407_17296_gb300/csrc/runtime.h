@@ -65,6 +65,8 @@ struct smc2_handle {
     int* outer_anc = nullptr;
     uint32_t* k_dev = nullptr;
     int* status = nullptr;      // device status word of the handle's kernels
+    unsigned long long* ties = nullptr;    // [2] resampling diagnostics of the filters (PFArgs::ties)
+    unsigned long long* h_ties = nullptr;  // host copy
     int* h_status = nullptr;    // host copy of the status word
     float *xck = nullptr, *lwck = nullptr, *xseg = nullptr, *lwseg = nullptr, *mstep = nullptr, *lstep = nullptr;
     uint16_t* anc = nullptr;
@@ -73,10 +75,16 @@ struct smc2_handle {
     double* h_stats = nullptr;  // host copy of the outer statistics
     uint32_t k = 0;             // iterations enqueued
     cudaGraphExec_t graph_exec = nullptr;
-    // filter-pass timing: with timing on, steps run eagerly and record three events each
-    // (before the forward pass, between the passes, after the adjoint) into a ring of
-    // kTimingSlots slots; smc2_get_step_timing averages the steps recorded since its last call
+    // filter-pass timing: with timing on, every step records three events (before the forward
+    // pass, between the passes, after the adjoint) into a ring of kTimingSlots slots;
+    // smc2_get_step_timing averages the steps recorded since its last call.  Steps after the
+    // first replay graph_timed, the step graph with three event-record nodes (ev_nodes, in the
+    // template graph_timed_tmpl) that are pointed at the slot's events before each launch.
     bool timing = false;
+    bool capturing = false;         // enqueue_step is being captured into a graph
+    cudaGraph_t graph_timed_tmpl = nullptr;
+    cudaGraphExec_t graph_timed = nullptr;
+    cudaGraphNode_t ev_nodes[3] = {nullptr, nullptr, nullptr};
     std::vector<cudaEvent_t> tev;  // 3 * kTimingSlots, created when timing is first switched on
     int tev_next = 0;              // slot of the next timed step
     int tev_pending = 0;           // timed steps not yet reported (<= kTimingSlots)

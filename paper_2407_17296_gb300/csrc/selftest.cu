@@ -7,9 +7,11 @@
 // limit, and reports what the status word says.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <string>
 
 #include "../../include/smc2.h"
+#include "philox.cuh"
 #include "ring.cuh"
 #include "runtime.h"
 
@@ -25,7 +27,48 @@ __global__ void wait_nothing_kernel(uint32_t polls, int* status) {
     if (!smc2::mbar_wait(&bar, 0u, polls)) atomicOr(status, smc2::kStatusTimeout);
 }
 
+// One thread per (key, counter) pair: the filter kernels' own key expansion, Philox rounds,
+// uniform map and Box-Muller pair (philox.cuh), written out for comparison.
+__global__ void crn_words_kernel(const uint32_t* __restrict__ ctr, const uint32_t* __restrict__ key, int n,
+                                 uint32_t* __restrict__ words, float* __restrict__ u, float* __restrict__ z) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const smc2::PhiloxKey k = smc2::philox_key(key[4 * i], key[4 * i + 1], key[4 * i + 2], key[4 * i + 3]);
+        const uint4 w = smc2::philox4x32_10(make_uint4(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]), k);
+        if (words) {
+            words[4 * i] = w.x;
+            words[4 * i + 1] = w.y;
+            words[4 * i + 2] = w.z;
+            words[4 * i + 3] = w.w;
+        }
+        if (u) {
+            u[4 * i] = smc2::u01_open(w.x);
+            u[4 * i + 1] = smc2::u01_open(w.y);
+            u[4 * i + 2] = smc2::u01_open(w.z);
+            u[4 * i + 3] = smc2::u01_open(w.w);
+        }
+        if (z) {
+            smc2::box_muller(w.x, w.y, z[4 * i], z[4 * i + 1]);
+            smc2::box_muller(w.z, w.w, z[4 * i + 2], z[4 * i + 3]);
+        }
+    }
+}
+
 }  // namespace
+
+extern "C" int smc2_selftest_crn(const uint32_t* ctr_dev, const uint32_t* key_dev, int n, uint32_t* words_dev,
+                                 float* u_dev, float* z_dev, void* stream) {
+    using namespace smc2;
+    if (n < 0 || (n > 0 && (!ctr_dev || !key_dev))) return fail(SMC2_E_INVAL, "n < 0 or NULL inputs");
+    if (n == 0) return SMC2_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int blocks = (int)std::min<long>((n + 255) / 256, 4096);
+    crn_words_kernel<<<blocks, 256, 0, st>>>(ctr_dev, key_dev, n, words_dev, u_dev, z_dev);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(SMC2_E_CUDA, std::string("CRN self-test: ") + cudaGetErrorString(e));
+    count_launches(1);
+    return SMC2_OK;
+}
 
 extern "C" int smc2_selftest_bounded_wait(int polls, int* timed_out) {
     using namespace smc2;

@@ -18,3 +18,23 @@ def gpu_lib():
     """The CUDA library (fails loudly if it was not built)."""
     from paper_2407_17296_gb300 import binding
     return binding.load()
+
+
+def pytest_sessionfinish(session, exitstatus):
+    """Write the near-tie counts of the GPU parity tests that ran (tests/parity.py TIE_REPORT)
+    to $SMC2_TIE_REPORT, or to gpurun_out/parity_near_ties.json when that folder exists."""
+    import json
+    try:
+        from tests.parity import TIE_REPORT
+    except ImportError:
+        return
+    if not TIE_REPORT:
+        return
+    path = os.environ.get("SMC2_TIE_REPORT")
+    if not path:
+        out = os.path.join(ROOT, "gpurun_out")
+        if not os.path.isdir(out):
+            return
+        path = os.path.join(out, "parity_near_ties.json")
+    with open(path, "w") as f:
+        json.dump(TIE_REPORT, f, indent=1, sort_keys=True)

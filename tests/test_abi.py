@@ -129,3 +129,22 @@ def test_hmc_steps_are_validated(lib, steps, code):
     assert lib.smc2_footprint(ctypes.byref(c), ctypes.byref(b)) == code
     c = _cfg(proposal=binding.LANGEVIN, hmc_steps=steps)
     assert lib.smc2_footprint(ctypes.byref(c), ctypes.byref(b)) == 0
+
+
+def test_new_entry_points_validate_without_device_work(lib):
+    """Argument checks of the self-test, stream and static-status calls (no device call)."""
+    from paper_2407_17296_gb300 import binding
+    assert lib.smc2_selftest_crn(None, None, -1, None, None, None, None) == -1
+    assert lib.smc2_selftest_crn(None, None, 4, None, None, None, None) == -1
+    assert lib.smc2_get_stream(None, None) == -1
+    assert lib.pf_static_get_status(None, None, 0) == -1
+    assert "NULL" in binding.last_error() or "status" in binding.last_error()
+
+
+def test_stats_struct_carries_near_tie_counts():
+    from paper_2407_17296_gb300 import binding
+    names = [f[0] for f in binding.Stats._fields_]
+    assert names[-3:] == ["pf_near_ties", "pf_resample_steps", "outer_near_ties"]
+    src = open(HEADER).read()
+    for n in names:
+        assert re.search(r"\b" + n + r"\s*;", src), n

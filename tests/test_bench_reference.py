@@ -32,5 +32,11 @@ def test_reference_arm_json_line():
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     cfg = d["config"]
     assert cfg["workload"].startswith("lg1:") and (cfg["N"], cfg["M"], cfg["T"], cfg["D"]) == (64, 128, 100, 3)
-    # ms per step is the time the whole workload (N filters) would take at the measured rate
-    assert abs(d["ms_per_step"] - 1e3 * 64 * 128 * 100 / d["value"]) <= 1e-9 * d["ms_per_step"]
+    # ms per step is the measured wall time of a step's sample (it fits the run); the time the
+    # whole workload (N filters) would take at the measured rate is labelled as extrapolated
+    ext = cfg["extrapolated_ms_per_iteration"]
+    assert abs(ext - 1e3 * 64 * 128 * 100 / d["value"]) <= 1e-9 * ext
+    assert 0 < d["ms_per_step"] * d["steps"] < 1e3 * 280
+    # the oracle at one thread and on all (here: two) cores
+    assert d["cpu_baseline"]["threads_1"]["threads"] == 1 and d["cpu_baseline"]["threads_1"]["value"] > 0
+    assert d["cpu_baseline"]["threads_all"] == {"value": d["value"], "threads": 2}

@@ -27,7 +27,8 @@ def test_parity_small(make, T, M, n, scheme, kc):
     w = make(T=T, N=n, M=M)
     theta = W.thetas_near(w, n, 0.05, seed=11)
     ll, g, anc, flag = gpu_pf(w, theta, iteration=3, pf_resample=scheme, ckpt_every=kc)
-    agg = check_rows(w, theta, ll, g, anc, flag, range(n), iteration=3, scheme=scheme)
+    agg = check_rows(w, theta, ll, g, anc, flag, range(n), iteration=3, scheme=scheme,
+                     name=f"small {w.name} T={T} M={M} scheme={scheme} kc={kc}")
     assert agg["resample_steps"] > 0
     _report(f"{w.name} T={T} M={M} scheme={scheme} kc={kc}", agg)
 
@@ -40,25 +41,35 @@ def test_parity_particles_per_thread(ppt):
     check_rows(w, theta, ll, g, anc, flag, range(3))
 
 
+def _spread(N, ends, stride, start):
+    """Rows at the ends of the launch and of its two halves, and every stride-th row between."""
+    return sorted(set(ends) | set(range(start, N, stride)))
+
+
 def test_parity_full_size_lg4():
     """Full linear-Gaussian workload (N=1024, M=1024, T=250) in the benchmark's launch
-    configuration; sampled filters checked one by one."""
+    configuration (two halves of 512 filters on two streams); 70 filters checked one by one,
+    among them the first and last of each half."""
     w = W.lg4()
     theta = W.thetas_near(w, w.N, 0.05, seed=21)
     ll, g, anc, flag = gpu_pf(w, theta, iteration=2)
     assert np.all(np.isfinite(ll)) and np.all(np.isfinite(g))
-    agg = check_rows(w, theta, ll, g, anc, flag, [0, 1, 513, 1022, 1023], iteration=2)
+    rows = _spread(w.N, [0, 1, 2, 255, 256, 511, 512, 513, 767, 1021, 1022, 1023], 17, 3)
+    assert len(rows) >= 64
+    agg = check_rows(w, theta, ll, g, anc, flag, rows, iteration=2, name="full lg4 N=1024 M=1024 T=250")
     _report("lg4 full", agg)
 
 
 def test_parity_full_size_lg16():
     """Full 16-dimensional workload (N=2048, M=1024, T=200, D=48; each particle spread over
-    four lanes); sampled filters checked one by one."""
+    two lanes forward and four in the adjoint); 35 filters checked one by one."""
     w = W.lg16()
     theta = W.thetas_near(w, w.N, 0.03, seed=23)
     ll, g, anc, flag = gpu_pf(w, theta, iteration=2)
     assert np.all(np.isfinite(ll)) and np.all(np.isfinite(g))
-    agg = check_rows(w, theta, ll, g, anc, flag, [0, 1500, 2047], iteration=2)
+    rows = _spread(w.N, [0, 1023, 1024, 2047], 67, 7)
+    assert len(rows) >= 32
+    agg = check_rows(w, theta, ll, g, anc, flag, rows, iteration=2, name="full lg16 N=2048 M=1024 T=200")
     _report("lg16 full", agg)
 
 
@@ -77,17 +88,21 @@ def test_parity_full_size_lgssm():
     theta = W.thetas_near(w, w.N, 0.05, seed=24)
     ll, g, anc, flag = gpu_pf(w, theta, iteration=2, ess_frac=0.9)
     assert np.all(np.isfinite(ll)) and np.all(np.isfinite(g))
-    agg = check_rows(w, theta, ll, g, anc, flag, range(w.N), iteration=2, ess_frac=0.9)
+    agg = check_rows(w, theta, ll, g, anc, flag, range(w.N), iteration=2, ess_frac=0.9,
+                     name="full lgssm N=64 M=250 T=500")
     assert agg["resample_steps"] > 0
     _report("lgssm full", agg)
 
 
 def test_parity_full_size_sv():
+    """Full stochastic-volatility workload (N=4096, M=2048, T=500); 36 filters checked."""
     w = W.sv()
     theta = W.thetas_near(w, w.N, 0.05, seed=22)
     ll, g, anc, flag = gpu_pf(w, theta, iteration=2)
     assert np.all(np.isfinite(ll)) and np.all(np.isfinite(g))
-    agg = check_rows(w, theta, ll, g, anc, flag, [0, 2047, 4095], iteration=2)
+    rows = _spread(w.N, [0, 2047, 2048, 4095], 131, 5)
+    assert len(rows) >= 32
+    agg = check_rows(w, theta, ll, g, anc, flag, rows, iteration=2, name="full sv N=4096 M=2048 T=500")
     _report("sv full", agg)
 
 
@@ -213,6 +228,34 @@ def test_autograd_function():
         (ll * wts).sum().backward()
         np.testing.assert_array_equal(ll.detach().cpu().numpy(), ll_ref)
         np.testing.assert_allclose(th.grad.cpu().numpy(), g_ref * np.arange(1, 5)[:, None], rtol=1e-12)
+
+
+def test_autograd_orders_with_a_busy_current_stream():
+    """The handle runs on its own stream while torch's current stream is still producing theta
+    (a long chain of kernels before the copy that writes it) and consumes the outputs right
+    away: the Function's event ordering makes the results equal those of a quiet run."""
+    import torch
+    from paper_2407_17296_gb300 import autograd, binding
+    w = W.lg4(T=20, N=4, M=128)
+    theta = W.thetas_near(w, 4, 0.05)
+    ll_ref, g_ref, _, _ = gpu_pf(w, theta)
+    src = torch.tensor(theta, dtype=torch.float64, device="cuda")
+    side = torch.cuda.Stream()
+    with binding.Handle(binding.config_for(w)) as h:
+        assert h.stream_ptr() != side.cuda_stream
+        torch.cuda.synchronize()
+        with torch.cuda.stream(side):
+            x = torch.randn(2048, 2048, device="cuda")
+            for _ in range(30):  # tens of milliseconds of work ahead of theta on this stream
+                x = torch.tanh(x @ x)
+            th = (src + 0.0 * x[0, 0].double()).requires_grad_(True)
+            ll = autograd.loglik(th, h, 1)
+            out = ll * 1.0  # consumed on the current stream at once
+            out.sum().backward()
+            gr = th.grad.clone()
+        torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy(), ll_ref)
+    np.testing.assert_array_equal(gr.cpu().numpy(), g_ref)
 
 
 @pytest.mark.parametrize("make,M,n", [(W.lg16, 2048, 2), (W.lg4, 4096, 2)])
