@@ -69,6 +69,8 @@ def _args():
     p.add_argument("--hmc-steps", type=int, default=0,
                    help="run the workload with the HMC proposal of this many leapfrog steps "
                         "(step gamma / sqrt(L); every step runs the N filters)")
+    p.add_argument("--resample", default="systematic", choices=["systematic", "multinomial"],
+                   help="the filters' resampling scheme (multinomial is the paper's, Sec. II-B)")
     p.add_argument("--launch", default=None,
                    help="pin the launch instead of tuning: fwd_ppt,fwd_regs,adj_ppt,adj_regs,ckpt")
     p.add_argument("--experiment", default=None, choices=["lgssm"],
@@ -151,8 +153,8 @@ class ClockSampler:
 
 def _oracle_filter(args):
     import oracle
-    fam, dx, dy, H, theta, y, M, seed, it, row = args
-    r = oracle.pf(fam, dx, dy, H, theta, y, M, seed, it, row, want_tape=False)
+    fam, dx, dy, H, theta, y, M, seed, it, row, scheme = args
+    r = oracle.pf(fam, dx, dy, H, theta, y, M, seed, it, row, scheme=scheme, want_tape=False)
     return r["loglik"]
 
 
@@ -169,13 +171,14 @@ def cpu_oracle_rate(w, budget_s, procs=None, pool=None):
     H = None if w.H is None else np.asarray(w.H, dtype=np.float64)
     # calibrate on one filter, then size the sample to the budget
     t0 = time.perf_counter()
-    _oracle_filter((w.family, w.dx, w.dy, H, theta[0], w.y, w.M, w.seed, 2, 0))
+    scheme = 1 if getattr(w, "resample", "systematic") == "multinomial" else 0
+    _oracle_filter((w.family, w.dx, w.dy, H, theta[0], w.y, w.M, w.seed, 2, 0, scheme))
     one = time.perf_counter() - t0
     # enough filter runs for the budget, cycling over the iteration's filters when they
     # are fewer (small workloads would otherwise time milliseconds of pool overhead)
     n = int(max(procs, min(500000, budget_s * procs / max(one, 1e-6))))
     n = max(procs, (n // procs) * procs)
-    jobs = [(w.family, w.dx, w.dy, H, theta[i % w.N], w.y, w.M, w.seed, 2, i % w.N) for i in range(n)]
+    jobs = [(w.family, w.dx, w.dy, H, theta[i % w.N], w.y, w.M, w.seed, 2, i % w.N, scheme) for i in range(n)]
     if procs == 1:
         t0 = time.perf_counter()
         for j in jobs:
@@ -222,13 +225,15 @@ def make_workload(a):
         # outer weights degenerate on these workloads
         from dataclasses import replace
         w = replace(w, proposal="hmc", hmc_steps=a.hmc_steps, gamma=w.gamma / math.sqrt(a.hmc_steps))
+    w.resample = a.resample
     return w
 
 
 def workload_config(w):
     """The workload part of the JSON line's config, the same for both arms."""
     return {"workload": f"{w.name}: LG-diag d_x={w.dx} d_y={w.dy}" if w.family == 0 else f"{w.name}: SV",
-            "N": w.N, "M": w.M, "T": w.T, "D": w.D, "proposal": w.proposal, "gamma": w.gamma}
+            "N": w.N, "M": w.M, "T": w.T, "D": w.D, "proposal": w.proposal, "gamma": w.gamma,
+            "resample": getattr(w, "resample", "systematic")}
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -248,7 +253,8 @@ def run_gpu(a, rank, world, local):
     w.seed = w.seed + 1000 * rank
     binding.load()
     stream = torch.cuda.Stream(device=dev)
-    cfg = binding.config_for(w, stream=stream.cuda_stream)
+    cfg = binding.config_for(w, stream=stream.cuda_stream,
+                             pf_resample=binding.MULTINOMIAL if w.resample == "multinomial" else binding.SYSTEMATIC)
     if a.launch:
         binding.set_launch(cfg, [int(v) for v in a.launch.split(",")])
     elif not a.no_autotune:

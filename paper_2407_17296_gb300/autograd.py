@@ -8,10 +8,13 @@ The gradient is the one of App. A/B (common random numbers and ancestors held
 fixed), so it is exact for the estimator, as the paper's autograd gradient is.
 
 Stream order: the handle enqueues on its own stream.  forward makes that stream
-wait for torch's current stream (so theta is ready), makes the current stream
-wait for the handle's work (so the outputs are ready for the ops that follow),
-and marks the tensors the kernels touch as used on the handle's stream (so the
-caching allocator does not hand their memory out while the kernels run).
+wait for torch's current stream (so theta is ready) and makes the current stream
+wait for the handle's work (so the outputs are ready for the ops that follow).
+theta's contiguous copy and the outputs are allocated on the current stream, and
+torch's caching allocator hands a freed block only to later allocations on that
+same stream, whose work is queued behind the wait: no memory the kernels touch can
+be reused while they run.  (The tensors are not marked as used on the handle's
+stream: that stream may be destroyed with the handle before they are freed.)
 """
 import torch
 
@@ -37,9 +40,6 @@ class CRNPFLogLik(torch.autograd.Function):
                 hs.wait_stream(cur)  # theta (and its contiguous copy) written first
                 handle.pf_loglik_grad(th, iteration, ll, grad)
                 cur.wait_stream(hs)  # later ops on the current stream see ll and grad
-                for t in (th, ll, grad):
-                    if t is not None:
-                        t.record_stream(hs)
         ctx.save_for_backward(grad if grad is not None else th.new_zeros(0))
         return ll
 

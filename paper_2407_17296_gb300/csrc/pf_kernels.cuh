@@ -785,32 +785,60 @@ __device__ __forceinline__ void gather_adjoint_segmented(float (&xbar)[P][DL], c
         }
 }
 
-// Adjoint of the gather for unsorted ancestors (multinomial resampling): each thread clears
-// its own rows of `stage`, then every child adds its cotangent into its parent's row with
-// shared-memory atomics, and each thread reads back its own rows.  Two barriers.
+// Adjoint of the gather for unsorted ancestors (multinomial resampling), deterministic: the
+// cotangents are summed into their parents' rows of `stage` as integers (fixed point with one
+// power-of-two scale for the step, chosen from the block's largest |xbar| so that a sum over all
+// M children fits in 31 bits), so the result does not depend on the order of the shared-memory
+// atomics.  Each value is rounded once to a multiple of 2^-E (E = 30 - ceil(log2 M) - e, with
+// |xbar| < 2^e), at most M 2^-31 of the largest cotangent; a parent's sum is exact before its
+// conversion back to FP32.  Non-finite cotangents make every cotangent NaN (as float atomics
+// would).  wmax: 32 floats of scratch.  Two barriers.
 template <int P, int DX, int DL, int G>
 __device__ __forceinline__ void gather_adjoint_scatter(float (&xbar)[P][DL], const int (&ai)[P], int j0, int gl,
-                                                       int M, float* stage) {
+                                                       int M, float* stage, float* wmax) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int* acc = reinterpret_cast<int*>(stage);
+    float mx = 0.f;
+    bool bad = false;
 #pragma unroll
     for (int p = 0; p < P; ++p)
         if (j0 + p < M)
 #pragma unroll
-            for (int k = 0; k < DL; ++k) stage[(size_t)(j0 + p) * DX + gl * DL + k] = 0.f;
+            for (int k = 0; k < DL; ++k) {
+                acc[(j0 + p) * DX + gl * DL + k] = 0;  // the thread's own rows (x_t already read)
+                const float v = fabsf(xbar[p][k]);
+                bad |= !(v <= 3.0e38f);
+                mx = fmaxf(mx, v);
+            }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, o));
+    bad = __any_sync(kFull, bad);
+    if (lane == 0) wmax[wid] = bad ? INFINITY : mx;
     __syncthreads();
+    float m = 0.f;
+    for (int w = 0; w < nw; ++w) m = fmaxf(m, wmax[w]);  // the same value in every thread
+    const bool finite = m <= 3.0e38f;
+    // m < 2^e from the exponent field (zero and denormal m give the largest scale, clamped)
+    const int e = (int)((__float_as_uint(m) >> 23) & 0xffu) - 126;
+    const int lgM = 32 - __clz(max(M - 1, 1));  // ceil(log2 M), 1 for M <= 2
+    const int E = min(max(30 - lgM - e, -126), 126);
+    const float scale = __uint_as_float((uint32_t)(E + 127) << 23);
+    const float inv = __uint_as_float((uint32_t)(127 - E) << 23);
+    if (finite) {
 #pragma unroll
-    for (int p = 0; p < P; ++p)
-        if (j0 + p < M)
+        for (int p = 0; p < P; ++p)
+            if (j0 + p < M)
 #pragma unroll
-            for (int k = 0; k < DL; ++k) atomicAdd(&stage[(size_t)ai[p] * DX + gl * DL + k], xbar[p][k]);
+                for (int k = 0; k < DL; ++k)
+                    atomicAdd(&acc[ai[p] * DX + gl * DL + k], __float2int_rn(xbar[p][k] * scale));
+    }
     __syncthreads();
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-        if (j0 + p < M) {
-            read_staged<DX, DL>(stage, j0 + p, gl, xbar[p]);
-        } else {
 #pragma unroll
-            for (int k = 0; k < DL; ++k) xbar[p][k] = 0.f;
-        }
+        for (int k = 0; k < DL; ++k)
+            xbar[p][k] = (j0 + p < M) ? (finite ? (float)acc[(j0 + p) * DX + gl * DL + k] * inv : __int_as_float(0x7fc00000))
+                                      : 0.f;
     }
 }
 
@@ -1251,7 +1279,7 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
                 // adjoint of the gather x'_i = x_{a_i}: sum the cotangents of each parent's
                 // offspring, staged in the rows of x_t (each thread has read its own)
                 if (scheme != 0)
-                    gather_adjoint_scatter<P, DX, DL, G>(xbar, ai, j0, gl, M, st);
+                    gather_adjoint_scatter<P, DX, DL, G>(xbar, ai, j0, gl, M, st, segw);
                 else if (walk_rows && !(fb & 2))
                     gather_adjoint_runs<P, DX, DL, G>(xbar, j0, gl, M, offbuf + (nres & 1u) * (uint32_t)tape_stride(M),
                                                       st);

@@ -11,17 +11,27 @@ from paper_2407_17296_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 
+# jobs whose filters resample with the multinomial scheme (the paper's, Sec. II-B)
+MULTINOMIAL_JOBS = (6, 7)
+
+
 def _jobs():
     from dataclasses import replace
     return [W.lg1(T=50, N=64, M=128, K=3), W.lg4(T=40, N=32, M=256, K=3),
             W.sv(T=60, N=48, M=128, K=4), W.lg16(T=20, N=16, M=128, K=2),
             W.lg4(T=30, N=64, M=100, K=2, proposal="rw"),
-            replace(W.lg1(T=50, N=64, M=128, K=3, proposal="hmc"), hmc_steps=2, gamma=0.1)]
+            replace(W.lg1(T=50, N=64, M=128, K=3, proposal="hmc"), hmc_steps=2, gamma=0.1),
+            W.lg4(T=40, N=32, M=256, K=3), W.sv(T=60, N=48, M=128, K=3)]
 
 
-def _alone(w):
+def _cfg(i, w):
     from paper_2407_17296_gb300 import binding
-    with binding.Handle(binding.config_for(w)) as h:
+    return binding.config_for(w, pf_resample=1 if i in MULTINOMIAL_JOBS else 0)
+
+
+def _alone(i, w):
+    from paper_2407_17296_gb300 import binding
+    with binding.Handle(_cfg(i, w)) as h:
         st = None
         for _ in range(w.K):
             st = h.step()
@@ -46,9 +56,9 @@ def _wait(server, ids, timeout=120.0):
 def test_results_alone_equal_results_in_the_mix():
     from paper_2407_17296_gb300 import binding
     jobs = _jobs()
-    alone = [_alone(w) for w in jobs]
+    alone = [_alone(i, w) for i, w in enumerate(jobs)]
     with binding.Server(hbm_budget=8 << 30, max_active=8) as srv:
-        ids = [srv.submit(binding.config_for(w)) for w in jobs]
+        ids = [srv.submit(_cfg(i, w)) for i, w in enumerate(jobs)]
         res = _wait(srv, ids)
     for w, j, (th, lw, rec) in zip(jobs, ids, alone):
         r = res[j]
