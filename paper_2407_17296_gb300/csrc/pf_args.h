@@ -53,6 +53,24 @@ constexpr float kNearTieBand = 1e-6f;
 // starts on a 16-byte boundary (bulk asynchronous copies need it).
 SMC2_HD inline int padded_particles(int M) { return (M + 3) & ~3; }
 
+// Forward passes of 4-d states with one lane per particle stage each step's states in shared
+// memory and write the slice with one bulk copy (see forward_filter).
+SMC2_HD constexpr bool bulk_slices(int G, int DX) { return G == 1 && DX == 4; }
+
+// Rows of bulk-copied slices are stored swizzled when M is a multiple of 8 (every group of 8
+// rows is then complete inside the slice).
+SMC2_HD inline bool swizzled_slices(int G, int DX, int M) { return bulk_slices(G, DX) && (M & 7) == 0; }
+
+// Position of particle j's row inside a stored state slice (in HBM and in the adjoint's ring):
+// for swizzled slices of 16-byte rows (swz = swizzled_slices), row j sits at j XOR (bits 3..5
+// of j), which keeps the eight rows a quarter warp writes or reads (consecutive threads own
+// consecutive particles) in eight different 16-byte bank groups; identity otherwise.
+template <int DX, int G>
+__host__ __device__ __forceinline__ int slice_row(int j, bool swz) {
+    if constexpr (bulk_slices(G, DX)) return swz ? j ^ ((j >> 3) & 7) : j;
+    else return j;
+}
+
 // Rows of the ancestor tape are padded to a multiple of 8 entries (16 bytes).
 SMC2_HD inline int tape_stride(int M) { return (M + 7) & ~7; }
 
@@ -64,6 +82,11 @@ constexpr size_t kSmemLimit = 227 * 1024 - 1024;
 // bounds the forward pass records) for 1-d and 4-d states with one lane per particle; the
 // 16-d model (several lanes per particle) uses a segmented sum.
 SMC2_HD constexpr bool gather_walk(int G, int DX) { return G == 1 && (DX == 4 || DX == 1); }
+
+// Slots of the adjoint's shared-memory ring of trajectory slices: the model shape's preferred
+// count when its plan fits kSmemLimit, else its fallback (0: no ring, slices read from memory).
+SMC2_HD constexpr int ring_preferred(int DX) { return DX >= 16 ? 3 : (DX == 4 ? 5 : 8); }
+SMC2_HD constexpr int ring_fallback(int DX) { return DX >= 16 ? 0 : (DX >= 4 ? 2 : 4); }
 
 // Dynamic shared-memory plan (mirrored on the host to size the launch).
 struct SmemLayout {
@@ -80,7 +103,10 @@ struct SmemLayout {
             return r;
         };
         const size_t Mp = (size_t)padded_particles(M);
-        xstage = fwd ? take(sizeof(float) * (size_t)((M + 7) & ~7) * DX)  // gather slots: M rounded up to 8
+        // fwd: gather slots (M rounded up to 8), two slices when the step's states are staged
+        // for a bulk copy (the slice of step t in buffer t & 1)
+        xstage = fwd ? (bulk_slices(G, DX) ? take(sizeof(float) * Mp * DX * 2)
+                                           : take(sizeof(float) * (size_t)((M + 7) & ~7) * DX))
                      : take(sizeof(float) * Mp * DX * (R > 0 ? R : 1));
         // fwd: multinomial cumulative weights; bwd: two log-weight buffers
         cs = fwd ? take(sizeof(float) * (size_t)M) : take(sizeof(float) * 2 * Mp);
@@ -98,11 +124,6 @@ struct SmemLayout {
     }
 };
 
-// Slots of the adjoint's shared-memory ring of trajectory slices: the model shape's
-// preferred count when the plan fits kSmemLimit, else its fallback (0: no ring, slices
-// read from memory).
-SMC2_HD constexpr int ring_preferred(int DX) { return DX >= 16 ? 3 : (DX == 4 ? 5 : 8); }
-SMC2_HD constexpr int ring_fallback(int DX) { return DX >= 16 ? 0 : (DX >= 4 ? 2 : 4); }
 SMC2_HD inline int ring_slots(int M, int DX, int D, int G) {
     return SmemLayout(M, DX, D, false, G, ring_preferred(DX)).total <= kSmemLimit ? ring_preferred(DX)
                                                                                   : ring_fallback(DX);

@@ -419,10 +419,11 @@ __device__ __forceinline__ void load_run(const float* __restrict__ src, int j0, 
     for (int p = 0; p < P; ++p) v[p] = (j0 + p < M) ? src[j0 + p] : 0.f;
 }
 
-// One particle's lane slice of a state row.
+// One particle's lane slice of a state row (row position slice_row(j) for the model shapes
+// whose slices are bulk-copied; G = DX / DL lanes a particle).
 template <int DX, int DL>
-__device__ __forceinline__ void store_row(float* __restrict__ xdst, int j, int gl, const float (&x)[DL]) {
-    float* dst = xdst + (size_t)j * DX + gl * DL;
+__device__ __forceinline__ void store_row(float* __restrict__ xdst, int j, int gl, bool swz, const float (&x)[DL]) {
+    float* dst = xdst + (size_t)slice_row<DX, DX / DL>(j, swz) * DX + gl * DL;
     if constexpr (DL % 4 == 0) {
 #pragma unroll
         for (int k = 0; k < DL; k += 4)
@@ -442,9 +443,10 @@ __device__ __forceinline__ void store_state(float* __restrict__ xdst, float* __r
         for (int p = 0; p < P; ++p) v[p] = x[p][0];
         store_run<P>(xdst, j0, M, v);
     } else {
+        const bool swz = swizzled_slices(DX / DL, DX, M);
 #pragma unroll
         for (int p = 0; p < P; ++p)
-            if (j0 + p < M) store_row<DX, DL>(xdst, j0 + p, gl, x[p]);
+            if (j0 + p < M) store_row<DX, DL>(xdst, j0 + p, gl, swz, x[p]);
     }
     if (lwdst && gl == 0) store_run<P>(lwdst, j0, M, lw);
 }
@@ -452,9 +454,10 @@ __device__ __forceinline__ void store_state(float* __restrict__ xdst, float* __r
 template <int P, int DX, int DL>
 __device__ __forceinline__ void load_x(const float* __restrict__ xsrc, int j0, int gl, int M,
                                        float (&x)[P][DL]) {
+    const bool swz = swizzled_slices(DX / DL, DX, M);
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-        const float* src = xsrc + (size_t)min(j0 + p, M - 1) * DX + gl * DL;
+        const float* src = xsrc + (size_t)slice_row<DX, DX / DL>(min(j0 + p, M - 1), swz) * DX + gl * DL;
         if constexpr (DL % 4 == 0) {
 #pragma unroll
             for (int k = 0; k < DL; k += 4) {
@@ -482,6 +485,28 @@ __device__ __forceinline__ void stage_x(float* xstage, int j0, int gl, int M, co
             } else {
 #pragma unroll
                 for (int k = 0; k < DL; ++k) dst[k] = x[p][k];
+            }
+        }
+    }
+}
+
+// A thread's particles' full rows into a shared slice buffer at their slice_row positions
+// (one lane a particle: G = 1).
+template <int P, int DX, int DL>
+__device__ __forceinline__ void stage_x_rows(float* buf, int j0, int M, const float (&x)[P][DL]) {
+    static_assert(DL == DX, "full rows only");
+    const bool swz = swizzled_slices(1, DX, M);
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        if (j0 + p < M) {
+            float* dst = buf + slice_row<DX, 1>(j0 + p, swz) * DX;
+            if constexpr (DX % 4 == 0) {
+#pragma unroll
+                for (int k = 0; k < DX; k += 4)
+                    *reinterpret_cast<float4*>(dst + k) = make_float4(x[p][k], x[p][k + 1], x[p][k + 2], x[p][k + 3]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < DX; ++k) dst[k] = x[p][k];
             }
         }
     }
@@ -901,13 +926,36 @@ __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, cons
         }
     }
     const float logM = logf((float)M);
-    float Lprev = logM;
     bool resample = false, dead = false;
+    // Bulk-copied slices (bulk_slices): at the end of step t every thread writes its states x_t
+    // into shared buffer t & 1 (rows at slice_row positions, conflict-free across a quarter
+    // warp); at step t + 1, after the weight reduction's barriers, thread 0 copies that buffer to
+    // the trajectory with one bulk copy, and a resampling step t + 1 gathers its ancestors' rows
+    // from it.  Thread 0 waits at the start of step t + 1 until the copy issued at step t has
+    // read buffer (t - 1) & 1, which the threads overwrite at the end of step t + 1 (after the
+    // reduction's barriers).  ckslot: the trajectory slot of step tt, -1 if it is not stored.
+    constexpr bool kBulk = bulk_slices(G, DX);
+    const bool swz = swizzled_slices(G, DX, M);
+    float* const sbuf0 = xstage;
+    float* const sbuf1 = xstage + (size_t)padded_particles(M) * DX;
+    const uint32_t slice_bytes = (uint32_t)(sizeof(float) * padded_particles(M) * DX);
+    auto ckslot = [&](int tt) -> int {
+        if (a.kc == 1) return tt;
+        return (tt % a.kc == 0 && tt < T) ? tt / a.kc : -1;
+    };
+    if constexpr (kBulk) {
+        stage_x_rows<P, DX, DL>(sbuf0, j0, M, x);
+        fence_proxy_async_shared();
+    }
     if (store) {
-        store_state<P, DX, DL>(tr.x_ck(0), tr.lw_ck(0), j0, gl, M, x, lw);
+        if constexpr (kBulk) {
+            store_run<P>(tr.lw_ck(0), j0, M, lw);  // x_0 follows by bulk copy at step 1
+        } else {
+            store_state<P, DX, DL>(tr.x_ck(0), tr.lw_ck(0), j0, gl, M, x, lw);
+        }
         if (tid == 0) {
             a.mstep[(size_t)f * (T + 1)] = 0.f;
-            a.lstep[(size_t)f * (T + 1)] = Lprev;
+            a.lstep[(size_t)f * (T + 1)] = logM;
         }
     }
     const bool count_ties = a.ties != nullptr;
@@ -915,11 +963,16 @@ __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, cons
     float nu_lane = 0.f;  // systematic offset of step 32 k + 1 + lane, drawn for 32 steps at once
     for (int t = 1; t <= T; ++t) {
         int max_offspring = 0;
+        if constexpr (kBulk) {
+            if (tid == 0) bulk_wait_read<0>();  // the copy of step t - 2's buffer has read it
+        }
         if (a.scheme == 0 && ((t - 1) & 31) == 0) {
             const uint4 w = philox4x32_10(make_uint4((uint32_t)(t + (tid & 31)), 0u, kStreamResample, 0u), key);
             nu_lane = u01_open(w.x);
         }
         if (resample) {
+            // x_{t-1} is already in shared buffer (t - 1) & 1 for bulk-copied slices
+            if constexpr (!kBulk)
 #pragma unroll
             for (int p = 0; p < P; ++p)
                 if (j0 + p < M) {
@@ -964,13 +1017,14 @@ __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, cons
                             const float4 v = st4[gather_f4<P, DX, DL, G>(anc[p], gl, k / 4)];
                             x[p][k] = v.x; x[p][k + 1] = v.y; x[p][k + 2] = v.z; x[p][k + 3] = v.w;
                         }
+                    } else if constexpr (kBulk) {
+                        read_staged<DX, DL>((t & 1) ? sbuf0 : sbuf1, slice_row<DX, G>(anc[p], swz), gl, x[p]);
                     } else {
                         read_staged<DX, DL>(xstage, gather_slot<P, DX, G>(anc[p]), gl, x[p]);
                     }
                 }
                 lw[p] = (j0 + p < M) ? 0.f : -INFINITY;
             }
-            Lprev = logM;
         }
         // flag bit 0: resampled before step t; bit 1: some parent got more than
         // kWalkMaxOffspring offspring (the adjoint then uses the balanced gather adjoint)
@@ -997,31 +1051,53 @@ __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, cons
         }
         // with kc = 1 every state slice is stored: issue the stores before the reduction's
         // barriers so that they drain while the block synchronises
-        if (store && a.kc == 1) {
+        if (!kBulk && store && a.kc == 1) {
             const float nolw[P] = {};
             store_state<P, DX, DL>(tr.x_ck(t), nullptr, j0, gl, M, x, nolw);
         }
         float m, s1, s2;
         block_lse3<P>(lw, lead, red + (t & 1) * 32, red + 64 + (t & 1), m, s1, s2);
+        if constexpr (kBulk) {
+            // x_{t-1} (written by every thread before this step's barriers) to its slot
+            if (tid == 0 && store && ckslot(t - 1) >= 0) {
+                bulk_copy_s2g(tr.x_ck(ckslot(t - 1)), (t & 1) ? sbuf0 : sbuf1, slice_bytes);
+                bulk_commit();
+            }
+        }
         if (!(isfinite(m) && isfinite(s1) && s1 > 0.f)) {
             dead = true;
             break;
         }
-        const float ls1 = logf(s1);
 #pragma unroll
         for (int p = 0; p < P; ++p) lw[p] -= m;
-        Lprev = ls1;
         resample = (t < T) && (s1 * s1 < a.ess_frac * (float)M * s2);
         if (tid == 0) {  // per-step scalars: the adjoint's and the log-likelihood sum's inputs
             a.mstep[(size_t)f * (T + 1) + t] = m;
-            a.lstep[(size_t)f * (T + 1) + t] = ls1;
+            a.lstep[(size_t)f * (T + 1) + t] = logf(s1);
         }
         if (store) {
             // with kc = 1 the adjoint reads log w only at steps followed by resampling and at T
             if (a.kc == 1) {
                 if ((resample || t == T) && lead) store_run<P>(tr.lw_ck(t), j0, M, lw);
-            } else if (t % a.kc == 0 && t < T)
-                store_state<P, DX, DL>(tr.x_ck(t / a.kc), tr.lw_ck(t / a.kc), j0, gl, M, x, lw);
+            } else if (t % a.kc == 0 && t < T) {
+                if constexpr (kBulk) store_run<P>(tr.lw_ck(t / a.kc), j0, M, lw);
+                else store_state<P, DX, DL>(tr.x_ck(t / a.kc), tr.lw_ck(t / a.kc), j0, gl, M, x, lw);
+            }
+        }
+        if constexpr (kBulk) {
+            stage_x_rows<P, DX, DL>((t & 1) ? sbuf1 : sbuf0, j0, M, x);
+            fence_proxy_async_shared();
+        }
+    }
+    if constexpr (kBulk) {
+        // the last slice, then every copy complete before the buffers serve the next filter
+        __syncthreads();
+        if (tid == 0) {
+            if (store && !dead && ckslot(T) >= 0) {
+                bulk_copy_s2g(tr.x_ck(ckslot(T)), (T & 1) ? sbuf1 : sbuf0, slice_bytes);
+                bulk_commit();
+            }
+            bulk_wait<0>();
         }
     }
     // log p-hat = sum_t (m_t + log s1_t - L_{t-1}) accumulated in FP64 by warp 0 from the
@@ -1058,6 +1134,7 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     const int gl = (G > 1) ? (tid & (G - 1)) : 0;
     const int M = a.M, T = a.T, kc = a.kc;
+    const bool swz = swizzled_slices(G, DX, M);  // row order of the stored slices (slice_row)
     float* xstage = reinterpret_cast<float*>(smem + L.xstage);
     float* segw = reinterpret_cast<float*>(smem + L.starts);
     uint16_t* ancbuf = reinterpret_cast<uint16_t*>(smem + L.marks);  // two tape-row buffers
@@ -1196,9 +1273,12 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
         const int scheme = a.scheme;
         const bool walk_rows = kGatherWalk<G, DX> && a.offs != nullptr;
         const float* yrow = a.y + (size_t)(t1 - 1) * DY + (G > 1 ? gl * DL : 0);
-        int jc[P];  // own rows, clamped (padding particles read the last row)
+        int jc[P], jr[P];  // own particles, clamped (padding particles read the last row); their slice rows
 #pragma unroll
-        for (int p = 0; p < P; ++p) jc[p] = min(j0 + p, M - 1);
+        for (int p = 0; p < P; ++p) {
+            jc[p] = min(j0 + p, M - 1);
+            jr[p] = slice_row<DX, G>(jc[p], swz);
+        }
         uint8_t fb_next = t1 > t0 ? flags[t1 - 1] : (uint8_t)0;
         for (int k = 0; k < Ls - 1; ++k) {
             const int t = t1 - k;
@@ -1228,7 +1308,7 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
                 load_own_1d<P, DL>(sx, j0, M, xt);
             } else {
 #pragma unroll
-                for (int p = 0; p < P; ++p) read_staged<DX, DL>(sx, jc[p], gl, xt[p]);
+                for (int p = 0; p < P; ++p) read_staged<DX, DL>(sx, jr[p], gl, xt[p]);
             }
             const float* yt = yrow;
             yrow -= DY;
@@ -1236,7 +1316,7 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
 #pragma unroll
             for (int p = 0; p < P; ++p)
                 if constexpr (!Mdl::kFused) Mdl::bwd_obs(prm, xt[p], yt, lwbar[p], xbar[p], thb);
-            int ai[P];
+            int ai[P], ar[P];  // ancestors (own particles without resampling) and their slice rows
             const uint16_t* ancs = ancbuf + (nres & 1u) * (uint32_t)tape_stride(M);
             if (fl) {
                 // the prefetched tape row and log-weights have landed (each thread waits for
@@ -1254,9 +1334,14 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
 #pragma unroll
                     for (int p = 0; p < P; ++p) ai[p] = min((int)ancs[jc[p]], M - 1);
                 }
+#pragma unroll
+                for (int p = 0; p < P; ++p) ar[p] = slice_row<DX, G>(ai[p], swz);
             } else {
 #pragma unroll
-                for (int p = 0; p < P; ++p) ai[p] = jc[p];
+                for (int p = 0; p < P; ++p) {
+                    ai[p] = jc[p];
+                    ar[p] = jr[p];
+                }
             }
             float xp[P][DL];
             if constexpr (DX == 1 && G == 1) {
@@ -1268,7 +1353,7 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
                 }
             } else {
 #pragma unroll
-                for (int p = 0; p < P; ++p) read_staged<DX, DL>(sp, ai[p], gl, xp[p]);
+                for (int p = 0; p < P; ++p) read_staged<DX, DL>(sp, ar[p], gl, xp[p]);
             }
 #pragma unroll
             for (int p = 0; p < P; ++p) {
@@ -1315,7 +1400,7 @@ __device__ void backward_filter(const PFArgs& a, int f, unsigned char* smem, con
 #pragma unroll
             for (int p = 0; p < P; ++p) {
                 float x0[DL];
-                read_staged<DX, DL>(s0, min(j0 + p, M - 1), gl, x0);
+                read_staged<DX, DL>(s0, slice_row<DX, G>(min(j0 + p, M - 1), swz), gl, x0);
                 if (j0 + p < M) Mdl::bwd_init(prm, x0, xbar[p], thb);
             }
         }
