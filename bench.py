@@ -64,6 +64,7 @@ def _args():
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU baseline sample")
     p.add_argument("--cpu-procs", type=int, default=0, help="oracle processes (0: all host cores)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-serving", action="store_true", help="skip the short serving comparison of the line")
     p.add_argument("--N", type=int, default=0, help="override the number of samples (profiling runs)")
     p.add_argument("--no-autotune", action="store_true", help="use the default launch configuration")
     p.add_argument("--hmc-steps", type=int, default=0,
@@ -391,6 +392,8 @@ def run_gpu(a, rank, world, local):
         "clocks": clocks,
         "gpu_launches": int(launches),
     }
+    if not a.no_serving and world == 1:
+        out["serving"] = serving_leg()
     if not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_line(w, a.cpu_seconds, a.cpu_procs or None)
     if world > 1:
@@ -446,6 +449,74 @@ def run_reference(a, rank, world):
     }
 
 
+def _serve_jobs(jobs, arrivals, mode, budget, max_active=16):
+    """Submit the jobs at the given arrival times (seconds from the start) to a server in one
+    mode: 'fused' (ready jobs step together, filter passes of jobs of one kernel variant in one
+    persistent launch), 'streams' (every job on its own stream) or 'serial' (one job at a time).
+    Returns (latencies [s], makespan [s])."""
+    import numpy as np
+    from paper_2407_17296_gb300 import binding
+    lat = np.zeros(len(jobs))
+    with binding.Server(budget, 1 if mode == "serial" else max_active) as srv:
+        srv.set_fused(mode == "fused")
+        ids = [None] * len(jobs)
+        done = 0
+        nxt = 0
+        t0 = time.perf_counter()
+        while done < len(jobs):
+            now = time.perf_counter() - t0
+            while nxt < len(jobs) and arrivals[nxt] <= now:
+                ids[nxt] = srv.submit(binding.config_for(jobs[nxt]))
+                nxt += 1
+            for j in range(nxt):
+                if ids[j] is not None:
+                    r = srv.poll(ids[j])
+                    if r is not None:
+                        if r["status"] != 0:
+                            raise RuntimeError(f"served job {j} failed: {r['status']}")
+                        lat[j] = r["latency_s"]
+                        ids[j] = None
+                        done += 1
+            time.sleep(0.0005)
+        makespan = time.perf_counter() - t0
+    return lat, makespan
+
+
+def _mode_line(jobs, lat, span):
+    import numpy as np
+    work = float(sum(w.N * w.M * w.T * w.K for w in jobs))
+    return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "particle_steps_per_s": work / span, "makespan_s": span}
+
+
+def serving_leg(n_jobs=48, iters=2, ensemble=32):
+    """Short serving comparison for the benchmark line, all jobs submitted at once (capacity):
+    (1) the first n_jobs of the served mix (families lg1/lg4/sv/lg16, T ~ U[50, 1000],
+    N in {256, 1024, 4096}, M in {128, 512, 2048}); (2) `ensemble` replicate runs of the small
+    linear-Gaussian job (N=64, M=128, T=100, 10 iterations, own seeds), the case one job alone
+    leaves most of the GPU idle; each in the three server modes."""
+    import numpy as np
+    import torch
+    from dataclasses import replace
+    from paper_2407_17296_gb300 import workloads
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(0.8 * free)
+    mix = [replace(wl, K=iters) for _, wl in workloads.serving_stream(n_jobs=n_jobs, rate_hz=1.0)]
+    ens = [replace(workloads.lg1(), seed=5000 + r) for r in range(ensemble)]
+    out = {"workload": f"{n_jobs} jobs of the served mix, {iters} SMC2 iterations each, all submitted at once; "
+                       f"{ensemble} replicate runs of lg1 (N=64, M=128, T=100, 10 iterations)",
+           "max_active": 16}
+    for name, jobs, mx in (("mix", mix, 16), ("ensemble", ens, ensemble)):
+        res = {}
+        for mode in ("fused", "streams", "serial"):
+            lat, span = _serve_jobs(jobs, np.zeros(len(jobs)), mode, budget, mx)
+            res[mode] = _mode_line(jobs, lat, span)
+        res["fused_over_serial_throughput"] = res["fused"]["particle_steps_per_s"] / res["serial"]["particle_steps_per_s"]
+        res["fused_over_streams_throughput"] = res["fused"]["particle_steps_per_s"] / res["streams"]["particle_steps_per_s"]
+        out[name] = res
+    return out
+
+
 def run_serve(a):
     """256 jobs of the four model families with T ~ U[50, 1000], N in {256, 1024, 4096},
     M in {128, 512, 2048}, Poisson arrivals.
@@ -464,63 +535,34 @@ def run_serve(a):
     jobs = []
     for t, wl in stream:
         jobs.append((t, replace(wl, K=a.serve_iters)))
-    work = [wl.N * wl.M * wl.T * wl.K for _, wl in jobs]
     free, _ = torch.cuda.mem_get_info()
     budget = int(0.8 * free)
 
-    def run(arrivals, max_active):
-        lat = np.zeros(len(jobs))
-        with binding.Server(budget, max_active) as srv:
-            ids = [None] * len(jobs)
-            done = 0
-            nxt = 0
-            t0 = time.perf_counter()
-            while done < len(jobs):
-                now = time.perf_counter() - t0
-                while nxt < len(jobs) and arrivals[nxt] <= now:
-                    ids[nxt] = srv.submit(binding.config_for(jobs[nxt][1]))
-                    nxt += 1
-                for j in range(nxt):
-                    if ids[j] is not None:
-                        r = srv.poll(ids[j])
-                        if r is not None:
-                            if r["status"] != 0:
-                                raise RuntimeError(f"served job {j} failed: {r['status']}")
-                            lat[j] = r["latency_s"]
-                            ids[j] = None
-                            done += 1
-                time.sleep(0.0005)
-            makespan = time.perf_counter() - t0
-        return lat, makespan
-
-    sat_lat, sat_span = run(np.zeros(len(jobs)), 16)
+    wls = [wl for _, wl in jobs]
+    sat = {m: _serve_jobs(wls, np.zeros(len(jobs)), m, budget) for m in ("fused", "streams", "serial")}
+    sat_span = sat["fused"][1]
     capacity = len(jobs) / sat_span
     base = np.array([t for t, _ in jobs])
-    total = float(sum(work))
 
     def at_load(load):
         lam = load * capacity
         arrivals = base * (1.0 / lam) / (base[-1] / len(jobs))  # same Poisson pattern at rate lam
-        b_lat, b_span = run(arrivals, 16)
-        s_lat, s_span = run(arrivals, 1)
-        return {"load": load, "arrival_rate_jobs_per_s": lam,
-                "batched": {"p50_s": float(np.percentile(b_lat, 50)), "p99_s": float(np.percentile(b_lat, 99)),
-                            "particle_steps_per_s": total / b_span, "makespan_s": b_span, "max_active": 16},
-                "serial": {"p50_s": float(np.percentile(s_lat, 50)), "p99_s": float(np.percentile(s_lat, 99)),
-                           "particle_steps_per_s": total / s_span, "makespan_s": s_span, "max_active": 1}}
+        res = {"load": load, "arrival_rate_jobs_per_s": lam}
+        for mode in ("fused", "streams", "serial"):
+            lat, span = _serve_jobs(wls, arrivals, mode, budget)
+            res[mode] = {**_mode_line(wls, lat, span), "max_active": 1 if mode == "serial" else 16}
+        return res
 
     loads = [at_load(a.serve_load)] + ([at_load(1.0)] if a.serve_load != 1.0 else [])
     out = {
-        "metric": "served-job latency p50/p99 and particle-steps/s, batched vs serial",
+        "metric": "served-job latency p50/p99 and particle-steps/s: fused batching, per-job streams, serial",
         "workload": f"{len(jobs)} jobs, families lg1/lg4/sv/lg16, T~U[50,1000], N in {{256,1024,4096}}, "
                     f"M in {{128,512,2048}}, {a.serve_iters} SMC2 iterations per job, Poisson arrivals",
         "capacity_jobs_per_s": capacity,
-        "saturated_batched": {"particle_steps_per_s": total / sat_span, "makespan_s": sat_span},
+        "saturated": {m: _mode_line(wls, *sat[m]) for m in sat},
         "hbm_budget_bytes": budget,
         "loads": loads,
     }
-    # the first load's figures at the top level (the headline comparison)
-    out.update({k: loads[0][k] for k in ("load", "arrival_rate_jobs_per_s", "batched", "serial")})
     return out
 
 

@@ -207,6 +207,29 @@ int smc2_step_filters(smc2_handle* h, int row0, int n, double* loglik_dev, doubl
 int smc2_step_update(smc2_handle* h, const double* loglik_all_dev, const double* grad_all_dev,
                      smc2_stats* out);
 
+/*
+ * Fused iterations of several jobs (persistent multi-job filter kernels).  smc2_batch_step runs
+ * one SMC^2 iteration of each of the n handles, exactly as smc2_step on each would (the same
+ * results, bit for bit), but the particle-filter passes of handles that share a kernel variant
+ * (model shape, particles per thread, register cap), a block size and an adjoint ring are fused
+ * into one forward and one adjoint launch over all their filters: a persistent grid whose blocks
+ * take (job, filter) items from a device counter, longest filters first, so jobs of different
+ * T, N, parameters and data fill the GPU together (Table I: the filters of an iteration are the
+ * O(N/P) work).  Each handle's proposal and update run on its own stream; a group's fused passes
+ * run on the stream of its longest job, which first waits for the others' proposals, and their
+ * streams wait for the passes.  A handle alone in its group, and an HMC move after the first
+ * iteration (its leapfrog points need several filter passes), step as smc2_step does.
+ * stats: [n] caller storage or NULL; the call synchronises every handle's stream.
+ * smc2_batch_create allocates the device descriptors for up to max_jobs handles (1..4096) on the
+ * current device; a batch serves one call at a time.  Errors: SMC2_E_INVAL (n outside
+ * [0, max_jobs], NULL or repeated handles, a split step pending), SMC2_E_NOMEM, SMC2_E_CUDA,
+ * SMC2_E_TIMEOUT as smc2_step.
+ */
+typedef struct smc2_batch smc2_batch;
+int smc2_batch_create(int max_jobs, smc2_batch** out);
+int smc2_batch_step(smc2_batch* b, smc2_handle* const* handles, int n, smc2_stats* stats);
+int smc2_batch_destroy(smc2_batch* b);
+
 /* Copy the current samples to host: theta_host [N][D] and logw_host [N] (either may be NULL). */
 int smc2_get_samples(smc2_handle* h, double* theta_host, double* logw_host);
 
@@ -355,6 +378,12 @@ typedef struct smc2_result {
  * different jobs overlap on the GPU.  A worker thread drives the loop.
  */
 int smc2_server_create(size_t hbm_budget, int max_active, smc2_server** out);
+
+/* Fused batching on (default) or off: with it on, the jobs ready for their next iteration at the
+ * same moment step together through smc2_batch_step (their filter passes fused into persistent
+ * multi-job launches where they share a kernel variant and block size); off, every job steps on
+ * its own stream.  Results are the same either way.  Errors: SMC2_E_INVAL. */
+int smc2_server_set_fused(smc2_server* s, int on);
 
 /* Queue a job (cfg and y are copied; cfg->K_iters iterations).  Returns immediately.
  * SMC2_E_NOMEM only if the job can never fit the budget. */

@@ -27,7 +27,8 @@ EXPORTS = ("smc2_config_init", "smc2_create", "pf_loglik_grad", "pf_loglik_grad_
            "smc2_get_trace", "smc2_set_observations", "smc2_footprint", "smc2_destroy",
            "smc2_autotune", "smc2_get_launch", "smc2_set_launch", "smc2_get_status", "smc2_selftest_bounded_wait", "smc2_kernel_launches", "smc2_last_error", "smc2_server_create",
            "smc2_submit", "smc2_poll", "smc2_cancel", "smc2_server_destroy",
-           "pf_loglik_grad_static", "pf_static_get_status", "smc2_get_stream", "smc2_selftest_crn")
+           "pf_loglik_grad_static", "pf_static_get_status", "smc2_get_stream", "smc2_selftest_crn",
+           "smc2_batch_create", "smc2_batch_step", "smc2_batch_destroy", "smc2_server_set_fused")
 
 
 class Config(ctypes.Structure):
@@ -145,6 +146,10 @@ def load(path: str = LIB_PATH):
         "pf_static_get_status": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
         "smc2_get_stream": (ctypes.c_int, [vp, ctypes.POINTER(vp)]),
         "smc2_selftest_crn": (ctypes.c_int, [vp, vp, ctypes.c_int, vp, vp, vp, vp]),
+        "smc2_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(vp)]),
+        "smc2_batch_step": (ctypes.c_int, [vp, ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(Stats)]),
+        "smc2_batch_destroy": (ctypes.c_int, [vp]),
+        "smc2_server_set_fused": (ctypes.c_int, [vp, ctypes.c_int]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -368,6 +373,48 @@ class Handle:
         check(self.lib.smc2_set_observations(self.h, _ptr(ya)), "smc2_set_observations")
 
 
+class Batch:
+    """Fused iterations of several handles (smc2_batch_create / smc2_batch_step)."""
+
+    def __init__(self, max_jobs: int):
+        self.lib = load()
+        b = ctypes.c_void_p()
+        check(self.lib.smc2_batch_create(int(max_jobs), ctypes.byref(b)), "smc2_batch_create")
+        self.b = b
+
+    def step(self, handles, want_means=True):
+        """One SMC^2 iteration of every handle (fused filter passes); list of stats dicts."""
+        import numpy as np
+        n = len(handles)
+        arr = (ctypes.c_void_p * max(n, 1))(*[h.h.value for h in handles])
+        st = (Stats * max(n, 1))()
+        means = []
+        for i, h in enumerate(handles):
+            m, r = np.zeros(h.D), np.zeros(h.D)
+            if want_means:
+                st[i].mean, st[i].recycled_mean = m.ctypes.data, r.ctypes.data
+            means.append((m, r))
+        check(self.lib.smc2_batch_step(self.b, arr, n, st), "smc2_batch_step")
+        return [_stats_dict(st[i], means[i][0], means[i][1]) for i in range(n)]
+
+    def close(self):
+        if getattr(self, "b", None) is not None and self.b.value:
+            check(self.lib.smc2_batch_destroy(self.b), "smc2_batch_destroy")
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
 class Server:
     """Continuous-batching request loop (smc2_server_create ... smc2_server_destroy)."""
 
@@ -379,6 +426,10 @@ class Server:
         self.s = s
         self.D = {}
         self.N = {}
+
+    def set_fused(self, on=True):
+        """Fused batching of ready jobs (default) or one stream a job."""
+        check(self.lib.smc2_server_set_fused(self.s, 1 if on else 0), "smc2_server_set_fused")
 
     def submit(self, cfg: Config) -> int:
         jid = ctypes.c_uint64(0)

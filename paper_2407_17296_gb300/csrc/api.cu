@@ -35,6 +35,16 @@ pf_kernel_fn lookup_lg16_fwd(int P, int regs);
 pf_kernel_fn lookup_lg16_bwd(int P, int regs);
 pf_kernel_fn lookup_opt_fwd(int P, int regs);
 pf_kernel_fn lookup_opt_bwd(int P, int regs);
+pf_multi_fn lookup_lg1_fwd_multi(int P, int regs);
+pf_multi_fn lookup_lg1_bwd_multi(int P, int regs);
+pf_multi_fn lookup_lg4_fwd_multi(int P, int regs);
+pf_multi_fn lookup_lg4_bwd_multi(int P, int regs);
+pf_multi_fn lookup_sv_fwd_multi(int P, int regs);
+pf_multi_fn lookup_sv_bwd_multi(int P, int regs);
+pf_multi_fn lookup_lg16_fwd_multi(int P, int regs);
+pf_multi_fn lookup_lg16_bwd_multi(int P, int regs);
+pf_multi_fn lookup_opt_fwd_multi(int P, int regs);
+pf_multi_fn lookup_opt_bwd_multi(int P, int regs);
 }  // namespace smc2
 
 using namespace smc2;
@@ -114,6 +124,26 @@ pf_kernel_fn smc2::lookup_backward(const smc2_config* c, int P, int regs) {
     if (c->d_x == 1) return lookup_lg1_bwd(P, regs);
     if (c->d_x == 4) return lookup_lg4_bwd(P, regs);
     if (c->d_x == 16) return lookup_lg16_bwd(P, regs);
+    return nullptr;
+}
+
+pf_multi_fn smc2::lookup_forward_multi(const smc2_config* c, int P, int regs) {
+    if (!variant_fits(c, P, regs, true)) return nullptr;
+    if (c->model_family == SMC2_SV) return lookup_sv_fwd_multi(P, regs);
+    if (c->model_family == SMC2_LG_OPT) return lookup_opt_fwd_multi(P, regs);
+    if (c->d_x == 1) return lookup_lg1_fwd_multi(P, regs);
+    if (c->d_x == 4) return lookup_lg4_fwd_multi(P, regs);
+    if (c->d_x == 16) return lookup_lg16_fwd_multi(P, regs);
+    return nullptr;
+}
+
+pf_multi_fn smc2::lookup_backward_multi(const smc2_config* c, int P, int regs) {
+    if (!variant_fits(c, P, regs, false)) return nullptr;
+    if (c->model_family == SMC2_SV) return lookup_sv_bwd_multi(P, regs);
+    if (c->model_family == SMC2_LG_OPT) return lookup_opt_bwd_multi(P, regs);
+    if (c->d_x == 1) return lookup_lg1_bwd_multi(P, regs);
+    if (c->d_x == 4) return lookup_lg4_bwd_multi(P, regs);
+    if (c->d_x == 16) return lookup_lg16_bwd_multi(P, regs);
     return nullptr;
 }
 
@@ -649,7 +679,7 @@ OuterArgs smc2::make_outer_args(smc2_handle* h) {
 
 // Kernel launches of one iteration after the first: propose, the filter passes of every
 // leapfrog point (one point for RW and Langevin), the leapfrog kicks between them, update.
-static int launches_per_step(const smc2_handle* h) {
+int smc2::launches_per_step(const smc2_handle* h) {
     const int L = h->cfg.proposal == SMC2_HMC ? h->cfg.hmc_steps : 1;
     return 1 + L * filter_launches(h, h->cfg.N, true) + (L - 1) + kOuterUpdateLaunches;
 }

@@ -140,6 +140,22 @@ SMC2_HD inline int pf_threads(int M, int P, int G = 1) {
 // particles (0 if none, -1 if the query failed).
 typedef int (*pf_kernel_fn)(const PFArgs& a, void* stream, int grid);
 
+// Work list of a multi-job launch (persistent kernels over the filters of several jobs that
+// share a model shape and launch variant): job j's filters are items first[j] .. first[j+1]-1;
+// every block takes the next item from the device counter *head (zero before the launch) until
+// none is left.  Jobs are listed longest first, so the long filters start first.
+struct MultiArgs {
+    const PFArgs* jobs;  // device [n_jobs] launch arguments of each job (its own buffers, sizes, keys)
+    const int* first;    // device [n_jobs + 1], first[0] = 0, first[n_jobs] = n_items
+    int n_jobs, n_items;
+    int* head;           // device work counter
+    int M_max;           // largest M: the block size and shared-memory plan of the launch
+    int R;               // adjoint: ring slots shared by every job of the launch
+};
+
+// Host-side launcher of a multi-job pass: grid 0 queries the blocks of one SM as pf_kernel_fn.
+typedef int (*pf_multi_fn)(const MultiArgs& m, void* stream, int grid);
+
 // A launch choice: particles per thread and register cap of each pass, checkpoint interval.
 struct LaunchChoice {
     int pf = 4, rf = 128, pb = 4, rb = 128, kc = 1;

@@ -1529,6 +1529,141 @@ int launch_backward(const PFArgs& a, void* stream, int grid) {
     return (int)cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- multi-job persistent kernels
+//
+// One launch over the filters of several jobs (MultiArgs): a grid of (SMs x resident blocks)
+// blocks, each taking the next (job, filter) item from a device counter until the list is
+// exhausted, so jobs of different T, N, seeds, parameters and data fill the GPU together and a
+// block that finishes a short filter starts the next item at once.  Each item runs exactly the
+// per-filter code of the single-job kernels with its own job's arguments (copied into shared
+// memory), so every filter's result is bit-identical to its job's own launch.  The block size is
+// the one of the largest M in the list (smaller jobs leave their surplus threads as padding
+// particles); the adjoint's ring barriers sit in static shared memory, since the plan's offsets
+// depend on M.
+
+// thread 0: next item, its job (binary search over first[]) and that job's arguments into sa;
+// returns false (in every thread) once the list is exhausted.  One __syncthreads.
+__device__ __forceinline__ bool next_item(const MultiArgs& m, PFArgs& sa, int* s_item, int& f) {
+    if (threadIdx.x == 0) {
+        const int i = atomicAdd(m.head, 1);
+        if (i < m.n_items) {
+            int lo = 0, hi = m.n_jobs - 1;  // largest j with first[j] <= i
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (m.first[mid] <= i) lo = mid;
+                else hi = mid - 1;
+            }
+            sa = m.jobs[lo];
+            s_item[0] = i;
+            s_item[1] = i - m.first[lo];
+        } else {
+            s_item[0] = m.n_items;
+        }
+    }
+    __syncthreads();
+    f = s_item[1];
+    return s_item[0] < m.n_items;
+}
+
+template <class Mdl, int P, int REGS>
+__global__ void __maxnreg__(REGS) pf_forward_multi_kernel(MultiArgs m) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ typename Mdl::Params sprm;
+    __shared__ PFArgs sa;
+    __shared__ int s_item[2];
+    int f = 0;
+    while (next_item(m, sa, s_item, f)) {
+        const SmemLayout L(sa.M, Mdl::DX, Mdl::D, true, Mdl::G);
+        forward_filter<Mdl, P>(sa, f, smem, L, sprm);
+        __syncthreads();  // every thread is done with sa and the shared buffers
+    }
+}
+
+template <class Mdl, int P, int R>
+__device__ void backward_multi(const MultiArgs& m, unsigned char* smem, typename Mdl::Params& sprm, PFArgs& sa,
+                               int* s_item, uint64_t* bars) {
+    SliceRing<(R > 0 ? R : 1), Mdl::DX> ring;
+    ring.slots = reinterpret_cast<float*>(smem);  // the plan's first region for every M
+    ring.full = bars;
+    if constexpr (R > 0) {
+        if (threadIdx.x == 0) {
+            for (int r = 0; r < R; ++r) {
+                mbar_init(&ring.full[r], 1);
+                mbar_init(&ring.full[R + r], blockDim.x >> 5);
+            }
+            mbar_fence_init();
+        }
+    }
+    __syncthreads();
+    uint32_t g = 0;
+    int f = 0;
+    while (next_item(m, sa, s_item, f)) {
+        const SmemLayout L(sa.M, Mdl::DX, Mdl::D, false, Mdl::G, R);
+        ring.M = sa.M;  // slot size of this job's slices
+        backward_filter<Mdl, P, R>(sa, f, smem, L, sprm, ring, g);
+        // the next item's plan may place ring slots (filled by bulk copies) where this one wrote
+        // with ordinary stores
+        fence_proxy_async_shared();
+        __syncthreads();
+    }
+}
+
+template <class Mdl, int P, int REGS>
+__global__ void __maxnreg__(REGS) pf_backward_multi_kernel(MultiArgs m) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ typename Mdl::Params sprm;
+    __shared__ PFArgs sa;
+    __shared__ int s_item[2];
+    constexpr int Ra = ring_preferred(Mdl::DX), Rb = ring_fallback(Mdl::DX);
+    __shared__ uint64_t bars[2 * (Ra > Rb ? Ra : (Rb > 0 ? Rb : 1))];
+    if constexpr (Ra == Rb) {
+        backward_multi<Mdl, P, Ra>(m, smem, sprm, sa, s_item, bars);
+    } else {
+        if (m.R == Ra) backward_multi<Mdl, P, Ra>(m, smem, sprm, sa, s_item, bars);
+        else backward_multi<Mdl, P, Rb>(m, smem, sprm, sa, s_item, bars);
+    }
+}
+
+template <class Mdl, int P, int REGS>
+int launch_forward_multi(const MultiArgs& m, void* stream, int grid) {
+    const int threads = pf_threads(m.M_max, P, Mdl::G);
+    const size_t smem = SmemLayout(m.M_max, Mdl::DX, Mdl::D, true, Mdl::G).total;
+    if (threads > kMaxThreads) return grid ? -1 : 0;
+    const size_t stat = sizeof(typename Mdl::Params) + sizeof(PFArgs) + 64;
+    if (smem + stat > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(pf_forward_multi_kernel<Mdl, P, REGS>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) {
+            if (grid) return (int)e;
+            cudaGetLastError();
+            return -1;
+        }
+    }
+    if (grid == 0) return blocks_per_sm(pf_forward_multi_kernel<Mdl, P, REGS>, threads, smem);
+    pf_forward_multi_kernel<Mdl, P, REGS><<<grid, threads, smem, static_cast<cudaStream_t>(stream)>>>(m);
+    return (int)cudaGetLastError();
+}
+
+template <class Mdl, int P, int REGS>
+int launch_backward_multi(const MultiArgs& m, void* stream, int grid) {
+    const int threads = pf_threads(m.M_max, P, Mdl::G);
+    const size_t smem = SmemLayout(m.M_max, Mdl::DX, Mdl::D, false, Mdl::G, m.R).total;
+    if (threads > kMaxThreads) return grid ? -1 : 0;
+    const size_t stat = sizeof(typename Mdl::Params) + sizeof(PFArgs) + 256;
+    if (smem + stat > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(pf_backward_multi_kernel<Mdl, P, REGS>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) {
+            if (grid) return (int)e;
+            cudaGetLastError();
+            return -1;
+        }
+    }
+    if (grid == 0) return blocks_per_sm(pf_backward_multi_kernel<Mdl, P, REGS>, threads, smem);
+    pf_backward_multi_kernel<Mdl, P, REGS><<<grid, threads, smem, static_cast<cudaStream_t>(stream)>>>(m);
+    return (int)cudaGetLastError();
+}
+
 // The launch variants compiled for every model: (particles per thread, register cap).
 #define SMC2_PF_VARIANTS(X) X(1, 64) X(1, 128) X(2, 64) X(2, 128) X(4, 64) X(4, 80) X(4, 128) X(8, 64) X(8, 128)
 

@@ -14,4 +14,13 @@ pf_kernel_fn lookup_lg16_bwd(int P, int regs) {
     return nullptr;
 }
 
+pf_multi_fn lookup_lg16_bwd_multi(int P, int regs) {
+    using Mdl = LGSplit<16, 4>;
+#define SMC2_CASE(PP, RR) \
+    if (P == PP && regs == RR) return &launch_backward_multi<Mdl, PP, RR>;
+    SMC2_PF_VARIANTS(SMC2_CASE)
+#undef SMC2_CASE
+    return nullptr;
+}
+
 }  // namespace smc2

@@ -14,4 +14,13 @@ pf_kernel_fn lookup_lg16_fwd(int P, int regs) {
     return nullptr;
 }
 
+pf_multi_fn lookup_lg16_fwd_multi(int P, int regs) {
+    using Mdl = LGSplit<16, 2>;
+#define SMC2_CASE(PP, RR) \
+    if (P == PP && regs == RR) return &launch_forward_multi<Mdl, PP, RR>;
+    SMC2_PF_VARIANTS(SMC2_CASE)
+#undef SMC2_CASE
+    return nullptr;
+}
+
 }  // namespace smc2

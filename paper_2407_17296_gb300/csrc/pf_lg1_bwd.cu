@@ -1,5 +1,6 @@
 // pf_lg1_bwd.cu -- backward-pass kernel variants for one model shape
-// (LGDiag<1, 1, true>).  One translation unit per model and pass so the build compiles in parallel.
+// (LGDiag<1, 1, true>).  One translation unit per model and pass so the build compiles in parallel; the
+// _multi lookup gives the persistent multi-job kernel of the same variant.
 #include "pf_kernels.cuh"
 
 namespace smc2 {
@@ -8,6 +9,15 @@ pf_kernel_fn lookup_lg1_bwd(int P, int regs) {
     using Mdl = LGDiag<1, 1, true>;
 #define SMC2_CASE(PP, RR) \
     if (P == PP && regs == RR) return &launch_backward<Mdl, PP, RR>;
+    SMC2_PF_VARIANTS(SMC2_CASE)
+#undef SMC2_CASE
+    return nullptr;
+}
+
+pf_multi_fn lookup_lg1_bwd_multi(int P, int regs) {
+    using Mdl = LGDiag<1, 1, true>;
+#define SMC2_CASE(PP, RR) \
+    if (P == PP && regs == RR) return &launch_backward_multi<Mdl, PP, RR>;
     SMC2_PF_VARIANTS(SMC2_CASE)
 #undef SMC2_CASE
     return nullptr;

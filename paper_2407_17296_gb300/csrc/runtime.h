@@ -31,6 +31,8 @@ int model_lanes(const smc2_config* c, bool forward);  // lanes per particle (G) 
 bool variant_fits(const smc2_config* c, int P, int regs, bool forward);  // block size and registers allow it
 pf_kernel_fn lookup_forward(const smc2_config* c, int P, int regs);
 pf_kernel_fn lookup_backward(const smc2_config* c, int P, int regs);
+pf_multi_fn lookup_forward_multi(const smc2_config* c, int P, int regs);
+pf_multi_fn lookup_backward_multi(const smc2_config* c, int P, int regs);
 int choose_kc(const smc2_config* c);
 // launch choice: explicit particles_per_thread / ckpt_every, else the autotuner's cached
 // choice for this shape, else a heuristic default
@@ -102,4 +104,8 @@ int enqueue_step(smc2_handle* h);
 int step_async(smc2_handle* h);
 int read_stats(smc2_handle* h, smc2_stats* out);
 int read_status(smc2_handle* h, int* status);
+int launches_per_step(const smc2_handle* h);
 }  // namespace smc2
+
+// One SMC^2 iteration of several handles with fused filter passes (batch.cu); enqueues only.
+int smc2_batch_step_async(smc2_batch* b, smc2_handle* const* hs, int n);

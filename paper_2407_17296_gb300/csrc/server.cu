@@ -6,14 +6,19 @@
 // max_active run; an admitted job keeps all of its state on the device and
 // advances one SMC^2 iteration at a time on its own stream, so iterations of
 // different jobs overlap on the GPU and a finished job frees its slot and memory
-// for the next arrival at once.  smc2_poll reports completion and hands back the
-// final samples, weights and the recycled posterior-mean estimate.
+// for the next arrival at once.  With fused batching (the default) the jobs that are
+// ready for their next iteration at the same moment step together through
+// smc2_batch_step: the filter passes of jobs that share a kernel variant and block size run
+// as one persistent multi-job launch (batch.cu), the rest of each iteration on the job's own
+// stream.  smc2_poll reports completion and hands back the final samples, weights and the
+// recycled posterior-mean estimate.
 //
 // Autotuner: for a model shape it times every supported particles-per-thread
 // value and a few checkpoint intervals on the current device with CUDA events
 // and caches the fastest choice in-process.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cstdint>
 #include <condition_variable>
@@ -65,6 +70,8 @@ struct smc2_server {
     std::vector<Job*> active;
     uint64_t next_id = 1;
     bool stop = false;
+    bool fused = true;              // ready jobs step together with fused filter passes
+    smc2_batch* batch = nullptr;    // descriptors of the fused launches (max_active jobs)
     std::thread worker;
 };
 
@@ -130,7 +137,9 @@ void worker_loop(smc2_server* s) {
             s->active.push_back(j);
             progressed = true;
         }
-        // advance every active job by one iteration when its previous one has finished
+        // advance every active job by one iteration when its previous one has finished: with
+        // fused batching, collect the ready jobs and step them together
+        std::vector<Job*> ready;
         for (size_t a = 0; a < s->active.size();) {
             Job* j = s->active[a];
             if (j->state == Job::kCancelled) {
@@ -161,6 +170,11 @@ void worker_loop(smc2_server* s) {
                 progressed = true;
                 continue;
             }
+            if (s->fused && s->batch) {
+                ready.push_back(j);
+                ++a;
+                continue;
+            }
             int rc = step_async(j->h);
             if (rc == SMC2_OK && cudaEventRecord(j->ev, j->h->stream) != cudaSuccess) rc = SMC2_E_CUDA;
             if (rc != SMC2_OK) {
@@ -171,6 +185,22 @@ void worker_loop(smc2_server* s) {
             j->in_flight = true;
             progressed = true;
             ++a;
+        }
+        if (!ready.empty()) {
+            std::vector<smc2_handle*> hs;
+            for (Job* j : ready) hs.push_back(j->h);
+            int rc = smc2_batch_step_async(s->batch, hs.data(), (int)hs.size());
+            for (Job* j : ready) {
+                int rj = rc;
+                if (rj == SMC2_OK && cudaEventRecord(j->ev, j->h->stream) != cudaSuccess) rj = SMC2_E_CUDA;
+                if (rj != SMC2_OK) {
+                    finish_job(s, j, rj);
+                    s->active.erase(std::find(s->active.begin(), s->active.end(), j));
+                    continue;
+                }
+                j->in_flight = true;
+            }
+            progressed = true;
         }
         if (!progressed) {
             if (s->active.empty() && s->pending.empty())
@@ -206,8 +236,16 @@ extern "C" int smc2_server_create(size_t hbm_budget, int max_active, smc2_server
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
     }
     cudaGetLastError();
+    if (smc2_batch_create(max_active, &s->batch) != SMC2_OK) s->batch = nullptr;  // per-job steps then
     s->worker = std::thread(worker_loop, s);
     *out = s;
+    return SMC2_OK;
+}
+
+extern "C" int smc2_server_set_fused(smc2_server* s, int on) {
+    if (!s) return fail(SMC2_E_INVAL, "NULL server");
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->fused = on != 0;
     return SMC2_OK;
 }
 
@@ -292,6 +330,7 @@ extern "C" int smc2_server_destroy(smc2_server* s) {
     }
     s->cv.notify_all();
     if (s->worker.joinable()) s->worker.join();
+    if (s->batch) smc2_batch_destroy(s->batch);
     delete s;
     return SMC2_OK;
 }

@@ -148,3 +148,13 @@ def test_stats_struct_carries_near_tie_counts():
     src = open(HEADER).read()
     for n in names:
         assert re.search(r"\b" + n + r"\s*;", src), n
+
+
+def test_batch_entry_points_validate_without_device_work(lib):
+    import ctypes as C
+    out = C.c_void_p()
+    assert lib.smc2_batch_create(0, C.byref(out)) == -1
+    assert lib.smc2_batch_create(5000, C.byref(out)) == -1
+    assert lib.smc2_batch_destroy(None) == -1
+    assert lib.smc2_batch_step(None, None, 1, None) == -1
+    assert lib.smc2_server_set_fused(None, 1) == -1

@@ -53,11 +53,15 @@ def _wait(server, ids, timeout=120.0):
     return out
 
 
-def test_results_alone_equal_results_in_the_mix():
+@pytest.mark.parametrize("fused", [True, False])
+def test_results_alone_equal_results_in_the_mix(fused):
+    """With fused batching (ready jobs step together, filter passes of jobs of one kernel variant
+    in one persistent launch) and without it (one stream a job)."""
     from paper_2407_17296_gb300 import binding
     jobs = _jobs()
     alone = [_alone(i, w) for i, w in enumerate(jobs)]
     with binding.Server(hbm_budget=8 << 30, max_active=8) as srv:
+        srv.set_fused(fused)
         ids = [srv.submit(_cfg(i, w)) for i, w in enumerate(jobs)]
         res = _wait(srv, ids)
     for w, j, (th, lw, rec) in zip(jobs, ids, alone):
