@@ -65,6 +65,10 @@ def _args():
     p.add_argument("--cpu-procs", type=int, default=0, help="oracle processes (0: all host cores)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-serving", action="store_true", help="skip the short serving comparison of the line")
+    p.add_argument("--mode", default="auto", choices=["auto", "sharded", "replicas"],
+                   help="several GPUs: one job whose rows are split over the ranks (sharded: N rows a rank, "
+                        "one all-gather of the filter outputs per iteration) or independent jobs (replicas); "
+                        "auto = sharded when the job's N x ranks fits a handle")
     p.add_argument("--N", type=int, default=0, help="override the number of samples (profiling runs)")
     p.add_argument("--no-autotune", action="store_true", help="use the default launch configuration")
     p.add_argument("--hmc-steps", type=int, default=0,
@@ -250,8 +254,18 @@ def run_gpu(a, rank, world, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     w = make_workload(a)
-    # weak scaling: every rank runs its own independent job (own seed), no data-path collective
-    w.seed = w.seed + 1000 * rank
+    mode = a.mode
+    if mode == "auto":
+        mode = "sharded" if world > 1 and w.N * world <= 16384 and w.proposal != "hmc" else "replicas"
+    if mode == "sharded":
+        # weak scaling of one job: N rows a rank of a job with N x ranks samples, the ranks
+        # exchanging the filter outputs (one all-gather) before every outer update
+        from dataclasses import replace
+        w = replace(w, N=w.N * world)
+        w.resample = a.resample
+    else:
+        # weak scaling: every rank runs its own independent job (own seed), no data-path collective
+        w.seed = w.seed + 1000 * rank
     binding.load()
     stream = torch.cuda.Stream(device=dev)
     cfg = binding.config_for(w, stream=stream.cuda_stream,
@@ -263,6 +277,8 @@ def run_gpu(a, rank, world, local):
         binding.autotune(cfg, workloads.thetas_near(w, w.N, 0.05, seed=5))
     h = binding.Handle(cfg)
     launch = h.launch()
+    if mode == "sharded":
+        return run_sharded(a, rank, world, dev, w, h, stream, launch)
     ps_launch = w.N * w.M * w.T  # particle-steps of one filter launch (one leapfrog point)
     ps_per_step = ps_launch * (w.hmc_steps if w.proposal == "hmc" else 1)
 
@@ -372,7 +388,7 @@ def run_gpu(a, rank, world, local):
                             f"fwd+adjoint at each point), L-kernel weights, resample"),
                    "dead_samples": dead,
                    "l2": "inputs larger than L2 (particle trajectory of several GB written and read per step)",
-                   "parallelism": f"replicas x{world} (independent jobs)"},
+                   "parallelism": f"replicas x{world} (independent jobs)" if world > 1 else "one job, one GPU"},
         "smc2_iters_per_s": 1e3 / ms_step,
         "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s",
                      "frac": achieved_tops / peak_tops if peak_tops else None, "traffic": traffic,
@@ -399,6 +415,100 @@ def run_gpu(a, rank, world, local):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+    return out
+
+
+def run_sharded(a, rank, world, dev, w, h, stream, launch):
+    """One SMC^2 job whose N x ranks filters are split over the ranks (sharded.py): each rank
+    filters its N rows, one NCCL all-gather of the filter outputs, the outer update everywhere.
+    value = filter particle-steps of the whole job per second (the max over ranks of the time)."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2407_17296_gb300 import binding, sharded
+    if world == 1 and not dist.is_initialized():
+        import socket
+        with socket.socket() as s_:
+            s_.bind(("127.0.0.1", 0))
+            port = s_.getsockname()[1]
+        dist.init_process_group("nccl", init_method=f"tcp://127.0.0.1:{port}", rank=0, world_size=1,
+                                device_id=dev)
+    eng = sharded.HandleEngine(h, stream)
+    drv = sharded.ShardedSMC2(eng, w.N, w.D)
+    with torch.cuda.stream(stream):
+        for _ in range(a.warmup):
+            drv.step()
+    torch.cuda.synchronize()
+    clk = ClockSampler(int(str(dev).split(":")[-1]) if ":" in str(dev) else 0)
+    clk.start()
+    time.sleep(0.3)
+    dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = binding.kernel_launches()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for k in range(a.steps):
+            evs[k][0].record(stream)
+            ll, g = eng.step_filters(drv.row0, drv.n)
+            evs[k][1].record(stream)
+            ll_all, g_all = drv._exchange(ll, g)
+            eng.step_update(ll_all, g_all)
+        ev1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    launches = binding.kernel_launches() - launches0
+    clocks = clk.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    pf_ms = float(np.mean([e0.elapsed_time(e1) for e0, e1 in evs]))
+    # end to end: observations in, statistics and the samples out, every step
+    y_host = torch.tensor(w.y, dtype=torch.float32).pin_memory().numpy()
+    dist.barrier()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for _ in range(a.steps):
+            h.set_observations(y_host)
+            drv.step()
+            h.samples()
+    e2e_s = time.perf_counter() - t0
+    times = torch.tensor([ms_total, e2e_s, pf_ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(times, op=dist.ReduceOp.MAX)
+    ms_total, e2e_s, pf_ms = float(times[0]), float(times[1]), float(times[2])
+    h.close()
+    if rank != 0:
+        dist.destroy_process_group()
+        return None
+    ps_step = w.N * w.M * w.T
+    props = torch.cuda.get_device_properties(dev)
+    max_mhz = clocks.get("sm_max_mhz") or 2070.0
+    peak_tops = world * props.multi_processor_count * 128 * max_mhz * 1e6 / 1e12
+    achieved = ALG_OPS.get(w.name, 0) * ps_step / (pf_ms / 1e3) / 1e12
+    out = {
+        "metric": METRIC, "value": ps_step * a.steps / (ms_total / 1e3), "unit": UNIT, "n_gpus": world,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_total / a.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded simulation of the model; no dataset)",
+        "config": {**workload_config(w),
+                   "launch": {"forward_ppt": launch[0], "forward_regs": launch[1], "adjoint_ppt": launch[2],
+                              "adjoint_regs": launch[3], "ckpt_every": launch[4]},
+                   "step": "one SMC2 iteration of one job: propose, each rank's N/ranks filters fwd+adjoint, "
+                           "all-gather of the filter outputs, L-kernel weights, resample",
+                   "l2": "inputs larger than L2 (particle trajectory of several GB written and read per step)",
+                   "parallelism": f"sharded x{world} (rows of one job split over the ranks, one NCCL "
+                                  f"all-gather of N x (1 + D) FP64 values per iteration)"},
+        "smc2_iters_per_s": 1e3 * a.steps / ms_total,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
+                     "frac": achieved / peak_tops, "traffic": None,
+                     "kernel": "pf_forward_kernel + pf_backward_kernel (each rank's rows, max over ranks)",
+                     "kernel_ms": pf_ms, "ops_per_particle_step": ALG_OPS.get(w.name),
+                     "peak_basis": f"{world} x {props.multi_processor_count} SMs x 128 lanes x {max_mhz:.0f} MHz"},
+        "e2e": {"value": ps_step * a.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(w.T * w.dy * 4),
+                "d2h_bytes_per_step": int(w.N * w.D * 8 + w.N * 8 + 8 * (6 + 2 * w.D))},
+        "clocks": clocks,
+        "gpu_launches": int(launches),
+    }
+    dist.destroy_process_group()
     return out
 
 

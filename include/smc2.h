@@ -117,6 +117,8 @@ typedef struct smc2_stats {
  * smc2_create: validate cfg, copy y and H, allocate the device-resident state of
  * one inference job (theta [N][D], log-weights, log pi-hat, gradients, particle
  * checkpoints and the ancestor tape).  The library owns every allocation it makes.
+ * Sizes: 1 <= N <= 16384 samples, 1 <= M <= 4096 particles (less where a model's block would
+ * not fit), T >= 1.
  * Errors: SMC2_E_INVAL (bad or unsupported cfg), SMC2_E_NOMEM, SMC2_E_CUDA.
  * Problem statement: Sec. II (f, g, y_{1:T}, M) and Sec. III (prior, N, step size).
  */

@@ -220,7 +220,7 @@ int smc2::validate(const smc2_config* c, int* D) {
     if (c->D != *D) return fail(SMC2_E_INVAL, "D does not match the model family");
     if (c->T < 1 || c->N < 1 || c->M < 1) return fail(SMC2_E_INVAL, "T, N and M must be positive");
     if (c->M > 4096) return fail(SMC2_E_INVAL, "M must be <= 4096");
-    if (c->N > 4096) return fail(SMC2_E_INVAL, "N must be <= 4096");
+    if (c->N > 16384) return fail(SMC2_E_INVAL, "N must be <= 16384");
     if (!c->y) return fail(SMC2_E_INVAL, "y is NULL");
     if (!(c->ess_frac >= 0.f && c->ess_frac <= 1.f)) return fail(SMC2_E_INVAL, "ess_frac must be in [0, 1]");
     if (c->pf_resample != SMC2_SYSTEMATIC && c->pf_resample != SMC2_MULTINOMIAL)

@@ -57,6 +57,9 @@ class ShardedSMC2:
     ``step_update(loglik [N], grad [N][D]) -> stats``) on every rank of `group`."""
 
     def __init__(self, engine, N: int, D: int, group=None, device=None):
+        """device: where the exchange buffers live -- the engine's device for NCCL (default),
+        the CPU for a gloo group (the rows then travel through host memory and are copied back
+        to the engine's device before the update)."""
         self.engine = engine
         self.N, self.D = N, D
         self.group = group
@@ -65,7 +68,8 @@ class ShardedSMC2:
         self.rows = [shard_rows(N, self.world, r) for r in range(self.world)]
         self.row0, self.n = self.rows[self.rank]
         self.nmax = max(n for _, n in self.rows)
-        self.device = device if device is not None else getattr(engine, "device", torch.device("cpu"))
+        self.engine_device = getattr(engine, "device", torch.device("cpu"))
+        self.device = device if device is not None else self.engine_device
         self.stream = getattr(engine, "stream", None)
 
     def _exchange(self, ll, g):
@@ -75,7 +79,7 @@ class ShardedSMC2:
         buf[:self.n, 1:] = g
         parts = [torch.empty_like(buf) for _ in range(self.world)]
         dist.all_gather(parts, buf, group=self.group)
-        rows = torch.cat([p[:n] for p, (_, n) in zip(parts, self.rows)], dim=0)
+        rows = torch.cat([p[:n] for p, (_, n) in zip(parts, self.rows)], dim=0).to(self.engine_device)
         return rows[:, 0].contiguous(), rows[:, 1:].contiguous()
 
     def step(self):

@@ -96,3 +96,35 @@ def test_sharded_driver_nccl_world_one():
             np.testing.assert_array_equal(th, th_ref)
     finally:
         dist.destroy_process_group()
+
+
+def test_two_processes_cuda_engine_gloo_exchange():
+    """Two processes, each a rank with its own handle on the same GPU (their kernels never wait
+    on one another), filter their halves of the rows; the rows are exchanged by a gloo
+    all-gather through host memory.  Both replicas equal one handle running smc2_step."""
+    import multiprocessing as mp
+    import socket
+    from .sharded_cuda_worker import worker
+    N, K = 24, 3
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=worker, args=(r, 2, port, N, K, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted([q.get(timeout=300) for _ in range(2)], key=lambda r: r[0])
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    for r in res:
+        assert r[1] >= 0, r[5]
+    assert [(r[1], r[2]) for r in res] == [shard_rows(N, 2, 0), shard_rows(N, 2, 1)]
+    w = workloads.lg4(T=30, N=N, M=256, K=K)
+    stats_ref, th_ref, lw_ref = _ref_run(w, K)
+    for r in res:
+        np.testing.assert_array_equal(r[3], th_ref)
+        np.testing.assert_array_equal(r[4], lw_ref)
+        assert [s[1] for s in r[5]] == [st["ess"] for st in stats_ref]
+        assert [s[2] for s in r[5]] == [st["resampled"] for st in stats_ref]
