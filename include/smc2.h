@@ -388,7 +388,10 @@ int smc2_server_create(size_t hbm_budget, int max_active, smc2_server** out);
 int smc2_server_set_fused(smc2_server* s, int on);
 
 /* Queue a job (cfg and y are copied; cfg->K_iters iterations).  Returns immediately.
- * SMC2_E_NOMEM only if the job can never fit the budget. */
+ * Admission (in arrival order) takes the job's own checkpoint interval when its footprint fits
+ * the memory left; with ckpt_every = 0 it may instead take a longer interval whose footprint
+ * fits (fewer stored steps, more recomputation: the job starts now instead of waiting).
+ * SMC2_E_NOMEM only if the job can never fit the budget (at the longest interval). */
 int smc2_submit(smc2_server* s, const smc2_config* cfg, uint64_t* job_id);
 
 /* SMC2_PENDING while queued or running; SMC2_OK once finished (fills *out and

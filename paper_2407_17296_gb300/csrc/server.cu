@@ -77,6 +77,43 @@ struct smc2_server {
 
 namespace {
 
+// Footprint of cfg at checkpoint interval kc (validated cfg).
+size_t footprint_at(const smc2_config* cfg, int kc) {
+    smc2_config c = *cfg;
+    c.ckpt_every = kc;
+    size_t b = 0;
+    return smc2_footprint(&c, &b) == SMC2_OK ? b : SIZE_MAX;
+}
+
+// The checkpoint interval a job is admitted with when `room` bytes are free: its own choice
+// (ckpt_every, else the automatic one) when that fits, else -- unless the caller fixed
+// ckpt_every -- the smallest power-of-two interval whose footprint fits (fewer stored steps,
+// more recomputation in the adjoint: the job runs now instead of waiting for memory), else 0.
+int admission_kc(const smc2_config* cfg, size_t room, size_t* bytes) {
+    const size_t own = footprint_at(cfg, cfg->ckpt_every);
+    if (own <= room) {
+        *bytes = own;
+        return cfg->ckpt_every;
+    }
+    if (cfg->ckpt_every > 0) return 0;
+    for (int kc = 2; kc <= cfg->T; kc *= 2) {
+        const size_t b = footprint_at(cfg, kc);
+        if (b <= room) {
+            *bytes = b;
+            return kc;
+        }
+    }
+    return 0;
+}
+
+// Smallest footprint of cfg over the checkpoint intervals admission may choose.
+size_t min_footprint(const smc2_config* cfg) {
+    size_t best = footprint_at(cfg, cfg->ckpt_every);
+    if (cfg->ckpt_every > 0) return best;
+    for (int kc = 2; kc <= cfg->T; kc *= 2) best = std::min(best, footprint_at(cfg, kc));
+    return best;
+}
+
 void finish_job(smc2_server* s, Job* j, int status) {
     if (j->h) {
         if (status == SMC2_OK) {
@@ -115,9 +152,14 @@ void worker_loop(smc2_server* s) {
                 continue;
             }
             Job* j = it->second.get();
-            if (s->used + j->bytes > s->budget) break;
+            // the job's own checkpoint interval if it fits, else a longer one that does
+            size_t bytes = 0;
+            const int kc = admission_kc(&j->cfg, s->budget - s->used, &bytes);
+            if (bytes == 0) break;  // nothing fits yet: wait for memory
+            j->bytes = bytes;
             s->pending.pop_front();
             smc2_config c = j->cfg;
+            c.ckpt_every = kc;
             c.y = j->y.data();
             c.y_on_device = 0;
             c.H = j->H.empty() ? nullptr : j->H.data();
@@ -255,9 +297,9 @@ extern "C" int smc2_submit(smc2_server* s, const smc2_config* cfg, uint64_t* job
     int rc = validate(cfg, &D);
     if (rc) return rc;
     if (cfg->y_on_device) return fail(SMC2_E_INVAL, "served jobs take host observations");
-    size_t bytes = 0;
-    rc = smc2_footprint(cfg, &bytes);
+    rc = smc2_footprint(cfg, nullptr);
     if (rc) return rc;
+    const size_t bytes = min_footprint(cfg);  // with the longest checkpoint interval admission may take
     if (bytes > s->budget) return fail(SMC2_E_NOMEM, "job footprint exceeds the server's HBM budget");
     if (cfg->K_iters < 1) return fail(SMC2_E_INVAL, "K_iters must be >= 1");
     auto j = std::make_unique<Job>();

@@ -20,6 +20,8 @@ def _jobs():
         (replace(W.lg1(T=20, N=30, M=128, K=3), seed=99), {}),
         (W.sv(T=40, N=24, M=128, K=3), {}),
         (replace(W.lg1(T=30, N=32, M=128, K=3, proposal="hmc"), hmc_steps=2, gamma=0.1), {}),
+        (W.lgssm(T=60, N=32, M=250, K=3), {}),         # optimal proposal, uniform priors
+        (replace(W.lgssm(T=45, N=20, M=250, K=3, proposal="rw"), seed=31), {}),
     ]
 
 
@@ -44,8 +46,8 @@ def test_batch_step_equals_each_job_alone():
                 n0 = binding.kernel_launches()
                 stats = b.step(hs)
                 # proposal + update of every job; one fused forward and adjoint launch per group of
-                # the fused jobs (4 groups: lg4 at 256 threads, lg1, sv; the HMC job after its first
-                # iteration steps on its own, with its graph or eager launches counted there)
+                # several jobs (lg4 at 128 threads, lg1, lgssm); sv alone in its group and the HMC
+                # job after its first iteration step on their own
                 assert binding.kernel_launches() - n0 >= 5 * (len(hs) - 1) + 2 * 3
                 for i, h in enumerate(hs):
                     st_ref, (th_ref, lw_ref) = ref[i][k]

@@ -74,21 +74,31 @@ def test_results_alone_equal_results_in_the_mix(fused):
 
 
 def test_admission_by_footprint_and_rejection():
+    """Admission by footprint: a job that fixes its checkpoint interval waits until memory frees
+    up; a job with the automatic interval is admitted at once with a longer interval (fewer
+    stored steps) when that fits the room left; a job that cannot fit even then is rejected."""
     from paper_2407_17296_gb300 import binding
     small = W.lg4(T=40, N=32, M=256, K=2)
-    cfg = binding.config_for(small)
-    fp = binding.footprint(cfg)
+    fp = binding.footprint(binding.config_for(small))  # the automatic interval stores every step
+    fp_min = min(binding.footprint(binding.config_for(small, ckpt_every=k)) for k in (2, 4, 8, 16, 32))
+    assert fp_min < 0.5 * fp
     # room for one job at a time: the second waits until the first frees its memory
     with binding.Server(hbm_budget=int(fp * 1.5), max_active=8) as srv:
-        ids = [srv.submit(binding.config_for(small)) for _ in range(3)]
+        ids = [srv.submit(binding.config_for(small, ckpt_every=1)) for _ in range(3)]
         res = _wait(srv, ids)
         assert all(res[j]["status"] == 0 for j in ids)
-        # the second job was admitted only after the first one finished
         first, second = res[ids[0]], res[ids[1]]
         assert second["queue_s"] >= 0.5 * (first["latency_s"] - first["queue_s"])
         big = binding.config_for(W.lg4(T=40, N=1024, M=1024, K=1))
         with pytest.raises(binding.Smc2Error, match="NOMEM"):
             srv.submit(big)
+    # room for one job and a bit: the second is admitted next to the first, with a longer interval
+    with binding.Server(hbm_budget=int(fp + 1.05 * fp_min), max_active=8) as srv:
+        ids = [srv.submit(binding.config_for(small)) for _ in range(2)]
+        res = _wait(srv, ids)
+        assert all(res[j]["status"] == 0 for j in ids)
+        first, second = res[ids[0]], res[ids[1]]
+        assert second["queue_s"] < first["latency_s"] - first["queue_s"]
 
 
 def test_cancel_and_unknown_ids():
