@@ -46,12 +46,13 @@ ALG_OPS_STRICT = {"lg1": 33 + 14, "lg4": 94 + 47, "sv": 36 + 15, "lg16": 333 + 1
 
 # DRAM bytes per filter of the forward + adjoint pair, measured with ncu on small launches
 # of each workload's shape (every step stored): dram__bytes_read.sum + dram__bytes_write.sum
-# of 304 filters for the 4-d workload (M = 1024, T = 250) and for SV (M = 2048, T = 500),
-# of 152 filters for the 16-d workload (M = 1024, T = 200); a launch of N filters moves N
-# times this.
-TRAFFIC_PER_FILTER = {("lg4", 1024, 250): (1482.174e6 + 1542.289e6) / 304,
-                      ("sv", 2048, 500): (1552.733e6 + 1624.368e6) / 304,
-                      ("lg16", 1024, 200): (2322.950e6 + 2196.211e6) / 152}
+# of the forward and the adjoint kernel over 304 filters for the 4-d workload (M = 1024,
+# T = 250; forward 8 particles/thread at 128 registers, adjoint 4 at 128) and for SV
+# (M = 2048, T = 500; forward 8 at 64, adjoint 8 at 128), over 152 filters for the 16-d
+# workload (M = 1024, T = 200; 8 at 128 both); a launch of N filters moves N times this.
+TRAFFIC_PER_FILTER = {("lg4", 1024, 250): (0.783e6 + 1485.469e6 + 1545.521e6 + 3.409e6) / 304,
+                      ("sv", 2048, 500): (1.823e6 + 1552.773e6 + 1612.209e6 + 0.372e6) / 304,
+                      ("lg16", 1024, 200): (1.002e6 + 2313.026e6 + 2190.548e6 + 2.515e6) / 152}
 
 
 def _args():
