@@ -32,6 +32,7 @@ STREAM_RESAMPLE = 1
 STREAM_INIT = 2
 STREAM_OUTER_XI = 3
 STREAM_OUTER_NU = 4
+STREAM_NUTS = 5
 
 STAT_NAMES = ("near_ties", "tie_followed", "nontie_mismatch", "flag_ties",
               "flag_mismatch", "resample_steps", "bad_hint", "tie_conditioned")

@@ -27,13 +27,31 @@ The L-kernel that reverses the momentum weights the end point by
 pi(theta_L) N(v_L; 0, gamma^2 I) / (pi(theta_0) N(v_0; 0, gamma^2 I)); with L = 1 this is
 the Langevin weight above.  Every leapfrog point runs the particle filters with the
 iteration's CRN keys.
+
+The NUTS proposal ("nuts"; Sec. V names NUTS beside HMC as the next proposal, without
+giving its L-kernel): the trajectory of the same leapfrog (step as above, run backwards in
+time by negating the velocity) is doubled in a random direction until it makes a U-turn,
+diverges or reaches the maximum depth J (Hoffman and Gelman's no-U-turn criterion: a
+sub-trajectory whose end points satisfy (theta+ - theta-) . v < 0 at either end stops the
+doubling).  The new point is drawn from the trajectory with multinomial weights exp(-H),
+H = -log pi + |v|^2 / (2 gamma^2): uniform progressive sampling inside each new
+sub-trajectory and biased progressive sampling when it is merged with the old one.
+Reading for the weight (the paper gives no L-kernel for NUTS): by default the NUTS kernel's
+own reversal, under which every weight stays unchanged (the move leaves pi(theta) N(v)
+invariant, so this is exact for a fixed target); as an option (nuts_unit_weight=False) the
+momentum-reversal L-kernel of the HMC move evaluated at the selected point (theta*, v*),
+log w += log pi(theta*) - log pi(theta_0) + |v_0|^2/(2 gamma^2) - |v*|^2/(2 gamma^2), which
+carries information but is not the importance weight of the NUTS proposal (the selected
+point is a random point of the trajectory, not its deterministic end).  Random numbers:
+Philox stream 5 (nuts_draws).
 """
 import math
 
 import numpy as np
 
 from . import pf as _pf, normals as _normals, uniform_open as _uniform_open
-from . import STREAM_OUTER_XI, STREAM_OUTER_NU, SYSTEMATIC
+from . import STREAM_OUTER_XI, STREAM_OUTER_NU, STREAM_NUTS, SYSTEMATIC
+from . import philox4x32_10 as _philox, STAT_NAMES as _STAT_NAMES
 
 LOG_2PI = np.log(2.0 * np.pi)
 
@@ -136,6 +154,164 @@ def hmc_xi(state, k, seed):
     return np.stack([_normals(seed, k, i, 0, STREAM_OUTER_XI, D) for i in range(N)])
 
 
+NUTS_DELTA_MAX = 1000.0   # a point with H - H_0 above this is divergent (Hoffman and Gelman)
+NUTS_KINDS = ("max_depth", "subtree_uturn", "divergent", "tree_uturn", "not_moved")
+
+
+def _u_open_word(w):
+    """U(0,1] of one 32-bit word: ((w >> 8) + 1) 2^-24."""
+    return ((int(w) >> 8) + 1) * 2.0 ** -24
+
+
+def nuts_draws(seed, k, i, J):
+    """The random numbers of one NUTS move of sample i at iteration k (Philox stream 5, the
+    sample's key): for doubling j, its direction (+1 if the top bit of word 0 of counter
+    (j, 0, 5, 0) is set, else -1) and its merge uniform (word 2 of that counter); for point n
+    of doubling j, its selection uniform (word 1 of counter (j, n, 5, 0)).  Points are
+    numbered s = 2^j - 1 + n in the order they are built."""
+    key = ((seed & 0xFFFFFFFF) ^ (k & 0xFFFFFFFF), ((seed >> 32) ^ i) & 0xFFFFFFFF)
+    dirs, u_sel, u_merge = [], [], []
+    for j in range(J):
+        for n in range(2 ** j):
+            w = _philox((j, n, STREAM_NUTS, 0), key)
+            if n == 0:
+                dirs.append(1 if (w[0] >> 31) else -1)
+                u_merge.append(_u_open_word(w[2]))
+            u_sel.append(_u_open_word(w[1]))
+    return dirs, u_sel, u_merge
+
+
+def _logaddexp(a, b):
+    if a == -np.inf:
+        return b
+    if b == -np.inf:
+        return a
+    m = max(a, b)
+    return m + math.log1p(math.exp(-abs(a - b)))
+
+
+def _uturn_margin(d, th_first, v_first, th_last, v_last):
+    """No-U-turn criterion of a sub-trajectory built in direction d from th_first to th_last:
+    the smaller of (theta+ - theta-) . v at its two ends (negative: a U-turn), and the same
+    relative to |theta+ - theta-| |v| (the scale of its rounding)."""
+    dth = d * (th_last - th_first)
+    a, b = float(dth @ v_first), float(dth @ v_last)
+    na = float(np.linalg.norm(dth))
+    rel = min(abs(a) / max(na * float(np.linalg.norm(v_first)), 1e-300),
+              abs(b) / max(na * float(np.linalg.norm(v_last)), 1e-300))
+    return min(a, b), rel
+
+
+def nuts_move(theta0, v0, lp0, grad0, payload0, point_fn, gamma, J, dirs, u_sel, u_merge,
+              hint=None, band_h=1e-3, band_u=1e-3):
+    """One NUTS move from (theta0, v0) with log pi(theta0) = lp0, grad log pi(theta0) = grad0.
+
+    point_fn(theta) -> (log pi, grad log pi, payload) runs the particle filter at a new point;
+    payload (the filter's log-likelihood and gradient) travels with the selected point.  The
+    random numbers come in as arguments (nuts_draws).  hint: decisions taken elsewhere,
+    {"sel": bits, "merge": bits, "stop": (s, kind)}; where this move decides differently, it
+    follows the hint when its own decision is within the band (a near-tie) and counts the
+    difference as a tie, else counts a mismatch (and still follows, so later steps compare).
+
+    Returns dict(theta, v, lp, payload, ke0, ke_sel, depth, stop=(s, kind), trace, stats)."""
+    g2 = gamma * gamma
+    half = 0.5 * g2
+
+    def kin(v):
+        return 0.5 * float(v @ v) / g2
+
+    stats = {"nuts_ties": 0, "nuts_mismatch": 0, "points": 0}
+    trace = {"sel": 0, "merge": 0, "stop": (2 ** J - 2, 0)}
+    ke0 = kin(v0)
+    sel = {"theta": theta0, "v": v0, "lp": lp0, "payload": payload0}
+    if not np.isfinite(lp0) or not np.all(np.isfinite(grad0)):
+        trace["stop"] = (-1, 4)
+        return dict(sel, ke0=ke0, ke_sel=ke0, depth=0, stop=(-1, 4), trace=trace, stats=stats)
+    H0 = -lp0 + ke0
+
+    def decide(own, key, margin, band):
+        """own decision, or the hint's where they differ (tie if |margin| < band)"""
+        if hint is None or key is None:
+            return own
+        other = key
+        if other != own:
+            stats["nuts_ties" if abs(margin) < band else "nuts_mismatch"] += 1
+        return other
+
+    def gpu_stops(s, kind):
+        if hint is None:
+            return None
+        hs, hk = hint["stop"]
+        return hs == s and hk == kind
+
+    lsw = -H0
+    ends = {+1: (theta0, v0, grad0), -1: (theta0, v0, grad0)}
+    depth = 0
+    for j in range(J):
+        d = dirs[j]
+        th_f, v_f, g_f = ends[d]
+        lsw_sub = -np.inf
+        cand = None
+        ck = {}
+        stopped = None
+        for n in range(2 ** j):
+            s = 2 ** j - 1 + n
+            # one leapfrog step in direction d from the frontier
+            vh = v_f + d * half * g_f
+            th = th_f + d * vh
+            lp, g, payload = point_fn(th)
+            stats["points"] += 1
+            broken = not (np.isfinite(lp) and np.all(np.isfinite(g)))
+            v = vh + d * half * g if not broken else vh
+            H = -lp + kin(v) if not broken else np.inf
+            own = broken or (H - H0 > NUTS_DELTA_MAX)
+            if decide(own, gpu_stops(s, 2), np.inf if broken else (H - H0 - NUTS_DELTA_MAX), band_h):
+                stopped = (s, 2)
+                break
+            # uniform progressive sampling inside the sub-trajectory
+            lsw_new = _logaddexp(lsw_sub, -H)
+            m = (-H - lsw_new) - math.log(u_sel[s])
+            hbit = None if hint is None else bool((hint["sel"] >> s) & 1)
+            if decide(m >= 0.0, hbit, m, band_h):
+                cand = {"theta": th, "v": v, "lp": lp, "payload": payload}
+                trace["sel"] |= 1 << s
+            lsw_sub = lsw_new
+            # no-U-turn checks of the completed blocks of 2, 4, ... points of this doubling
+            uturn, rel = False, np.inf
+            for l in range(1, j + 1):
+                if n % (2 ** l) == 0:
+                    ck[l] = (th, v)
+                if (n + 1) % (2 ** l) == 0:
+                    mg, r = _uturn_margin(d, ck[l][0], ck[l][1], th, v)
+                    if mg < 0.0:
+                        uturn = True
+                    rel = min(rel, r)
+            if decide(uturn, gpu_stops(s, 1), rel, band_u):
+                stopped = (s, 1)
+                break
+            th_f, v_f, g_f = th, v, g
+        if stopped is not None:
+            trace["stop"] = stopped
+            break
+        # biased progressive sampling: the new sub-trajectory's candidate replaces the
+        # selected point with probability min(1, W_new / W_old)
+        m = (lsw_sub - lsw) - math.log(u_merge[j])
+        hbit = None if hint is None else bool((hint["merge"] >> j) & 1)
+        if decide(m >= 0.0, hbit, m, band_h):
+            sel = cand
+            trace["merge"] |= 1 << j
+        lsw = _logaddexp(lsw, lsw_sub)
+        ends[d] = (th_f, v_f, g_f)
+        depth = j + 1
+        s_last = 2 ** (j + 1) - 2
+        mg, rel = _uturn_margin(+1, ends[-1][0], ends[-1][1], ends[+1][0], ends[+1][1])
+        if decide(mg < 0.0, gpu_stops(s_last, 3), rel, band_u):
+            trace["stop"] = (s_last, 3)
+            break
+    return dict(sel, ke0=ke0, ke_sel=kin(sel["v"]), depth=depth, stop=trace["stop"], trace=trace,
+                stats=stats)
+
+
 def propose(state, k, seed, gamma, proposal, m0, s0, prior_kind=GAUSSIAN_PRIOR):
     """theta' for iteration k: a prior draw at k = 1 (Eq. init_sample; a uniform prior maps the
     normal xi through its CDF), else the random-walk (SMC0) or Langevin (SMC1) move of
@@ -155,13 +331,22 @@ def update(state, k, theta_new, ll_new, g_new, seed, gamma, proposal, m0, s0, hi
     """Complete iteration k from the filter outputs at theta_new: weight, normalise,
     estimate, recycling statistic, ESS, resampling.  Updates state; returns the record.
     kinetic (HMC): (|v_0|^2, |v_L|^2) / (2 gamma^2) per sample, NaN where a leapfrog point
-    failed."""
+    failed; (NUTS): the per-sample weight correction of the move (nuts_step)."""
     N = state.logw.shape[0]
     lp_new = log_prior(theta_new, m0, s0, prior_kind) + ll_new
     gp_new = grad_log_prior(theta_new, m0, s0, prior_kind) + g_new
     if k == 1:
         # w_1 = pi/q_1 = p-hat(y|theta) (Eq. init_weights)
         logw = ll_new.copy()
+    elif proposal == "nuts":
+        # kinetic = (|v_0|^2/(2 gamma^2) - |v*|^2/(2 gamma^2) per sample, unit): the momentum
+        # reversal at the selected point, or (unit) the NUTS kernel's own reversal, which
+        # leaves the weight unchanged
+        corr, unit = kinetic
+        ok = (state.logw > -np.inf) & (lp_new > -np.inf) & (state.logpi > -np.inf)
+        with np.errstate(invalid="ignore", over="ignore"):
+            moved = state.logw if unit else state.logw + lp_new - state.logpi + corr
+            logw = np.where(ok, moved, -np.inf)
     elif proposal == "hmc":
         # momentum-reversal L-kernel: pi(theta_L) N(v_L) / (pi(theta_0) N(v_0))
         ke0, keL = kinetic
@@ -185,7 +370,7 @@ def update(state, k, theta_new, ll_new, g_new, seed, gamma, proposal, m0, s0, hi
     # The Langevin kernels (the SMC1 proposal of Sec. III-D, the L-kernel of Sec. III-E) need
     # grad log pi at the proposal.  Where it is not finite the sample can neither be
     # weighted nor moved: it carries weight zero, as does any non-finite weight.
-    grad_ok = np.all(np.isfinite(gp_new), axis=1) if proposal in ("langevin", "hmc") else np.ones(N, bool)
+    grad_ok = np.all(np.isfinite(gp_new), axis=1) if proposal in ("langevin", "hmc", "nuts") else np.ones(N, bool)
     logw = np.where(grad_ok & np.isfinite(logw), logw, -np.inf)
     theta, logpi, gradpi, loglik = theta_new, lp_new, gp_new, ll_new
 
@@ -228,11 +413,13 @@ def recycled_mean(records):
 def run(family, dx, dy, H, y, N, M, K, gamma, proposal, seed, prior_mean=None, prior_std=None,
         scheme=SYSTEMATIC, ess_frac=0.5, hints=None, band=1e-6, flag_band=1e-6,
         outer_band=1e-4, D=None, loglik_grad_fn=None, band_rel=0.0, outer_flag_band=1e-3,
-        prior_kind=GAUSSIAN_PRIOR, hmc_steps=1):
+        prior_kind=GAUSSIAN_PRIOR, hmc_steps=1, nuts_depth=3, nuts_unit_weight=True):
     """Run K iterations; returns (list of per-iteration records, recycled mean).
 
-    proposal: "rw" (SMC0), "langevin" (SMC1) or "hmc" (hmc_steps leapfrog steps; the hints,
-      when given, apply to the filters at the last leapfrog point).
+    proposal: "rw" (SMC0), "langevin" (SMC1), "hmc" (hmc_steps leapfrog steps; the hints,
+      when given, apply to the filters at the last leapfrog point) or "nuts" (trajectories of
+      at most 2^nuts_depth - 1 new points; hints may carry "nuts": per sample
+      {"sel", "merge", "stop"} decisions, followed at near-ties).
     hints: optional list, per iteration, of dicts with keys pf_anc (N,T,M), pf_flag (N,T),
       outer_anc (N,), outer_flag (bool): decisions taken elsewhere, followed at near-ties
       (PF level: |c - tau| < band; outer level: |c - tau| < outer_band, and the resampling
@@ -274,6 +461,11 @@ def run(family, dx, dy, H, y, N, M, K, gamma, proposal, seed, prior_mean=None, p
                 keL = 0.5 * np.sum(vL * vL, axis=1) / (gamma * gamma)
             keL = np.where(last["bad"], np.nan, keL)
             kinetic = (ke0, keL)
+        elif proposal == "nuts" and k > 1:
+            theta_new, ll_new, g_new, kinetic, pfstats, pfrows, nuts_rec = nuts_step(
+                state, k, seed, gamma, nuts_depth, nuts_unit_weight, family, dx, dy, H, y, M, scheme,
+                ess_frac, band, flag_band, band_rel, loglik_grad_fn, m0, s0, prior_kind,
+                hint.get("nuts") if hint is not None else None)
         else:
             theta_new = propose(state, k, seed, gamma, proposal, m0, s0, prior_kind)
             ll_new, g_new, pfstats, pfrows = run_filters(family, dx, dy, H, y, M, seed, k, theta_new,
@@ -283,8 +475,60 @@ def run(family, dx, dy, H, y, N, M, K, gamma, proposal, seed, prior_mean=None, p
                      outer_band, outer_flag_band, prior_kind, kinetic)
         rec["pf_stats"] = pfstats
         rec["pf_stats_rows"] = pfrows
+        if proposal == "nuts" and k > 1:
+            rec["nuts"] = nuts_rec
         records.append(rec)
     return records, recycled_mean(records)
+
+
+def nuts_step(state, k, seed, gamma, J, unit_weight, family, dx, dy, H, y, M, scheme, ess_frac,
+              band, flag_band, band_rel, loglik_grad_fn, m0, s0, prior_kind, hints=None):
+    """The NUTS move of every sample at iteration k > 1, one sample after the other: momentum
+    v_0 = gamma xi (xi from Philox stream 3, as the HMC move), the sample's particle filter
+    (its own CRN key) at every new trajectory point, the move of nuts_move.  Returns the
+    selected points, their filter outputs, (the kinetic-energy differences
+    |v_0|^2/(2 gamma^2) - |v*|^2/(2 gamma^2), unit_weight) for the weight (update), aggregated and
+    per-row filter statistics, and per-sample records (depth, stop, trace, stats)."""
+    N, D = state.theta.shape
+    xi = hmc_xi(state, k, seed)
+    theta_new = np.empty_like(state.theta)
+    ll_new = np.empty(N)
+    g_new = np.empty((N, D))
+    corr = np.empty(N)
+    agg, rows, recs = {}, [], []
+    for i in range(N):
+        row_stats = {}
+
+        def point_fn(th, i=i, row_stats=row_stats):
+            if loglik_grad_fn is not None:
+                ll, g = loglik_grad_fn(th)
+            else:
+                out = _pf(family, dx, dy, H, th, y, M, seed, k, i, scheme=scheme, ess_frac=ess_frac,
+                          want_grad=True, band=band, flag_band=flag_band, want_tape=False,
+                          band_rel=band_rel)
+                ll, g = out["loglik"], out["grad"]
+                for key, v in out["stats"].items():
+                    row_stats[key] = row_stats.get(key, 0) + v
+            lp = float(log_prior(th, m0, s0, prior_kind)) + ll
+            gp = grad_log_prior(th, m0, s0, prior_kind) + g
+            return lp, gp, (ll, np.asarray(g, dtype=np.float64))
+
+        dirs, u_sel, u_merge = nuts_draws(seed, k, i, J)
+        th0 = state.theta[i]
+        g0 = state.gradpi[i] - grad_log_prior(th0, m0, s0, prior_kind)
+        res = nuts_move(th0, gamma * xi[i], state.logpi[i], state.gradpi[i], (state.loglik[i], g0),
+                        point_fn, gamma, J, dirs, u_sel, u_merge,
+                        hint=hints[i] if hints is not None else None)
+        theta_new[i] = res["theta"]
+        ll_new[i], g_new[i] = res["payload"]
+        corr[i] = res["ke0"] - res["ke_sel"]
+        for key in _STAT_NAMES:
+            row_stats.setdefault(key, 0)
+        rows.append(row_stats)
+        for key, v in row_stats.items():
+            agg[key] = agg.get(key, 0) + v
+        recs.append({"depth": res["depth"], "stop": res["stop"], "trace": res["trace"], "stats": res["stats"]})
+    return theta_new, ll_new, g_new, (corr, bool(unit_weight)), agg, rows, recs
 
 
 def run_filters(family, dx, dy, H, y, M, seed, k, theta, rows, scheme=SYSTEMATIC, ess_frac=0.5,
