@@ -75,6 +75,10 @@ def _args():
     p.add_argument("--hmc-steps", type=int, default=0,
                    help="run the workload with the HMC proposal of this many leapfrog steps "
                         "(step gamma / sqrt(L); every step runs the N filters)")
+    p.add_argument("--nuts-depth", type=int, default=0,
+                   help="run the workload with the NUTS proposal of this maximum depth J (2^J - 1 "
+                        "trajectory points an iteration, each running the N filters; step "
+                        "gamma / sqrt(2^J - 1))")
     p.add_argument("--resample", default="systematic", choices=["systematic", "multinomial"],
                    help="the filters' resampling scheme (multinomial is the paper's, Sec. II-B)")
     p.add_argument("--launch", default=None,
@@ -231,8 +235,21 @@ def make_workload(a):
         # outer weights degenerate on these workloads
         from dataclasses import replace
         w = replace(w, proposal="hmc", hmc_steps=a.hmc_steps, gamma=w.gamma / math.sqrt(a.hmc_steps))
+    if a.nuts_depth:
+        from dataclasses import replace
+        pts = 2 ** a.nuts_depth - 1
+        w = replace(w, proposal="nuts", nuts_depth=a.nuts_depth, gamma=w.gamma / math.sqrt(pts))
     w.resample = a.resample
     return w
+
+
+def points_per_step(w):
+    """Filter launches (leapfrog points) of one SMC2 iteration after the first."""
+    if w.proposal == "hmc":
+        return w.hmc_steps
+    if w.proposal == "nuts":
+        return 2 ** w.nuts_depth - 1
+    return 1
 
 
 def workload_config(w):
@@ -257,7 +274,7 @@ def run_gpu(a, rank, world, local):
     w = make_workload(a)
     mode = a.mode
     if mode == "auto":
-        mode = "sharded" if world > 1 and w.N * world <= 16384 and w.proposal != "hmc" else "replicas"
+        mode = "sharded" if world > 1 and w.N * world <= 16384 and w.proposal not in ("hmc", "nuts") else "replicas"
     if mode == "sharded":
         # weak scaling of one job: N rows a rank of a job with N x ranks samples, the ranks
         # exchanging the filter outputs (one all-gather) before every outer update
@@ -281,7 +298,7 @@ def run_gpu(a, rank, world, local):
     if mode == "sharded":
         return run_sharded(a, rank, world, dev, w, h, stream, launch)
     ps_launch = w.N * w.M * w.T  # particle-steps of one filter launch (one leapfrog point)
-    ps_per_step = ps_launch * (w.hmc_steps if w.proposal == "hmc" else 1)
+    ps_per_step = ps_launch * points_per_step(w)
 
     def barrier():
         if world > 1:
@@ -384,9 +401,11 @@ def run_gpu(a, rank, world, local):
                    "launch": {"forward_ppt": launch[0], "forward_regs": launch[1], "adjoint_ppt": launch[2],
                               "adjoint_regs": launch[3], "ckpt_every": launch[4]},
                    "step": ("one SMC2 iteration: propose, N filters fwd+adjoint, L-kernel weights, resample"
-                            if w.proposal != "hmc" else
+                            if w.proposal not in ("hmc", "nuts") else
                             f"one SMC2 iteration: HMC move of {w.hmc_steps} leapfrog steps (N filters "
-                            f"fwd+adjoint at each point), L-kernel weights, resample"),
+                            f"fwd+adjoint at each point), L-kernel weights, resample" if w.proposal == "hmc" else
+                            f"one SMC2 iteration: NUTS move of depth {w.nuts_depth} ({2 ** w.nuts_depth - 1} "
+                            f"lockstep trajectory points, N filters fwd+adjoint at each), weights, resample"),
                    "dead_samples": dead,
                    "l2": "inputs larger than L2 (particle trajectory of several GB written and read per step)",
                    "parallelism": f"replicas x{world} (independent jobs)" if world > 1 else "one job, one GPU"},
@@ -537,7 +556,7 @@ def run_reference(a, rank, world):
     value = statistics.mean(rates)
     # what one whole iteration of the GPU arm's step (N filters at each of the move's leapfrog
     # points) would take at this rate: extrapolated, not timed
-    ms_iter = 1e3 * w.N * w.M * w.T * (w.hmc_steps if w.proposal == "hmc" else 1) / value
+    ms_iter = 1e3 * w.N * w.M * w.T * points_per_step(w) / value
     r1, _, i1 = cpu_oracle_rate(w, max(2.0, per), 1)
     return {
         "impl": "reference",

@@ -49,12 +49,27 @@ extern "C" {
  *    1/rho^2 = 1/phi^2 + 1/sigma^2, and weights p(y_t | x_{t-1}) = N(y_t; mu x_{t-1},
  *    phi^2 + sigma^2). */
 enum { SMC2_LG_DIAG = 0, SMC2_SV = 1, SMC2_LG_OPT = 2 };
-/* Outer proposals (Sec. III-D): SMC0 random walk, SMC1 Langevin, and HMC (the extension
- * Sec. V names): hmc_steps leapfrog steps whose single step is the SMC1 move, with
- * momentum v ~ N(0, gamma^2 I) and the momentum-reversal L-kernel, i.e. the weight
- * pi(theta_L) N(v_L; 0, gamma^2 I) / (pi(theta_0) N(v_0; 0, gamma^2 I)).  Every leapfrog
- * point runs the N particle filters (forward + adjoint) with the iteration's CRN keys. */
-enum { SMC2_RW = 0, SMC2_LANGEVIN = 1, SMC2_HMC = 2 };
+/* Outer proposals (Sec. III-D): SMC0 random walk, SMC1 Langevin, and HMC and NUTS (the
+ * extensions Sec. V names).  HMC: hmc_steps leapfrog steps whose single step is the SMC1
+ * move, with momentum v ~ N(0, gamma^2 I) and the momentum-reversal L-kernel, i.e. the weight
+ * pi(theta_L) N(v_L; 0, gamma^2 I) / (pi(theta_0) N(v_0; 0, gamma^2 I)).  NUTS: the same
+ * leapfrog, run forwards or backwards in time, doubles a trajectory in random directions
+ * until it makes a U-turn ((theta+ - theta-) . v < 0 at an end of a sub-trajectory), a point
+ * diverges (H - H_0 > 1000, H = -log pi + |v|^2 / (2 gamma^2), or a non-finite estimate) or
+ * the depth reaches nuts_max_depth; the new sample is drawn from the trajectory with weights
+ * exp(-H) (uniform progressive sampling inside a new sub-trajectory, biased progressive
+ * sampling when it is merged).  Its L-kernel (nuts_weight): SMC2_NUTS_REVERSAL, the NUTS
+ * kernel's own reversal, which leaves log w unchanged (exact for a fixed target; the
+ * default), or SMC2_NUTS_MOMENTUM_REVERSAL, the HMC weight above at the selected point and
+ * its momentum.  Random numbers: Philox stream 5 of the sample's key (direction of doubling
+ * j: top bit of word 0 of counter (j, 0, 5, 0); merge uniform: word 2 of that counter;
+ * selection uniform of point n of doubling j: word 1 of counter (j, n, 5, 0)); momentum:
+ * stream 3 as HMC.  The trajectory points of all samples are built in lockstep: every
+ * iteration runs 2^nuts_max_depth - 1 leapfrog points, each a forward + adjoint pass of the
+ * N particle filters with the iteration's CRN keys (samples whose trajectory has stopped
+ * ignore theirs). */
+enum { SMC2_RW = 0, SMC2_LANGEVIN = 1, SMC2_HMC = 2, SMC2_NUTS = 3 };
+enum { SMC2_NUTS_REVERSAL = 0, SMC2_NUTS_MOMENTUM_REVERSAL = 1 };
 /* Particle-filter resampler (Sec. II-B, App. B). */
 enum { SMC2_SYSTEMATIC = 0, SMC2_MULTINOMIAL = 1 };
 /* Prior on theta: Gaussian N(prior_mean, diag(prior_std^2)), or uniform on the box
@@ -83,10 +98,12 @@ typedef struct smc2_config {
     void* stream;               /* cudaStream_t for all work of the handle; NULL = a private stream */
     int32_t prior_kind;         /* SMC2_PRIOR_GAUSSIAN (default) or SMC2_PRIOR_UNIFORM */
     int32_t hmc_steps;          /* SMC2_HMC: leapfrog steps per move, 1..64 (1 = the SMC1 move) */
+    int32_t nuts_max_depth;     /* SMC2_NUTS: maximum number of doublings, 1..6 */
+    int32_t nuts_weight;        /* SMC2_NUTS: SMC2_NUTS_REVERSAL or SMC2_NUTS_MOMENTUM_REVERSAL */
 } smc2_config;
 
 /* Fill defaults: struct_size, ess_frac 0.5, K_iters 10, systematic, Langevin, gamma 0.1,
- * hmc_steps 1. */
+ * hmc_steps 1, nuts_max_depth 3, nuts_weight SMC2_NUTS_REVERSAL. */
 void smc2_config_init(smc2_config* cfg);
 
 typedef struct smc2_handle smc2_handle;
@@ -156,7 +173,8 @@ int pf_loglik_grad_host(smc2_handle* h, const double* theta_host, int n, uint32_
  *  k = 1: theta ~ prior (Eq. init_sample), PF, w = pi/q_1 (Eq. init_weights).
  *  k > 1: Langevin or random-walk move (Sec. III-D), PF at the new theta, weight with
  *         the L-kernel (Eq. l_weights, Sec. III-E); with SMC2_HMC, hmc_steps leapfrog steps
- *         (a PF forward + adjoint at every point) and the momentum-reversal weight.
+ *         (a PF forward + adjoint at every point) and the momentum-reversal weight; with
+ *         SMC2_NUTS, a no-U-turn trajectory of up to 2^nuts_max_depth - 1 points.
  *  then normalise, estimate, recycling statistic, ESS and, if N_eff < N/2,
  *  systematic resampling (Sec. III-A..C).  Fills *out (may be NULL) on the host:
  *  this call synchronises the handle's stream.
@@ -202,8 +220,8 @@ int smc2_get_step_timing(smc2_handle* h, float* ms);
  * Replicas that pass the same N rows to smc2_step_update stay identical, and equal to one
  * handle running smc2_step.  The two calls must alternate; smc2_step_update without a
  * preceding smc2_step_filters, or n < 0, row0 < 0, row0 + n > N, or NULL buffers with n > 0:
- * SMC2_E_INVAL; so is a handle with the SMC2_HMC proposal (its leapfrog needs every
- * sample's filters at each point).  Launch failures: SMC2_E_CUDA.
+ * SMC2_E_INVAL; so is a handle with the SMC2_HMC or SMC2_NUTS proposal (their leapfrog
+ * needs every sample's filters at each point).  Launch failures: SMC2_E_CUDA.
  */
 int smc2_step_filters(smc2_handle* h, int row0, int n, double* loglik_dev, double* grad_dev);
 int smc2_step_update(smc2_handle* h, const double* loglik_all_dev, const double* grad_all_dev,
@@ -248,6 +266,33 @@ int smc2_get_state(smc2_handle* h, double* loglik_host, double* gradpi_host);
  */
 int smc2_get_trace(smc2_handle* h, uint16_t* pf_anc, uint8_t* pf_flag, int32_t* outer_anc,
                    int32_t* outer_resampled);
+
+/*
+ * smc2_get_nuts_trace: the decisions of each sample's NUTS move in the last smc2_step (host
+ * buffers [N], any may be NULL), for verification.  Points are numbered s = 2^j - 1 + n (point
+ * n of doubling j).  sel: bit s set where point s became its sub-trajectory's candidate;
+ * merge: bit j set where doubling j's candidate replaced the selected point; stop_point and
+ * stop_kind: where and why the trajectory stopped (kind 0: maximum depth, at the last point;
+ * 1: U-turn inside a sub-trajectory; 2: divergent or non-finite point; 3: U-turn of the whole
+ * trajectory, at the last point of a doubling; 4: not moved, stop_point -1, because the
+ * sample's log pi or gradient is not finite).  SMC2_E_INVAL if the handle's proposal is not
+ * SMC2_NUTS or no NUTS move ran yet.  Synchronises the handle's stream.
+ */
+int smc2_get_nuts_trace(smc2_handle* h, uint64_t* sel, uint32_t* merge, int32_t* stop_point,
+                        int32_t* stop_kind);
+
+/*
+ * Per-point tapes, for verification of moves with several leapfrog points (HMC, NUTS).
+ * smc2_set_point_trace(h, on): with on, every later iteration also keeps the ancestor tape and
+ * resampling flags of the filter launch at each of its leapfrog points (device copies; the
+ * first call allocates 2 bytes x points x N x T x M rounded up to 8, plus points x N x T bytes;
+ * while on, iterations run without the captured graph).  smc2_get_point_trace(h, point, pf_anc,
+ * pf_flag) copies point `point` (0-based, in launch order; NUTS: s = 2^j - 1 + n) of the last
+ * iteration to host buffers laid out as smc2_get_trace's.  SMC2_E_INVAL if tracing was never on
+ * or point is out of range; SMC2_E_NOMEM if the allocation fails.
+ */
+int smc2_set_point_trace(smc2_handle* h, int on);
+int smc2_get_point_trace(smc2_handle* h, int point, uint16_t* pf_anc, uint8_t* pf_flag);
 
 /*
  * pf_loglik_grad_static: pf_loglik_grad for callers that cannot allocate device memory

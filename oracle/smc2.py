@@ -206,8 +206,9 @@ def nuts_move(theta0, v0, lp0, grad0, payload0, point_fn, gamma, J, dirs, u_sel,
               hint=None, band_h=1e-3, band_u=1e-3):
     """One NUTS move from (theta0, v0) with log pi(theta0) = lp0, grad log pi(theta0) = grad0.
 
-    point_fn(theta) -> (log pi, grad log pi, payload) runs the particle filter at a new point;
-    payload (the filter's log-likelihood and gradient) travels with the selected point.  The
+    point_fn(theta, s) -> (log pi, grad log pi, payload) runs the particle filter at new point s
+    (s = 2^j - 1 + n for point n of doubling j); payload (the filter's log-likelihood and
+    gradient) travels with the selected point.  The
     random numbers come in as arguments (nuts_draws).  hint: decisions taken elsewhere,
     {"sel": bits, "merge": bits, "stop": (s, kind)}; where this move decides differently, it
     follows the hint when its own decision is within the band (a near-tie) and counts the
@@ -259,7 +260,7 @@ def nuts_move(theta0, v0, lp0, grad0, payload0, point_fn, gamma, J, dirs, u_sel,
             # one leapfrog step in direction d from the frontier
             vh = v_f + d * half * g_f
             th = th_f + d * vh
-            lp, g, payload = point_fn(th)
+            lp, g, payload = point_fn(th, s)
             stats["points"] += 1
             broken = not (np.isfinite(lp) and np.all(np.isfinite(g)))
             v = vh + d * half * g if not broken else vh
@@ -464,8 +465,7 @@ def run(family, dx, dy, H, y, N, M, K, gamma, proposal, seed, prior_mean=None, p
         elif proposal == "nuts" and k > 1:
             theta_new, ll_new, g_new, kinetic, pfstats, pfrows, nuts_rec = nuts_step(
                 state, k, seed, gamma, nuts_depth, nuts_unit_weight, family, dx, dy, H, y, M, scheme,
-                ess_frac, band, flag_band, band_rel, loglik_grad_fn, m0, s0, prior_kind,
-                hint.get("nuts") if hint is not None else None)
+                ess_frac, band, flag_band, band_rel, loglik_grad_fn, m0, s0, prior_kind, hint)
         else:
             theta_new = propose(state, k, seed, gamma, proposal, m0, s0, prior_kind)
             ll_new, g_new, pfstats, pfrows = run_filters(family, dx, dy, H, y, M, seed, k, theta_new,
@@ -482,14 +482,18 @@ def run(family, dx, dy, H, y, N, M, K, gamma, proposal, seed, prior_mean=None, p
 
 
 def nuts_step(state, k, seed, gamma, J, unit_weight, family, dx, dy, H, y, M, scheme, ess_frac,
-              band, flag_band, band_rel, loglik_grad_fn, m0, s0, prior_kind, hints=None):
+              band, flag_band, band_rel, loglik_grad_fn, m0, s0, prior_kind, hint=None):
     """The NUTS move of every sample at iteration k > 1, one sample after the other: momentum
     v_0 = gamma xi (xi from Philox stream 3, as the HMC move), the sample's particle filter
     (its own CRN key) at every new trajectory point, the move of nuts_move.  Returns the
     selected points, their filter outputs, (the kinetic-energy differences
     |v_0|^2/(2 gamma^2) - |v*|^2/(2 gamma^2), unit_weight) for the weight (update), aggregated and
-    per-row filter statistics, and per-sample records (depth, stop, trace, stats)."""
+    per-row filter statistics, and per-sample records (depth, stop, trace, stats).  hint: optional
+    {"nuts": per-sample move decisions (nuts_move), "nuts_pf": per point s, (pf_anc [N][T][M],
+    pf_flag [N][T]) of the filters run elsewhere at that point} -- followed at near-ties only."""
     N, D = state.theta.shape
+    move_hints = hint.get("nuts") if hint is not None else None
+    pf_hints = hint.get("nuts_pf") if hint is not None else None
     xi = hmc_xi(state, k, seed)
     theta_new = np.empty_like(state.theta)
     ll_new = np.empty(N)
@@ -499,13 +503,16 @@ def nuts_step(state, k, seed, gamma, J, unit_weight, family, dx, dy, H, y, M, sc
     for i in range(N):
         row_stats = {}
 
-        def point_fn(th, i=i, row_stats=row_stats):
+        def point_fn(th, s, i=i, row_stats=row_stats):
             if loglik_grad_fn is not None:
                 ll, g = loglik_grad_fn(th)
             else:
+                ha = hf = None
+                if pf_hints is not None:
+                    ha, hf = pf_hints[s][0][i], pf_hints[s][1][i]
                 out = _pf(family, dx, dy, H, th, y, M, seed, k, i, scheme=scheme, ess_frac=ess_frac,
-                          want_grad=True, band=band, flag_band=flag_band, want_tape=False,
-                          band_rel=band_rel)
+                          want_grad=True, hint_anc=ha, hint_flag=hf, band=band, flag_band=flag_band,
+                          want_tape=False, band_rel=band_rel)
                 ll, g = out["loglik"], out["grad"]
                 for key, v in out["stats"].items():
                     row_stats[key] = row_stats.get(key, 0) + v
@@ -518,7 +525,7 @@ def nuts_step(state, k, seed, gamma, J, unit_weight, family, dx, dy, H, y, M, sc
         g0 = state.gradpi[i] - grad_log_prior(th0, m0, s0, prior_kind)
         res = nuts_move(th0, gamma * xi[i], state.logpi[i], state.gradpi[i], (state.loglik[i], g0),
                         point_fn, gamma, J, dirs, u_sel, u_merge,
-                        hint=hints[i] if hints is not None else None)
+                        hint=move_hints[i] if move_hints is not None else None)
         theta_new[i] = res["theta"]
         ll_new[i], g_new[i] = res["payload"]
         corr[i] = res["ke0"] - res["ke_sel"]
@@ -546,7 +553,7 @@ def run_filters(family, dx, dy, H, y, M, seed, k, theta, rows, scheme=SYSTEMATIC
             ll[r], g[r] = loglik_grad_fn(theta[i])
             continue
         ha = hf = None
-        if hint is not None:
+        if hint is not None and "pf_anc" in hint:
             ha = hint["pf_anc"][i]
             hf = hint["pf_flag"][i]
         out = _pf(family, dx, dy, H, theta[i], y, M, seed, k, i, scheme=scheme,

@@ -17,8 +17,9 @@ ERRORS = {-1: "SMC2_E_INVAL", -2: "SMC2_E_NOMEM", -3: "SMC2_E_CUDA", -4: "SMC2_E
           -5: "SMC2_E_NOTFOUND", -6: "SMC2_E_BUSY"}
 LG_DIAG, SV, LG_OPT = 0, 1, 2
 PRIOR_GAUSSIAN, PRIOR_UNIFORM = 0, 1
-RW, LANGEVIN, HMC = 0, 1, 2
-PROPOSALS = {"rw": RW, "langevin": LANGEVIN, "hmc": HMC}
+RW, LANGEVIN, HMC, NUTS = 0, 1, 2, 3
+PROPOSALS = {"rw": RW, "langevin": LANGEVIN, "hmc": HMC, "nuts": NUTS}
+NUTS_REVERSAL, NUTS_MOMENTUM_REVERSAL = 0, 1
 SYSTEMATIC, MULTINOMIAL = 0, 1
 
 # every symbol include/smc2.h declares
@@ -28,7 +29,8 @@ EXPORTS = ("smc2_config_init", "smc2_create", "pf_loglik_grad", "pf_loglik_grad_
            "smc2_autotune", "smc2_get_launch", "smc2_set_launch", "smc2_get_status", "smc2_selftest_bounded_wait", "smc2_kernel_launches", "smc2_last_error", "smc2_server_create",
            "smc2_submit", "smc2_poll", "smc2_cancel", "smc2_server_destroy",
            "pf_loglik_grad_static", "pf_static_get_status", "smc2_get_stream", "smc2_selftest_crn",
-           "smc2_batch_create", "smc2_batch_step", "smc2_batch_destroy", "smc2_server_set_fused")
+           "smc2_batch_create", "smc2_batch_step", "smc2_batch_destroy", "smc2_server_set_fused",
+           "smc2_get_nuts_trace", "smc2_set_point_trace", "smc2_get_point_trace")
 
 
 class Config(ctypes.Structure):
@@ -57,6 +59,8 @@ class Config(ctypes.Structure):
         ("stream", ctypes.c_void_p),
         ("prior_kind", ctypes.c_int32),
         ("hmc_steps", ctypes.c_int32),
+        ("nuts_max_depth", ctypes.c_int32),
+        ("nuts_weight", ctypes.c_int32),
     ]
 
 
@@ -125,6 +129,9 @@ def load(path: str = LIB_PATH):
         "smc2_get_samples": (ctypes.c_int, [vp, dp, dp]),
         "smc2_get_state": (ctypes.c_int, [vp, dp, dp]),
         "smc2_get_trace": (ctypes.c_int, [vp, vp, vp, vp, vp]),
+        "smc2_get_nuts_trace": (ctypes.c_int, [vp, vp, vp, vp, vp]),
+        "smc2_set_point_trace": (ctypes.c_int, [vp, ctypes.c_int]),
+        "smc2_get_point_trace": (ctypes.c_int, [vp, ctypes.c_int, vp, vp]),
         "smc2_set_observations": (ctypes.c_int, [vp, vp]),
         "smc2_footprint": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_size_t)]),
         "smc2_destroy": (ctypes.c_int, [vp]),
@@ -189,7 +196,7 @@ def _ptr(t):
 def make_config(family, dx, dy, T, N, M, D, y, H=None, prior_mean=None, prior_std=None,
                 proposal=LANGEVIN, gamma=0.1, K_iters=10, pf_resample=SYSTEMATIC, ess_frac=0.5,
                 seed=777, ckpt_every=0, particles_per_thread=0, stream=None, y_on_device=False,
-                prior_kind=PRIOR_GAUSSIAN, hmc_steps=1):
+                prior_kind=PRIOR_GAUSSIAN, hmc_steps=1, nuts_max_depth=3, nuts_weight=NUTS_REVERSAL):
     """Build a Config; numpy arrays referenced by it are kept alive on the returned object."""
     import numpy as np
     lib = load()
@@ -226,6 +233,8 @@ def make_config(family, dx, dy, T, N, M, D, y, H=None, prior_mean=None, prior_st
     c.stream = stream
     c.prior_kind = int(prior_kind)
     c.hmc_steps = int(hmc_steps)
+    c.nuts_max_depth = int(nuts_max_depth)
+    c.nuts_weight = int(nuts_weight)
     c._keep = keep
     return c
 
@@ -347,6 +356,29 @@ class Handle:
         check(self.lib.smc2_get_trace(self.h, _ptr(anc), _ptr(flag), _ptr(oanc), ctypes.byref(ores)),
               "smc2_get_trace")
         return anc, flag, oanc, bool(ores.value)
+
+    def set_point_trace(self, on=True):
+        check(self.lib.smc2_set_point_trace(self.h, int(bool(on))), "smc2_set_point_trace")
+
+    def point_trace(self, point):
+        """(pf_anc [N][T][M], pf_flag [N][T]) of leapfrog point `point` of the last iteration."""
+        import numpy as np
+        anc = np.zeros((self.N, self.T, self.M), dtype=np.uint16)
+        flag = np.zeros((self.N, self.T), dtype=np.uint8)
+        check(self.lib.smc2_get_point_trace(self.h, int(point), _ptr(anc), _ptr(flag)), "smc2_get_point_trace")
+        return anc, flag
+
+    def nuts_trace(self):
+        """Per-sample decisions of the last NUTS move: {"sel": [N] uint64, "merge": [N] uint32,
+        "stop_point": [N], "stop_kind": [N]} (smc2_get_nuts_trace)."""
+        import numpy as np
+        sel = np.zeros(self.N, dtype=np.uint64)
+        merge = np.zeros(self.N, dtype=np.uint32)
+        sp = np.zeros(self.N, dtype=np.int32)
+        sk = np.zeros(self.N, dtype=np.int32)
+        check(self.lib.smc2_get_nuts_trace(self.h, _ptr(sel), _ptr(merge), _ptr(sp), _ptr(sk)),
+              "smc2_get_nuts_trace")
+        return {"sel": sel, "merge": merge, "stop_point": sp, "stop_kind": sk}
 
     def stream_ptr(self):
         """The cudaStream_t (an int) on which the handle enqueues its work."""
@@ -537,7 +569,9 @@ def config_for(workload, **kw):
     args = dict(proposal=PROPOSALS[workload.proposal], gamma=workload.gamma, K_iters=workload.K,
                 seed=workload.seed, prior_mean=workload.prior_mean, prior_std=workload.prior_std,
                 prior_kind=getattr(workload, "prior_kind", PRIOR_GAUSSIAN),
-                hmc_steps=getattr(workload, "hmc_steps", 1))
+                hmc_steps=getattr(workload, "hmc_steps", 1),
+                nuts_max_depth=getattr(workload, "nuts_depth", 3),
+                nuts_weight=getattr(workload, "nuts_weight", NUTS_REVERSAL))
     args.update(kw)
     return make_config(workload.family, workload.dx, workload.dy, workload.T, workload.N, workload.M,
                        workload.D, workload.y, workload.H, **args)

@@ -79,6 +79,8 @@ extern "C" void smc2_config_init(smc2_config* c) {
     c->d_y = 1;
     c->proposal = SMC2_LANGEVIN;
     c->hmc_steps = 1;
+    c->nuts_max_depth = 3;
+    c->nuts_weight = SMC2_NUTS_REVERSAL;
     c->gamma = 0.1;
     c->K_iters = 10;
     c->pf_resample = SMC2_SYSTEMATIC;
@@ -225,10 +227,17 @@ int smc2::validate(const smc2_config* c, int* D) {
     if (!(c->ess_frac >= 0.f && c->ess_frac <= 1.f)) return fail(SMC2_E_INVAL, "ess_frac must be in [0, 1]");
     if (c->pf_resample != SMC2_SYSTEMATIC && c->pf_resample != SMC2_MULTINOMIAL)
         return fail(SMC2_E_INVAL, "unknown pf_resample");
-    if (c->proposal != SMC2_RW && c->proposal != SMC2_LANGEVIN && c->proposal != SMC2_HMC)
+    if (c->proposal != SMC2_RW && c->proposal != SMC2_LANGEVIN && c->proposal != SMC2_HMC &&
+        c->proposal != SMC2_NUTS)
         return fail(SMC2_E_INVAL, "unknown proposal");
     if (c->proposal == SMC2_HMC && (c->hmc_steps < 1 || c->hmc_steps > 64))
         return fail(SMC2_E_INVAL, "hmc_steps must be in [1, 64]");
+    if (c->proposal == SMC2_NUTS) {
+        if (c->nuts_max_depth < 1 || c->nuts_max_depth > kNutsMaxDepth)
+            return fail(SMC2_E_INVAL, "nuts_max_depth must be in [1, 6]");
+        if (c->nuts_weight != SMC2_NUTS_REVERSAL && c->nuts_weight != SMC2_NUTS_MOMENTUM_REVERSAL)
+            return fail(SMC2_E_INVAL, "unknown nuts_weight");
+    }
     if (!(c->gamma > 0.0)) return fail(SMC2_E_INVAL, "gamma must be positive");
     if (c->ckpt_every < 0) return fail(SMC2_E_INVAL, "ckpt_every must be >= 0");
     const int P = c->particles_per_thread;
@@ -272,6 +281,9 @@ void smc2::plan_sizes(const smc2_config* c, int D, int kc, Sizes* s) {
     s->flag = N * T;
     s->steps = 2 * N * (T + 1) * sizeof(float);
     s->state = sizeof(double) * (N * D * 6 + N * 7 + 2 * D + kStatsHead + 2 * D) + sizeof(int) * N + 64;
+    if (c->proposal == SMC2_NUTS)
+        s->state += N * (sizeof(double) * NutsLayout(D, c->nuts_max_depth).stride + 4 * sizeof(int) +
+                         sizeof(unsigned long long) + sizeof(uint32_t));
     s->obs = sizeof(float) * (T * c->d_y + c->d_y * DX);
     s->total = s->xck + s->lwck + s->xseg + s->lwseg + s->anc + s->offs + s->flag + s->steps + s->state + s->obs;
 }
@@ -314,7 +326,8 @@ static int choose_chunk(const smc2_handle* h) {
 
 static void free_handle_memory(smc2_handle* h) {
     void* ptrs[] = {h->y, h->H, h->prior_m, h->prior_s, h->theta, h->theta_new, h->logw, h->logpi,
-                    h->gradpi, h->loglik, h->ll_new, h->grad_new, h->tmp, h->mom, h->ke, h->stats, h->outer_anc,
+                    h->gradpi, h->loglik, h->ll_new, h->grad_new, h->tmp, h->mom, h->ke, h->nuts_state,
+                    h->nuts_int, h->nuts_sel, h->nuts_merge, h->pt_anc, h->pt_flag, h->stats, h->outer_anc,
                     h->k_dev, h->status, h->ties, h->xck, h->lwck, h->xseg, h->lwseg, h->anc, h->offs, h->flag, h->mstep, h->lstep};
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, h->stream);
@@ -378,6 +391,7 @@ extern "C" int smc2_create(const smc2_config* cfg, smc2_handle** out) {
     }
     const size_t N = cfg->N, T = cfg->T;
     struct Alloc { void** p; size_t bytes; };
+    const bool nuts = cfg->proposal == SMC2_NUTS;
     Alloc allocs[] = {
         {(void**)&h->y, sizeof(float) * T * cfg->d_y},
         {(void**)&h->H, sizeof(float) * cfg->d_y * cfg->d_x},
@@ -394,6 +408,10 @@ extern "C" int smc2_create(const smc2_config* cfg, smc2_handle** out) {
         {(void**)&h->tmp, sizeof(double) * N * D},
         {(void**)&h->mom, sizeof(double) * N * D},
         {(void**)&h->ke, sizeof(double) * N},
+        {(void**)&h->nuts_state, nuts ? sizeof(double) * N * NutsLayout(D, cfg->nuts_max_depth).stride : 0},
+        {(void**)&h->nuts_int, nuts ? sizeof(int) * 4 * N : 0},
+        {(void**)&h->nuts_sel, nuts ? sizeof(unsigned long long) * N : 0},
+        {(void**)&h->nuts_merge, nuts ? sizeof(uint32_t) * N : 0},
         {(void**)&h->stats, sizeof(double) * (kStatsHead + 2 * D)},
         {(void**)&h->outer_anc, sizeof(int) * N},
         {(void**)&h->k_dev, sizeof(uint32_t)},
@@ -672,16 +690,46 @@ OuterArgs smc2::make_outer_args(smc2_handle* h) {
     o.hmc = h->cfg.proposal == SMC2_HMC;
     o.mom = h->mom;
     o.ke = h->ke;
+    o.nuts = h->cfg.proposal == SMC2_NUTS;
+    o.nuts_depth = h->cfg.nuts_max_depth;
+    o.nuts_unit = h->cfg.nuts_weight == SMC2_NUTS_REVERSAL;
+    o.nuts_state = h->nuts_state;
+    o.nuts_int = h->nuts_int;
+    o.nuts_sel = h->nuts_sel;
+    o.nuts_merge = h->nuts_merge;
     o.stats = h->stats;
     o.outer_anc = h->outer_anc;
     return o;
 }
 
 // Kernel launches of one iteration after the first: propose, the filter passes of every
-// leapfrog point (one point for RW and Langevin), the leapfrog kicks between them, update.
+// leapfrog point (one point for RW and Langevin), the leapfrog kicks between them, update;
+// NUTS: begin, the filter passes and the point kernel of each of its 2^J - 1 points, finish,
+// update.
 int smc2::launches_per_step(const smc2_handle* h) {
+    if (h->cfg.proposal == SMC2_NUTS) {
+        const int P = (1 << h->cfg.nuts_max_depth) - 1;
+        return 1 + P * (filter_launches(h, h->cfg.N, true) + 1) + 1 + kOuterUpdateLaunches;
+    }
     const int L = h->cfg.proposal == SMC2_HMC ? h->cfg.hmc_steps : 1;
     return 1 + L * filter_launches(h, h->cfg.N, true) + (L - 1) + kOuterUpdateLaunches;
+}
+
+// Leapfrog points (filter launches) of an iteration after the first.
+static int points_per_step(const smc2_handle* h) {
+    if (h->cfg.proposal == SMC2_NUTS) return (1 << h->cfg.nuts_max_depth) - 1;
+    if (h->cfg.proposal == SMC2_HMC) return h->cfg.hmc_steps;
+    return 1;
+}
+
+// With point tracing on, keep the tape of the filter launch at point s.
+static int keep_point_tape(smc2_handle* h, int s) {
+    if (!h->point_trace || s >= h->pt_points) return SMC2_OK;
+    const size_t rows = (size_t)h->cfg.N * h->cfg.T;
+    const size_t anc = rows * tape_stride(h->cfg.M);
+    CUDA_TRY(cudaMemcpyAsync(h->pt_anc + s * anc, h->anc, sizeof(uint16_t) * anc, cudaMemcpyDeviceToDevice, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(h->pt_flag + s * rows, h->flag, rows, cudaMemcpyDeviceToDevice, h->stream));
+    return SMC2_OK;
 }
 
 int smc2::enqueue_step(smc2_handle* h) {
@@ -689,6 +737,24 @@ int smc2::enqueue_step(smc2_handle* h) {
     // the iteration's resampling diagnostics start from zero (a memset node in the step graph)
     CUDA_TRY(cudaMemsetAsync(h->ties, 0, 2 * sizeof(unsigned long long), h->stream));
     // iteration 1 draws from the prior: every proposal takes the same path there
+    if (o.nuts && h->k >= 1) {
+        // NUTS: the trajectory points of all samples in lockstep (timing mode times the
+        // filter passes at the last point)
+        const int P = (1 << o.nuts_depth) - 1;
+        if (launch_nuts_begin(o, h->stream)) return fail(SMC2_E_CUDA, "NUTS begin launch failed");
+        const PFArgs a = make_pf_args(h, h->theta_new, h->cfg.N, 0u, 0u, h->k_dev, h->ll_new, h->grad_new);
+        for (int s = 0; s < P; ++s) {
+            int rc = launch_filters(h, a, h->timing && s == P - 1);
+            if (!rc) rc = keep_point_tape(h, s);
+            if (rc) return rc;
+            if (launch_nuts_point(o, s, h->stream)) return fail(SMC2_E_CUDA, "NUTS point launch failed");
+        }
+        if (launch_nuts_finish(o, h->stream)) return fail(SMC2_E_CUDA, "NUTS finish launch failed");
+        if (launch_outer_update(o, h->stream)) return fail(SMC2_E_CUDA, "outer update launch failed");
+        count_launches(1 + P + 1 + kOuterUpdateLaunches);
+        h->nuts_ran = true;
+        return SMC2_OK;
+    }
     const bool hmc = o.hmc && h->k >= 1;
     const int L = hmc ? h->cfg.hmc_steps : 1;
     if ((hmc ? launch_hmc_start(o, h->stream) : launch_outer_propose(o, h->stream)))
@@ -697,6 +763,7 @@ int smc2::enqueue_step(smc2_handle* h) {
     for (int l = 0; l < L; ++l) {
         // timing mode times the filter passes at the last leapfrog point (one launch each)
         int rc = launch_filters(h, a, h->timing && l == L - 1);
+        if (!rc && h->k >= 1) rc = keep_point_tape(h, l);
         if (rc) return rc;
         if (l < L - 1 && launch_hmc_leap(o, h->stream)) return fail(SMC2_E_CUDA, "leapfrog launch failed");
     }
@@ -767,12 +834,13 @@ static void capture_step(smc2_handle* h, bool timed) {
 int smc2::step_async(smc2_handle* h) {
     // first iteration eagerly (sets kernel attributes); later ones replay a captured graph,
     // with timing on the same graph plus the event-record nodes of the filter passes
-    if (h->k >= 1 && !h->no_graph) {
+    // (point tracing adds copies to the step: it runs eagerly)
+    if (h->k >= 1 && !h->no_graph && !h->point_trace) {
         if (!h->timing && !h->graph_exec) capture_step(h, false);
         if (h->timing && !h->graph_timed) capture_step(h, true);
     }
     cudaGraphExec_t ge = h->timing ? h->graph_timed : h->graph_exec;
-    if (h->k >= 1 && ge) {
+    if (h->k >= 1 && ge && !h->point_trace) {
         if (h->timing) {
             cudaEvent_t* ev = &h->tev[3 * (h->tev_next % kTimingSlots)];
             for (int k = 0; k < 3; ++k)
@@ -876,9 +944,9 @@ extern "C" int smc2_step(smc2_handle* h, smc2_stats* out) {
 extern "C" int smc2_step_filters(smc2_handle* h, int row0, int n, double* loglik_dev, double* grad_dev) {
     if (!h) return fail(SMC2_E_INVAL, "handle is NULL");
     if (h->split_pending) return fail(SMC2_E_INVAL, "smc2_step_update must follow smc2_step_filters");
-    if (h->cfg.proposal == SMC2_HMC)
+    if (h->cfg.proposal == SMC2_HMC || h->cfg.proposal == SMC2_NUTS)
         return fail(SMC2_E_INVAL, "the split step supports the random-walk and Langevin proposals "
-                                  "(an HMC move needs every sample's filters at each leapfrog point)");
+                                  "(an HMC or NUTS move needs every sample's filters at each leapfrog point)");
     if (row0 < 0 || n < 0 || row0 + n > h->cfg.N) return fail(SMC2_E_INVAL, "rows must lie in [0, N)");
     if (n > 0 && (!loglik_dev || !grad_dev)) return fail(SMC2_E_INVAL, "loglik and grad must not be NULL");
     const OuterArgs o = make_outer_args(h);
@@ -950,6 +1018,57 @@ extern "C" int smc2_get_trace(smc2_handle* h, uint16_t* pf_anc, uint8_t* pf_flag
     CUDA_TRY(cudaStreamSynchronize(h->stream));
     if (pf_flag)  // the device flags carry a gather-adjoint hint in bit 1
         for (size_t i = 0; i < N * T; ++i) pf_flag[i] &= 1u;
+    return SMC2_OK;
+}
+
+extern "C" int smc2_set_point_trace(smc2_handle* h, int on) {
+    if (!h) return fail(SMC2_E_INVAL, "handle is NULL");
+    if (on && !h->pt_anc) {
+        const int P = points_per_step(h);
+        const size_t rows = (size_t)h->cfg.N * h->cfg.T;
+        cudaError_t e = cudaMallocAsync((void**)&h->pt_anc, sizeof(uint16_t) * P * rows * tape_stride(h->cfg.M), h->stream);
+        if (e == cudaSuccess) e = cudaMallocAsync((void**)&h->pt_flag, P * rows, h->stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(e == cudaErrorMemoryAllocation ? SMC2_E_NOMEM : SMC2_E_CUDA, "point trace allocation failed");
+        }
+        CUDA_TRY(cudaMemsetAsync(h->pt_flag, 0, P * rows, h->stream));
+        h->pt_points = P;
+    }
+    h->point_trace = on != 0;
+    return SMC2_OK;
+}
+
+extern "C" int smc2_get_point_trace(smc2_handle* h, int point, uint16_t* pf_anc, uint8_t* pf_flag) {
+    if (!h) return fail(SMC2_E_INVAL, "handle is NULL");
+    if (!h->pt_anc || point < 0 || point >= h->pt_points)
+        return fail(SMC2_E_INVAL, "point tracing is off or the point is out of range");
+    const size_t N = h->cfg.N, T = h->cfg.T, M = h->cfg.M, rows = N * T;
+    if (pf_anc)
+        CUDA_TRY(cudaMemcpy2DAsync(pf_anc, sizeof(uint16_t) * M, h->pt_anc + point * rows * tape_stride((int)M),
+                                   sizeof(uint16_t) * tape_stride((int)M), sizeof(uint16_t) * M, rows,
+                                   cudaMemcpyDeviceToHost, h->stream));
+    if (pf_flag) CUDA_TRY(cudaMemcpyAsync(pf_flag, h->pt_flag + point * rows, rows, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (pf_flag)
+        for (size_t i = 0; i < rows; ++i) pf_flag[i] &= 1u;
+    return SMC2_OK;
+}
+
+extern "C" int smc2_get_nuts_trace(smc2_handle* h, uint64_t* sel, uint32_t* merge, int32_t* stop_point,
+                                   int32_t* stop_kind) {
+    if (!h) return fail(SMC2_E_INVAL, "handle is NULL");
+    if (h->cfg.proposal != SMC2_NUTS || !h->nuts_ran) return fail(SMC2_E_INVAL, "no NUTS move has run");
+    const size_t N = h->cfg.N;
+    std::vector<int> ni(4 * N);
+    if (sel) CUDA_TRY(cudaMemcpyAsync(sel, h->nuts_sel, sizeof(uint64_t) * N, cudaMemcpyDeviceToHost, h->stream));
+    if (merge) CUDA_TRY(cudaMemcpyAsync(merge, h->nuts_merge, sizeof(uint32_t) * N, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(ni.data(), h->nuts_int, sizeof(int) * 4 * N, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    for (size_t i = 0; i < N; ++i) {
+        if (stop_point) stop_point[i] = ni[4 * i + kNuStopPoint];
+        if (stop_kind) stop_kind[i] = ni[4 * i + kNuStopKind];
+    }
     return SMC2_OK;
 }
 

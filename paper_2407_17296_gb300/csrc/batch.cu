@@ -7,7 +7,7 @@
 // adjoint ring are fused: one forward and one adjoint launch over all their filters, the blocks
 // taking (job, filter) items from a device counter, longest filters first.  The fused passes run
 // on the stream of the group's longest job, which first waits for the other jobs' proposals;
-// their streams wait for the passes before their updates.  A job alone in its group (and an HMC
+// their streams wait for the passes before their updates.  A job alone in its group (and an HMC or NUTS
 // move, whose leapfrog points run several filter passes) steps as smc2_step does.  The results
 // are those of smc2_step on each job, bit for bit.
 #include <cuda_runtime.h>
@@ -101,21 +101,21 @@ extern "C" int smc2_batch_destroy(smc2_batch* b) {
 int smc2_batch_step_async(smc2_batch* b, smc2_handle* const* hs, int n) {
     if (!b || (n > 0 && !hs)) return fail(SMC2_E_INVAL, "NULL argument");
     if (n < 0 || n > b->max_jobs) return fail(SMC2_E_INVAL, "n must be in [0, max_jobs]");
-    // fusable jobs: everything but HMC moves after the first iteration (their leapfrog points
-    // run several filter passes a step); those step on their own
+    // fusable jobs: everything but HMC and NUTS moves after the first iteration (their
+    // leapfrog points run several filter passes a step); those step on their own
     struct Item {
         int idx;
         smc2_handle* h;
     };
     std::map<std::tuple<const void*, const void*, int, int>, std::vector<Item>> groups;
-    std::vector<smc2_handle*> own;  // HMC moves
+    std::vector<smc2_handle*> own;  // HMC and NUTS moves
     for (int i = 0; i < n; ++i) {
         smc2_handle* h = hs[i];
         if (!h) return fail(SMC2_E_INVAL, "NULL handle");
         for (int k = 0; k < i; ++k)
             if (hs[k] == h) return fail(SMC2_E_INVAL, "a handle appears twice");
         if (h->split_pending) return fail(SMC2_E_INVAL, "a handle has a split step pending");
-        if (h->cfg.proposal == SMC2_HMC && h->k >= 1) {
+        if ((h->cfg.proposal == SMC2_HMC || h->cfg.proposal == SMC2_NUTS) && h->k >= 1) {
             own.push_back(h);
             continue;
         }
@@ -230,7 +230,7 @@ int smc2_batch_step_async(smc2_batch* b, smc2_handle* const* hs, int n) {
         first_off += ng + 1;
         ++g;
     }
-    // HMC moves and jobs alone in their group step on their own
+    // HMC and NUTS moves and jobs alone in their group step on their own
     for (smc2_handle* h : own) {
         const int rc = step_async(h);
         if (rc) return rc;

@@ -12,6 +12,10 @@
 // v ~ N(0, gamma^2 I), each step v += F(theta); theta += v; v += F(theta) (one step is the
 // SMC1 move), the filters run at every new point; the momentum-reversal L-kernel gives
 //   log w += log pi(theta_L) - log pi(theta_0) + |v_0|^2/(2 gamma^2) - |v_L|^2/(2 gamma^2).
+// NUTS (the other extension Sec. V names): the same leapfrog doubles a trajectory in random
+// directions until a U-turn, a divergent point or the maximum depth; the new sample is drawn
+// from it with weights exp(-H) (nuts_* kernels below); weight: the NUTS kernel's own
+// reversal (log w unchanged) or the momentum-reversal weight above at the selected point.
 // Then: normalise (Eq. normalise_smc2), estimate f~_k = sum w~ theta (Eq. realised_estimates),
 // l_k = (sum w)^2 / sum w^2 (Eq. recycling_I), ESS (Eq. ess_smc2) and, if ESS < N/2,
 // systematic resampling with one uniform per iteration (Philox stream 4), ancestors
@@ -181,6 +185,247 @@ __global__ void hmc_leap_kernel(OuterArgs a) {
     if (!ok) a.ke[i] = __longlong_as_double(0x7ff8000000000000ll);
 }
 
+// ---------------------------------------------------------------- NUTS move
+// One thread a sample; all samples build their trajectories in lockstep, point s = 2^j - 1 + n
+// being point n of doubling j.  In displacement form a leapfrog step in direction d from
+// (theta, v) is v_h = v + d F(theta), theta' = theta + d v_h, v' = v_h + d F(theta') with
+// F = 0.5 gamma^2 grad log pi (d = -1 runs the dynamics backwards in time; v stays the
+// forward-time velocity).
+
+__device__ __forceinline__ double logaddexp_d(double a, double b) {
+    if (a == -INFINITY) return b;
+    if (b == -INFINITY) return a;
+    return fmax(a, b) + log1p(exp(-fabs(a - b)));
+}
+
+// grad log prior at th[d] (Gaussian; 0 for the uniform prior, whose pinv[d] is 0)
+__device__ __forceinline__ double prior_grad(const OuterArgs& a, const double* pinv, double th, int d) {
+    return -(th - a.prior_mean[d]) * pinv[d] * pinv[d];
+}
+
+// (theta+ - theta-) . v at both ends of the sub-trajectory built in direction d from
+// (th1, v1) to (th2, v2): a U-turn when either is negative
+__device__ bool nuts_uturn(int D, int d, const double* th1, const double* v1, const double* th2,
+                           const double* v2) {
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < D; ++k) {
+        const double dth = d * (th2[k] - th1[k]);
+        a += dth * v1[k];
+        b += dth * v2[k];
+    }
+    return a < 0.0 || b < 0.0;
+}
+
+__device__ void nuts_stop(const OuterArgs& a, int i, int s, int kind) {
+    int* ni = a.nuts_int + 4 * i;
+    ni[kNuActive] = 0;
+    ni[kNuStopPoint] = s;
+    ni[kNuStopKind] = kind;
+}
+
+// Set up point s of sample i: at the start of doubling j draw its direction and take the
+// trajectory's end on that side as the frontier; then the first half kick and the drift, whose
+// position goes to theta_new for the particle filters.
+__device__ void nuts_prepare(const OuterArgs& a, int i, double* st, const NutsLayout& L, int s,
+                             const PhiloxKey& key) {
+    const int D = a.D;
+    const int j = 31 - __clz(s + 1), n = s + 1 - (1 << j);
+    int* ni = a.nuts_int + 4 * i;
+    if (n == 0) {
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)j, 0u, kStreamNuts, 0u), key);
+        const int d = (w.x >> 31) ? 1 : -1;
+        ni[kNuDir] = d;
+        const int th = d > 0 ? L.thp : L.thm, v = d > 0 ? L.vp : L.vm, g = d > 0 ? L.gp : L.gm;
+        for (int k = 0; k < D; ++k) {
+            st[L.thf + k] = st[th + k];
+            st[L.vf + k] = st[v + k];
+            st[L.gf + k] = st[g + k];
+        }
+        st[L.sc + kNuLswSub] = -INFINITY;
+    }
+    const double dh = ni[kNuDir] * 0.5 * a.gamma * a.gamma;
+    const double d = ni[kNuDir];
+    for (int k = 0; k < D; ++k) {
+        const double vh = st[L.vf + k] + dh * st[L.gf + k];
+        st[L.vh + k] = vh;
+        a.theta_new[(size_t)i * D + k] = st[L.thf + k] + d * vh;
+    }
+}
+
+// Iteration k > 1: momentum v_0 = gamma xi (Philox stream 3, as HMC), the trajectory {theta_0}
+// with log-weight -H_0, the selected point theta_0 (with its carried log-likelihood and filter
+// gradient), then point 0.  A sample whose log pi or gradient is not finite is not moved.
+__global__ void nuts_begin_kernel(OuterArgs a) {
+    __shared__ double pinv[65];
+    prior_constants(a, pinv);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.N) return;
+    const int D = a.D;
+    const NutsLayout L(D, a.nuts_depth);
+    double* st = a.nuts_state + (size_t)i * L.stride;
+    const uint32_t k = *a.k_dev + 1u;
+    const PhiloxKey key = philox_key(a.seed_lo, a.seed_hi, k, (uint32_t)i);
+    const double g2 = a.gamma * a.gamma;
+    const double lp0 = a.logpi[i];
+    bool ok = isfinite(lp0);
+    double vv = 0.0;
+    for (int d = 0; d < D; ++d) {
+        const size_t idx = (size_t)i * D + d;
+        const double v = a.gamma * outer_normal(key, d);
+        const double th = a.theta[idx], g = a.gradpi[idx];
+        ok = ok && isfinite(g);
+        st[L.thp + d] = st[L.thm + d] = st[L.ths + d] = th;
+        st[L.vp + d] = st[L.vm + d] = st[L.vs + d] = v;
+        st[L.gp + d] = st[L.gm + d] = g;
+        st[L.gfs + d] = g - prior_grad(a, pinv, th, d);  // the filter's gradient
+        vv += v * v;
+    }
+    const double K0 = 0.5 * vv / g2;
+    st[L.sc + kNuK0] = K0;
+    st[L.sc + kNuLp0] = lp0;
+    st[L.sc + kNuLpS] = lp0;
+    st[L.sc + kNuLlS] = a.loglik[i];
+    a.nuts_sel[i] = 0ull;
+    a.nuts_merge[i] = 0u;
+    int* ni = a.nuts_int + 4 * i;
+    if (!ok) {
+        nuts_stop(a, i, -1, 4);
+        for (int d = 0; d < D; ++d) a.theta_new[(size_t)i * D + d] = st[L.thp + d];
+        return;
+    }
+    const double H0 = -lp0 + K0;
+    st[L.sc + kNuH0] = H0;
+    st[L.sc + kNuLsw] = -H0;
+    ni[kNuActive] = 1;
+    ni[kNuStopPoint] = (1 << a.nuts_depth) - 2;
+    ni[kNuStopKind] = 0;
+    nuts_prepare(a, i, st, L, 0, key);
+}
+
+// After the filter passes at point s: complete the point of every sample still building
+// (second half kick with grad log pi = grad log prior + the filter's gradient, energy H),
+// stop at a divergent or non-finite point, uniform progressive sampling of the candidate,
+// the U-turn checks of the blocks of 2, 4, ... points this point completes; at the end of a
+// doubling the biased progressive merge, the new end, the whole trajectory's U-turn check and
+// the depth limit; then prepare point s + 1.
+__global__ void nuts_point_kernel(OuterArgs a, int s) {
+    __shared__ double pinv[65];
+    prior_constants(a, pinv);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.N) return;
+    int* ni = a.nuts_int + 4 * i;
+    if (!ni[kNuActive]) return;
+    const int D = a.D, J = a.nuts_depth;
+    const NutsLayout L(D, J);
+    double* st = a.nuts_state + (size_t)i * L.stride;
+    double* sc = st + L.sc;
+    const uint32_t k = *a.k_dev + 1u;
+    const PhiloxKey key = philox_key(a.seed_lo, a.seed_hi, k, (uint32_t)i);
+    const int j = 31 - __clz(s + 1), n = s + 1 - (1 << j);
+    const int d = ni[kNuDir];
+    const double g2 = a.gamma * a.gamma, dh = d * 0.5 * g2;
+    const double* th = a.theta_new + (size_t)i * D;
+    const double lln = a.ll_new[i];
+    const double lp = (lln > -INFINITY) ? log_prior_at(a, th, pinv) + lln : -INFINITY;
+    bool broken = !isfinite(lp);
+    double vv = 0.0;
+    // the new point becomes the frontier (the previous frontier is no longer needed)
+    for (int q = 0; q < D; ++q) {
+        const double g = prior_grad(a, pinv, th[q], q) + a.grad_new[(size_t)i * D + q];
+        broken = broken || !isfinite(g);
+        const double v = st[L.vh + q] + dh * g;
+        st[L.thf + q] = th[q];
+        st[L.vf + q] = v;
+        st[L.gf + q] = g;
+        vv += v * v;
+    }
+    const double H = -lp + 0.5 * vv / g2;
+    if (broken || !(H - sc[kNuH0] <= kNutsDeltaMax)) {
+        nuts_stop(a, i, s, 2);
+        return;
+    }
+    // uniform progressive sampling inside the doubling
+    const double lsw_new = logaddexp_d(sc[kNuLswSub], -H);
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)j, (uint32_t)n, kStreamNuts, 0u), key);
+    if ((-H - lsw_new) - log(u01_open_d(w.y)) >= 0.0) {
+        for (int q = 0; q < D; ++q) {
+            st[L.thc + q] = th[q];
+            st[L.vc + q] = st[L.vf + q];
+            st[L.gfc + q] = a.grad_new[(size_t)i * D + q];
+        }
+        sc[kNuLpC] = lp;
+        sc[kNuLlC] = lln;
+        a.nuts_sel[i] |= 1ull << s;
+    }
+    sc[kNuLswSub] = lsw_new;
+    // no-U-turn checks of the completed blocks of 2^l points (l = 1 .. j); a block's first
+    // point is kept in slot l when it is built
+    bool uturn = false;
+    for (int l = 1; l <= j; ++l) {
+        double* ck = st + L.ck + 2 * D * l;
+        if (n % (1 << l) == 0)
+            for (int q = 0; q < D; ++q) {
+                ck[q] = th[q];
+                ck[D + q] = st[L.vf + q];
+            }
+        if ((n + 1) % (1 << l) == 0) uturn = uturn || nuts_uturn(D, d, ck, ck + D, th, st + L.vf);
+    }
+    if (uturn) {
+        nuts_stop(a, i, s, 1);
+        return;
+    }
+    if (n + 1 == (1 << j)) {
+        // biased progressive sampling: the doubling's candidate replaces the selected point
+        // with probability min(1, W_new / W_old)
+        const uint4 w0 = philox4x32_10(make_uint4((uint32_t)j, 0u, kStreamNuts, 0u), key);
+        if ((sc[kNuLswSub] - sc[kNuLsw]) - log(u01_open_d(w0.z)) >= 0.0) {
+            for (int q = 0; q < D; ++q) {
+                st[L.ths + q] = st[L.thc + q];
+                st[L.vs + q] = st[L.vc + q];
+                st[L.gfs + q] = st[L.gfc + q];
+            }
+            sc[kNuLpS] = sc[kNuLpC];
+            sc[kNuLlS] = sc[kNuLlC];
+            a.nuts_merge[i] |= 1u << j;
+        }
+        sc[kNuLsw] = logaddexp_d(sc[kNuLsw], sc[kNuLswSub]);
+        const int te = d > 0 ? L.thp : L.thm, ve = d > 0 ? L.vp : L.vm, ge = d > 0 ? L.gp : L.gm;
+        for (int q = 0; q < D; ++q) {
+            st[te + q] = st[L.thf + q];
+            st[ve + q] = st[L.vf + q];
+            st[ge + q] = st[L.gf + q];
+        }
+        if (nuts_uturn(D, 1, st + L.thm, st + L.vm, st + L.thp, st + L.vp)) {
+            nuts_stop(a, i, s, 3);
+            return;
+        }
+        if (j + 1 == J) {
+            nuts_stop(a, i, s, 0);
+            return;
+        }
+    }
+    if (s + 1 < (1 << J) - 1) nuts_prepare(a, i, st, L, s + 1, key);
+}
+
+// The selected point of every sample becomes its proposal (theta_new, its log-likelihood and
+// filter gradient), with the weight correction of the momentum-reversal reading in ke.
+__global__ void nuts_finish_kernel(OuterArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.N) return;
+    const int D = a.D;
+    const NutsLayout L(D, a.nuts_depth);
+    const double* st = a.nuts_state + (size_t)i * L.stride;
+    double vv = 0.0;
+    for (int q = 0; q < D; ++q) {
+        const size_t idx = (size_t)i * D + q;
+        a.theta_new[idx] = st[L.ths + q];
+        a.grad_new[idx] = st[L.gfs + q];
+        vv += st[L.vs + q] * st[L.vs + q];
+    }
+    a.ll_new[i] = st[L.sc + kNuLlS];
+    a.ke[i] = st[L.sc + kNuK0] - 0.5 * vv / (a.gamma * a.gamma);
+}
+
 // 1. pseudo-marginal update of every sample with its particle-filter result (one thread a
 //    sample, any number of blocks)
 __global__ void outer_weight_kernel(OuterArgs a) {
@@ -198,7 +443,7 @@ __global__ void outer_weight_kernel(OuterArgs a) {
     // is not finite (e.g. FP32 overflow under explosive dynamics) the sample cannot be
     // weighted or moved and carries weight zero, as does any non-finite weight
     bool grad_ok = true;
-    if (a.langevin || a.hmc)
+    if (a.langevin || a.hmc || a.nuts)
         for (int d = 0; d < D; ++d) grad_ok = grad_ok && isfinite(a.grad_new[(size_t)i * D + d]);
     double lw;
     if (k == 1u) {
@@ -230,8 +475,11 @@ __global__ void outer_weight_kernel(OuterArgs a) {
                     kl += vl * vl;
                 }
                 corr = a.ke[i] - 0.5 * kl / g2;  // NaN for a broken trajectory
+            } else if (a.nuts) {
+                corr = a.ke[i];  // |v_0|^2/(2 gamma^2) - |v*|^2/(2 gamma^2) at the selected point
             }
-            lw = lw + (lpn - a.logpi[i]) + corr;
+            // the NUTS kernel's own reversal leaves the weight unchanged
+            if (!(a.nuts && a.nuts_unit)) lw = lw + (lpn - a.logpi[i]) + corr;
         } else {
             lw = -INFINITY;
         }
@@ -411,6 +659,21 @@ int launch_hmc_start(const OuterArgs& a, void* stream) {
 
 int launch_hmc_leap(const OuterArgs& a, void* stream) {
     hmc_leap_kernel<<<(a.N + 127) / 128, 128, 0, static_cast<cudaStream_t>(stream)>>>(a);
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+int launch_nuts_begin(const OuterArgs& a, void* stream) {
+    nuts_begin_kernel<<<(a.N + 127) / 128, 128, 0, static_cast<cudaStream_t>(stream)>>>(a);
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+int launch_nuts_point(const OuterArgs& a, int s, void* stream) {
+    nuts_point_kernel<<<(a.N + 127) / 128, 128, 0, static_cast<cudaStream_t>(stream)>>>(a, s);
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+int launch_nuts_finish(const OuterArgs& a, void* stream) {
+    nuts_finish_kernel<<<(a.N + 127) / 128, 128, 0, static_cast<cudaStream_t>(stream)>>>(a);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 

@@ -15,6 +15,8 @@
 //   stream 2 initial particles (t = 0, same normal indexing as stream 0)
 //   stream 3 outer-sampler normals (t = 0, normal index d)
 //   stream 4 outer-sampler resampling uniform (t = 0, call 0 word 0, row 0)
+//   stream 5 NUTS move (t = doubling j, call = point n of the doubling: word 0 of call 0 gives
+//            the direction, word 2 of call 0 the merge uniform, word 1 the selection uniform)
 // Uniforms: (0,1] = ((u >> 8) + 1) * 2^-24 (exact in FP32); [0,1) = (u >> 8) * 2^-24.
 // Box-Muller on (u0, u1): r = sqrt(-2 ln U(0,1](u0)), phi = 2 pi U[0,1)(u1),
 // z0 = r cos phi, z1 = r sin phi; (u2, u3) give z2, z3 the same way.
@@ -24,7 +26,7 @@
 namespace smc2 {
 
 enum : uint32_t { kStreamProp = 0, kStreamResample = 1, kStreamInit = 2,
-                  kStreamOuterXi = 3, kStreamOuterNu = 4 };
+                  kStreamOuterXi = 3, kStreamOuterNu = 4, kStreamNuts = 5 };
 
 // The key with its ten round keys (the Weyl schedule k + r * W), expanded once per filter:
 // a filter draws thousands of blocks with the same key.

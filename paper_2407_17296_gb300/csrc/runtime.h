@@ -64,6 +64,18 @@ struct smc2_handle {
     double *theta = nullptr, *theta_new = nullptr, *logw = nullptr, *logpi = nullptr, *gradpi = nullptr;
     double *loglik = nullptr, *ll_new = nullptr, *grad_new = nullptr, *tmp = nullptr, *stats = nullptr;
     double *mom = nullptr, *ke = nullptr;  // HMC: leapfrog momentum [N][D], start kinetic energy [N]
+    // NUTS: per-sample trajectory state, integer state and trace (OuterArgs::nuts_*)
+    double* nuts_state = nullptr;
+    int* nuts_int = nullptr;
+    unsigned long long* nuts_sel = nullptr;
+    uint32_t* nuts_merge = nullptr;
+    bool nuts_ran = false;  // a NUTS move has run (its trace is readable)
+    // per-point tapes (smc2_set_point_trace): the ancestor tape and flags of every leapfrog
+    // point's filter launch, [points][N][T][tape stride] and [points][N][T]
+    bool point_trace = false;
+    int pt_points = 0;
+    uint16_t* pt_anc = nullptr;
+    uint8_t* pt_flag = nullptr;
     int* outer_anc = nullptr;
     uint32_t* k_dev = nullptr;
     int* status = nullptr;      // device status word of the handle's kernels

@@ -59,6 +59,8 @@ class Workload:
     extra: dict = field(default_factory=dict)
     prior_kind: int = GAUSSIAN_PRIOR          # UNIFORM_PRIOR: U(prior_mean[d], prior_std[d])
     hmc_steps: int = 1                        # leapfrog steps of the "hmc" proposal
+    nuts_depth: int = 3                       # maximum doublings of the "nuts" proposal
+    nuts_weight: int = 0                      # 0: the NUTS kernel's reversal, 1: momentum reversal
 
     @property
     def particle_steps(self) -> int:
@@ -77,7 +79,7 @@ class Workload:
 def step_sizes(T: int):
     s = np.sqrt(500.0 / T)
     # an HMC move takes Langevin-sized leapfrog steps (one step is the Langevin move)
-    return {"langevin": 0.085 * s, "rw": 0.175 * s, "hmc": 0.085 * s}
+    return {"langevin": 0.085 * s, "rw": 0.175 * s, "hmc": 0.085 * s, "nuts": 0.085 * s}
 
 
 def simulate_lg(rng, a, q, r, H, T):
@@ -146,7 +148,7 @@ def lg16(T=200, N=2048, M=1024, K=30, proposal="langevin") -> Workload:
     # the paper's step sizes were tuned for its 3-parameter model; with 48 parameters a
     # Langevin step of 0.134 throws samples into explosive dynamics within a few iterations,
     # 0.03 (random walk 0.06) keeps the population alive (scaled with sqrt(200/T))
-    gam = {"langevin": 0.03, "rw": 0.06, "hmc": 0.03}[proposal] * np.sqrt(200.0 / T)
+    gam = {"langevin": 0.03, "rw": 0.06, "hmc": 0.03, "nuts": 0.03}[proposal] * np.sqrt(200.0 / T)
     return Workload("lg16", LG_DIAG, dx, dy, 3 * dx, T, N, M, K, th, y, None, proposal,
                     gam, 780, seed, prior_mean=m0, prior_std=s0)
 
@@ -162,7 +164,7 @@ def lgssm(T=500, N=64, M=250, K=15, proposal="langevin") -> Workload:
     lo = np.array([-1.0, 0.0, 0.0])
     hi = np.array([1.0, 5.0, 5.0])
     return Workload("lgssm", LG_OPT, 1, 1, 3, T, N, M, K, th, y, None, proposal,
-                    {"langevin": 0.085, "rw": 0.175, "hmc": 0.085}[proposal], 781, seed,
+                    {"langevin": 0.085, "rw": 0.175, "hmc": 0.085, "nuts": 0.085}[proposal], 781, seed,
                     prior_mean=lo, prior_std=hi, prior_kind=UNIFORM_PRIOR)
 
 

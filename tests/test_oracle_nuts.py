@@ -26,8 +26,9 @@ import oracle.smc2 as smc2
 
 
 def _gauss(mu, sd):
-    """log N(theta; mu, diag(sd^2)) up to a constant, its gradient, and the (ll, g) payload."""
-    def fn(th):
+    """log N(theta; mu, diag(sd^2)) up to a constant, its gradient, and the (ll, g) payload
+    (the point index s that the move passes is not needed)."""
+    def fn(th, s=None):
         z = (th - mu) / sd
         lp = float(-0.5 * np.sum(z * z))
         g = -z / sd
