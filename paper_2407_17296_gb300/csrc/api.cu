@@ -158,7 +158,14 @@ int smc2::model_lanes(const smc2_config* c, bool forward) {
 }
 
 bool smc2::variant_fits(const smc2_config* c, int P, int regs, bool forward) {
-    const int threads = pf_threads(c->M, P, model_lanes(c, forward));
+    const int G = model_lanes(c, forward);
+    const int threads = pf_threads(c->M, P, G);
+    if (forward) {
+        int D = 0;
+        if (family_dims(c, &D)) return false;
+        if (SmemLayout(c->M, c->d_x, D, true, G).total + eps_stage_bytes(threads, G, c->d_x, P) > kSmemLimit)
+            return false;
+    }
     return threads <= 1024 && threads * regs <= 65536;
 }
 

@@ -88,6 +88,20 @@ SMC2_HD constexpr bool gather_walk(int G, int DX) { return G == 1 && (DX == 4 ||
 SMC2_HD constexpr int ring_preferred(int DX) { return DX >= 16 ? 3 : (DX == 4 ? 5 : 8); }
 SMC2_HD constexpr int ring_fallback(int DX) { return DX >= 16 ? 0 : (DX >= 4 ? 2 : 4); }
 
+// The forward pass draws a step's normals in a rolled loop into shared memory (one float4 of
+// four normals per Philox call, laid out [call][thread], so a warp's accesses are contiguous)
+// and its unrolled per-particle loop reads them back: a small loop body instead of the
+// unrolled draws of every particle (fewer instruction-cache misses, fewer live registers).
+// It applies when a lane's share of a particle (DL = DX / G dimensions) fills whole calls.
+// Lane-split states stage half of the thread's particles at a time (a smaller region).  The
+// staging region follows the rest of the forward's plan: blockDim.x * eps_chunk(G, P) * DL
+// floats at SmemLayout::total.
+SMC2_HD constexpr bool eps_staged(int G, int DX) { return DX % 4 == 0 && (DX / G) % 4 == 0; }
+SMC2_HD constexpr int eps_chunk(int G, int P) { return (G > 1 && P >= 2) ? P / 2 : P; }
+SMC2_HD inline size_t eps_stage_bytes(int threads, int G, int DX, int P) {
+    return eps_staged(G, DX) ? sizeof(float) * (size_t)threads * eps_chunk(G, P) * (DX / G) : 0;
+}
+
 // Dynamic shared-memory plan (mirrored on the host to size the launch).
 struct SmemLayout {
     size_t xstage, cs, marks, starts, red, scanw, scanwi, misc, dred, bars, total;

@@ -889,6 +889,12 @@ struct Traj {
 
 // ---------------------------------------------------------------- forward pass
 
+// unroll factor of the forward's rolled loop of Philox calls (eps_staged)
+#ifndef SMC2_EPS_UNROLL
+#define SMC2_EPS_UNROLL 4
+#endif
+constexpr int kEpsUnroll = SMC2_EPS_UNROLL;
+
 template <class Mdl, int P>
 __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, const SmemLayout& L,
                                typename Mdl::Params& sprm) {
@@ -1032,7 +1038,50 @@ __device__ void forward_filter(const PFArgs& a, int f, unsigned char* smem, cons
             a.flag[(size_t)f * T + (t - 1)] =
                 resample ? (uint8_t)(1 | (max_offspring > kWalkMaxOffspring ? 2 : 0)) : (uint8_t)0;
 
-        {
+        if constexpr (eps_staged(G, DX)) {
+            // the step's normals through shared memory, PC particles at a time: a rolled loop
+            // of Philox calls (a small loop body), then the unrolled particle loop reads each
+            // particle's normals back (the thread's own slots: no barrier)
+            constexpr int PC = eps_chunk(G, P), CPP = DL / 4, C = PC * CPP;  // calls per particle, per round
+            float4* epsb = reinterpret_cast<float4*>(smem + L.total);
+            const float* yt = a.y + (size_t)(t - 1) * DY + (G > 1 ? gl * DL : 0);
+#pragma unroll
+            for (int c0 = 0; c0 < P; c0 += PC) {
+                // normal n = j*DX + gl*DL + k of particle j = j0 + c0 + c / CPP: call n / 4
+                const uint32_t base = (uint32_t)(((j0 + c0) * DX + gl * DL) / 4);
+#pragma unroll kEpsUnroll
+                for (int c = 0; c < C; ++c) {
+                    const uint32_t call = base + (uint32_t)((c / CPP) * (DX / 4) + c % CPP);
+                    const uint4 w = philox4x32_10(make_uint4((uint32_t)t, call, kStreamProp, 0u), key);
+                    float4 z;
+                    box_muller(w.x, w.y, z.x, z.y);
+                    box_muller(w.z, w.w, z.z, z.w);
+                    epsb[c * blockDim.x + tid] = z;
+                }
+#pragma unroll
+                for (int q = 0; q < PC; ++q) {
+                    const int p = c0 + q;
+                    float e[DL];
+#pragma unroll
+                    for (int k = 0; k < DL; k += 4) {
+                        const float4 v = epsb[((q * DL + k) / 4) * blockDim.x + tid];
+                        e[k] = v.x;
+                        e[k + 1] = v.y;
+                        e[k + 2] = v.z;
+                        e[k + 3] = v.w;
+                    }
+                    float g;
+                    if constexpr (Mdl::kFused) {
+                        g = Mdl::step(prm, x[p], e, yt);
+                    } else {
+                        Mdl::transition(prm, x[p], e);
+                        g = Mdl::loglik(prm, x[p], yt);
+                    }
+                    if constexpr (G > 1) g = group_sum<G>(g) + prm.cst;  // whole-particle log g
+                    lw[p] += g;  // padding particles stay at -inf
+                }
+            }
+        } else {
             float eps[P * DL];
             draw_normals<P, DX, DL>(key, (uint32_t)t, kStreamProp, j0, gl, eps);
             const float* yt = a.y + (size_t)(t - 1) * DY + (G > 1 ? gl * DL : 0);
@@ -1493,7 +1542,8 @@ int blocks_per_sm(K kernel, int threads, size_t smem) {
 template <class Mdl, int P, int REGS>
 int launch_forward(const PFArgs& a, void* stream, int grid) {
     const int threads = pf_threads(a.M, P, Mdl::G);
-    const size_t smem = SmemLayout(a.M, Mdl::DX, Mdl::D, true, Mdl::G).total;
+    const size_t smem = SmemLayout(a.M, Mdl::DX, Mdl::D, true, Mdl::G).total +
+                        eps_stage_bytes(threads, Mdl::G, Mdl::DX, P);
     if (threads > kMaxThreads) return grid ? -1 : 0;
     if (smem + sizeof(typename Mdl::Params) > 48 * 1024) {
         const cudaError_t e = cudaFuncSetAttribute(pf_forward_kernel<Mdl, P, REGS>,
@@ -1627,7 +1677,8 @@ __global__ void __maxnreg__(REGS) pf_backward_multi_kernel(MultiArgs m) {
 template <class Mdl, int P, int REGS>
 int launch_forward_multi(const MultiArgs& m, void* stream, int grid) {
     const int threads = pf_threads(m.M_max, P, Mdl::G);
-    const size_t smem = SmemLayout(m.M_max, Mdl::DX, Mdl::D, true, Mdl::G).total;
+    const size_t smem = SmemLayout(m.M_max, Mdl::DX, Mdl::D, true, Mdl::G).total +
+                        eps_stage_bytes(threads, Mdl::G, Mdl::DX, P);
     if (threads > kMaxThreads) return grid ? -1 : 0;
     const size_t stat = sizeof(typename Mdl::Params) + sizeof(PFArgs) + 64;
     if (smem + stat > 48 * 1024) {
