@@ -44,15 +44,20 @@ ALG_OPS = {"lg1": 55 + 55, "lg4": 155 + 93, "sv": 61 + 66, "lg16": 553 + 241}
 # operation; the key schedule is precomputed): the lower bound reported beside it.
 ALG_OPS_STRICT = {"lg1": 33 + 14, "lg4": 94 + 47, "sv": 36 + 15, "lg16": 333 + 154}
 
-# DRAM bytes per filter of the forward + adjoint pair, measured with ncu on small launches
-# of each workload's shape (every step stored): dram__bytes_read.sum + dram__bytes_write.sum
-# of the forward and the adjoint kernel over 304 filters for the 4-d workload (M = 1024,
-# T = 250; forward 8 particles/thread at 128 registers, adjoint 4 at 128) and for SV
-# (M = 2048, T = 500; forward 8 at 64, adjoint 8 at 128), over 152 filters for the 16-d
-# workload (M = 1024, T = 200; 8 at 128 both); a launch of N filters moves N times this.
-TRAFFIC_PER_FILTER = {("lg4", 1024, 250): (0.783e6 + 1485.469e6 + 1545.521e6 + 3.409e6) / 304,
+# DRAM bytes per filter of the forward + adjoint pair: dram__bytes_read.sum +
+# dram__bytes_write.sum from ncu (one pass, no replay) over the four filter launches of the
+# second SMC2 iteration of the benchmark command itself (two halves, each a forward and an
+# adjoint launch) for the 4-d workload (N = 1024, M = 1024, T = 250; forward 8 particles a
+# thread at 128 registers, adjoint 4 at 128) and the 16-d workload (N = 2048, M = 1024,
+# T = 200; 8 at 128 both), divided by N; for SV (M = 2048, T = 500; forward 8 at 64, adjoint 8
+# at 128) from a capture of 304 filters.  Every step's slice is stored and read back once;
+# the log-weights, tape and first-offspring rows of resampling steps add to it, so the bytes
+# per filter follow the resampling rate of the sampler's population.
+TRAFFIC_PER_FILTER = {("lg4", 1024, 250): (2755.332e6 + 1.253e6 + 2815.374e6 + 0.304e6 +
+                                           2752.610e6 + 1.293e6 + 2815.872e6 + 0.166e6) / 1024,
                       ("sv", 2048, 500): (1.823e6 + 1552.773e6 + 1612.209e6 + 0.372e6) / 304,
-                      ("lg16", 1024, 200): (1.002e6 + 2313.026e6 + 2190.548e6 + 2.515e6) / 152}
+                      ("lg16", 1024, 200): (14705.495e6 + 6.959e6 + 14755.096e6 + 19.128e6 +
+                                            14702.515e6 + 5.834e6 + 14756.709e6 + 19.663e6) / 2048}
 
 
 def _args():
