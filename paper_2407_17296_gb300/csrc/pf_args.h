@@ -85,7 +85,7 @@ SMC2_HD constexpr bool gather_walk(int G, int DX) { return G == 1 && (DX == 4 ||
 
 // Slots of the adjoint's shared-memory ring of trajectory slices: the model shape's preferred
 // count when its plan fits kSmemLimit, else its fallback (0: no ring, slices read from memory).
-SMC2_HD constexpr int ring_preferred(int DX) { return DX >= 16 ? 3 : (DX == 4 ? 5 : 8); }
+SMC2_HD constexpr int ring_preferred(int DX) { return DX >= 16 ? 3 : (DX == 4 ? 3 : 8); }
 SMC2_HD constexpr int ring_fallback(int DX) { return DX >= 16 ? 0 : (DX >= 4 ? 2 : 4); }
 
 // The forward pass draws a step's normals in a rolled loop into shared memory (one float4 of
