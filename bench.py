@@ -48,7 +48,8 @@ ALG_OPS_STRICT = {"lg1": 33 + 14, "lg4": 94 + 47, "sv": 36 + 15, "lg16": 333 + 1
 # dram__bytes_write.sum from ncu (one pass, no replay) over the four filter launches of the
 # second SMC2 iteration of the benchmark command itself (two halves, each a forward and an
 # adjoint launch) for the 4-d workload (N = 1024, M = 1024, T = 250; forward 8 particles a
-# thread at 128 registers, adjoint 4 at 128) and the 16-d workload (N = 2048, M = 1024,
+# thread at 128 registers, adjoint 4 at 128; with the adjoint at 80 registers the same
+# iteration moves 11.145 GB, the same bytes) and the 16-d workload (N = 2048, M = 1024,
 # T = 200; 8 at 128 both), divided by N; for SV (M = 2048, T = 500; forward 8 at 64, adjoint 8
 # at 128) from a capture of 304 filters.  Every step's slice is stored and read back once;
 # the log-weights, tape and first-offspring rows of resampling steps add to it, so the bytes
