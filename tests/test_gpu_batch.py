@@ -20,6 +20,7 @@ def _jobs():
         (replace(W.lg1(T=20, N=30, M=128, K=3), seed=99), {}),
         (W.sv(T=40, N=24, M=128, K=3), {}),
         (replace(W.lg1(T=30, N=32, M=128, K=3, proposal="hmc"), hmc_steps=2, gamma=0.1), {}),
+        (replace(W.lg1(T=30, N=24, M=128, K=3, proposal="nuts"), nuts_depth=2, gamma=0.1), {}),
         (W.lgssm(T=60, N=32, M=250, K=3), {}),         # optimal proposal, uniform priors
         (replace(W.lgssm(T=45, N=20, M=250, K=3, proposal="rw"), seed=31), {}),
     ]
@@ -47,8 +48,8 @@ def test_batch_step_equals_each_job_alone():
                 stats = b.step(hs)
                 # proposal + update of every job; one fused forward and adjoint launch per group of
                 # several jobs (lg4 at 128 threads, lg1, lgssm); sv alone in its group and the HMC
-                # job after its first iteration step on their own
-                assert binding.kernel_launches() - n0 >= 5 * (len(hs) - 1) + 2 * 3
+                # and NUTS jobs after their first iteration step on their own
+                assert binding.kernel_launches() - n0 >= 5 * (len(hs) - 2) + 2 * 3
                 for i, h in enumerate(hs):
                     st_ref, (th_ref, lw_ref) = ref[i][k]
                     th, lw = h.samples()

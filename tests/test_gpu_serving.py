@@ -12,7 +12,7 @@ pytestmark = pytest.mark.gpu
 
 
 # jobs whose filters resample with the multinomial scheme (the paper's, Sec. II-B)
-MULTINOMIAL_JOBS = (6, 7)
+MULTINOMIAL_JOBS = (7, 8)
 
 
 def _jobs():
@@ -21,6 +21,7 @@ def _jobs():
             W.sv(T=60, N=48, M=128, K=4), W.lg16(T=20, N=16, M=128, K=2),
             W.lg4(T=30, N=64, M=100, K=2, proposal="rw"),
             replace(W.lg1(T=50, N=64, M=128, K=3, proposal="hmc"), hmc_steps=2, gamma=0.1),
+            replace(W.lg1(T=40, N=32, M=128, K=3, proposal="nuts"), nuts_depth=2, gamma=0.1),
             W.lg4(T=40, N=32, M=256, K=3), W.sv(T=60, N=48, M=128, K=3)]
 
 
