@@ -59,13 +59,11 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, const PhiloxKey& key) {
     return c;
 }
 
-// Uniforms are built from bits: a plain int-to-float conversion runs on the narrow
-// FP64/conversion pipe of this GPU.
-// k * 2^-24 for an integer k in [0, 2^24], exactly: f = 2^23 + (k >> 1) has exponent 23,
-// so f * 2^-23 - 1 + (k & 1) * 2^-24 = k * 2^-24 (one fused multiply-add, exact result).
+// k * 2^-24 for an integer k in [0, 2^24], exactly: k converts to FP32 without rounding (24
+// significant bits at most) and the power-of-two scale is exact.  (The conversion measured
+// cheaper here than building the float from bits: 2-3% on the filter forward passes.)
 __device__ __forceinline__ float exact_u24_scaled(uint32_t k) {
-    const float f = __uint_as_float(0x4b000000u | (k >> 1));
-    return fmaf(f, 1.1920928955078125e-07f, (k & 1u) ? -0.99999994039535522461f : -1.0f);
+    return __uint2float_rn(k) * 5.9604644775390625e-08f;
 }
 
 __device__ __forceinline__ float u01_open(uint32_t u) {   // (0, 1]
