@@ -68,25 +68,15 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// floor(w * 2^40) for w in [0, 1], from the float's bits with integer operations only
-// (conversions between floats and 64-bit integers run on the narrow FP64 pipe) and no
-// branches: w = m * 2^(e - 150) with m the 24-bit significand, so w * 2^40 is
-// (m * 2^17) >> (127 - e); zero and denormal weights shift out all 41 bits.
+// floor(w * 2^40) for w in [0, 1]: the power-of-two scaling is exact, so the conversion
+// rounded toward zero is the floor (zero and denormal weights give 0).  (Building it from the
+// float's bits with integer operations, the earlier form, measured slower; same values.)
 __device__ __forceinline__ unsigned long long fixed40(float w) {
-    const uint32_t b = __float_as_uint(w);
-    const uint32_t e = min((b >> 23) & 0xffu, 127u);
-    const unsigned long long m = (unsigned long long)((b & 0x7fffffu) | 0x800000u) << 17;
-    return m >> min(127u - e, 63u);
+    return __float2ull_rz(w * 1099511627776.0f);
 }
 
-// S as a float, rounded toward zero (monotone in S), with integer operations only.
-__device__ __forceinline__ float u64_to_float_rz(unsigned long long S) {
-    const int lz = __clzll((long long)S);                   // 64 for S = 0
-    const uint32_t m = (uint32_t)((S << (lz & 63)) >> 40);  // leading 24 bits, top bit set
-    const uint32_t E = (uint32_t)(63 - lz);                 // S ~ m * 2^(E - 23)
-    const float f = __uint_as_float(((E + 127u) << 23) | (m & 0x7fffffu));
-    return S ? f : 0.f;
-}
+// S as a float, rounded toward zero (monotone in S).
+__device__ __forceinline__ float u64_to_float_rz(unsigned long long S) { return __ull2float_rz(S); }
 
 // min(max(floor(c) + 1, 0), M) for |c| < 2^22: the addition of 1.5 * 2^23 rounded down
 // leaves floor(c) in the low bits of the sum.
