@@ -338,10 +338,19 @@ __device__ __forceinline__ void multinomial_ancestors(const float (&lw)[P], bool
         if (lead && j < M) cs[j] = (j == M - 1) ? 1.0f : u64_to_float_rz(base + s[p]) * inv;
     }
     __syncthreads();
+    uint4 w4 = make_uint4(0u, 0u, 0u, 0u);  // the call of particles i .. i+3 (i % 4 == 0)
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         const int i = j0 + p;
-        const uint4 w = philox4x32_10(make_uint4(t, (uint32_t)i >> 2, kStreamResample, 0u), key);
+        // particle i's uniform is word i % 4 of call i / 4: with P a multiple of 4 (so j0 is
+        // too) a thread's particles fill whole calls and draw each call once
+        uint4 w;
+        if constexpr (P % 4 == 0) {
+            if (p % 4 == 0) w4 = philox4x32_10(make_uint4(t, (uint32_t)i >> 2, kStreamResample, 0u), key);
+            w = w4;
+        } else {
+            w = philox4x32_10(make_uint4(t, (uint32_t)i >> 2, kStreamResample, 0u), key);
+        }
         const uint32_t lanew = i & 3;
         const uint32_t u = lanew == 0 ? w.x : lanew == 1 ? w.y : lanew == 2 ? w.z : w.w;
         const float nu = u01_open(u);
