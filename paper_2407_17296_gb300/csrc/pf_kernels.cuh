@@ -321,7 +321,8 @@ __device__ __forceinline__ void systematic_ancestors(const float (&lw)[P], bool 
 }
 
 // Multinomial ancestors (the paper's scheme, App. B): one uniform nu_i per particle,
-// a_i = min{j : c_j >= nu_i} by binary search over the cumulative weights.  Two __syncthreads.
+// a_i = min{j : c_j >= nu_i} by a lower-bound search over the cumulative weights.  Two
+// __syncthreads.
 // With COUNT, nties grows by the thresholds nu_i of this thread that lie within kNearTieBand
 // of a cumulative weight next to the chosen index (c_a - nu_i < band or nu_i - c_{a-1} <= band).
 template <int P, int G, bool COUNT>
@@ -338,32 +339,46 @@ __device__ __forceinline__ void multinomial_ancestors(const float (&lw)[P], bool
         if (lead && j < M) cs[j] = (j == M - 1) ? 1.0f : u64_to_float_rz(base + s[p]) * inv;
     }
     __syncthreads();
-    uint4 w4 = make_uint4(0u, 0u, 0u, 0u);  // the call of particles i .. i+3 (i % 4 == 0)
+    // the thresholds of the thread's particles (particle i's uniform is word i % 4 of call
+    // i / 4: with P a multiple of 4, so j0 is too, a thread's particles fill whole calls and
+    // draw each call once)
+    float nu[P];
+    {
+        uint4 w4 = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const int i = j0 + p;
+            uint4 w;
+            if constexpr (P % 4 == 0) {
+                if (p % 4 == 0) w4 = philox4x32_10(make_uint4(t, (uint32_t)i >> 2, kStreamResample, 0u), key);
+                w = w4;
+            } else {
+                w = philox4x32_10(make_uint4(t, (uint32_t)i >> 2, kStreamResample, 0u), key);
+            }
+            const uint32_t lanew = i & 3;
+            nu[p] = u01_open(lanew == 0 ? w.x : lanew == 1 ? w.y : lanew == 2 ? w.z : w.w);
+        }
+    }
+    // a_i = min{j : c_j >= nu_i}: a lower-bound search of all the thread's thresholds at once
+    // (the same number of halving steps for every thread, P independent loads a step); the
+    // invariant is that every j < lo has c_j < nu, and c_{M-1} = 1 is never probed
+    int lo[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) lo[p] = 0;
+    for (int step = 1 << (31 - __clz(max(M - 1, 1))); step > 0; step >>= 1) {
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const int probe = lo[p] + step - 1;
+            if (probe < M - 1 && cs[probe] < nu[p]) lo[p] += step;
+        }
+    }
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         const int i = j0 + p;
-        // particle i's uniform is word i % 4 of call i / 4: with P a multiple of 4 (so j0 is
-        // too) a thread's particles fill whole calls and draw each call once
-        uint4 w;
-        if constexpr (P % 4 == 0) {
-            if (p % 4 == 0) w4 = philox4x32_10(make_uint4(t, (uint32_t)i >> 2, kStreamResample, 0u), key);
-            w = w4;
-        } else {
-            w = philox4x32_10(make_uint4(t, (uint32_t)i >> 2, kStreamResample, 0u), key);
-        }
-        const uint32_t lanew = i & 3;
-        const uint32_t u = lanew == 0 ? w.x : lanew == 1 ? w.y : lanew == 2 ? w.z : w.w;
-        const float nu = u01_open(u);
-        int lo = 0, hi = M - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (cs[mid] >= nu) hi = mid;
-            else lo = mid + 1;
-        }
-        anc[p] = lo;
+        anc[p] = lo[p];
         if constexpr (COUNT) {
             if (lead && i < M &&
-                (cs[lo] - nu < kNearTieBand || (lo > 0 && nu - cs[lo - 1] <= kNearTieBand)))
+                (cs[lo[p]] - nu[p] < kNearTieBand || (lo[p] > 0 && nu[p] - cs[lo[p] - 1] <= kNearTieBand)))
                 ++nties;
         }
     }
