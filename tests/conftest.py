@@ -22,19 +22,14 @@ def gpu_lib():
 
 def pytest_sessionfinish(session, exitstatus):
     """Write the near-tie counts of the GPU parity tests that ran (tests/parity.py TIE_REPORT)
-    to $SMC2_TIE_REPORT, or to gpurun_out/parity_near_ties.json when that folder exists."""
+    as JSON to the file $SMC2_TIE_REPORT names (nothing is written when it is unset)."""
     import json
     try:
         from tests.parity import TIE_REPORT
     except ImportError:
         return
-    if not TIE_REPORT:
-        return
     path = os.environ.get("SMC2_TIE_REPORT")
-    if not path:
-        out = os.path.join(ROOT, "gpurun_out")
-        if not os.path.isdir(out):
-            return
-        path = os.path.join(out, "parity_near_ties.json")
+    if not TIE_REPORT or not path:
+        return
     with open(path, "w") as f:
         json.dump(TIE_REPORT, f, indent=1, sort_keys=True)

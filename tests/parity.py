@@ -44,7 +44,7 @@ def gpu_pf(w, theta, iteration=1, row0=0, want_grad=True, **cfgkw):
 
 
 # near-tie counts of every check_rows call with a name, written at the end of the session
-# (conftest.py) so that a record of them exists beside the pass/fail verdict
+# (conftest.py) so that a record of them exists beside the pass/fail result
 TIE_REPORT = {}
 
 
