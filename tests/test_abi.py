@@ -158,3 +158,25 @@ def test_batch_entry_points_validate_without_device_work(lib):
     assert lib.smc2_batch_destroy(None) == -1
     assert lib.smc2_batch_step(None, None, 1, None) == -1
     assert lib.smc2_server_set_fused(None, 1) == -1
+
+
+@pytest.mark.parametrize("depth,weight,code", [(0, 0, -1), (7, 0, -1), (1, 0, 0), (3, 1, 0), (6, 0, 0),
+                                               (3, 2, -1), (3, -1, -1)])
+def test_nuts_fields_are_validated(lib, depth, weight, code):
+    """The NUTS proposal takes 1..6 doublings and one of its two L-kernels; the footprint grows
+    by the per-sample trajectory state ((16 + 2J) D + 9 doubles and the trace)."""
+    from paper_2407_17296_gb300 import binding
+    c = _cfg(proposal=binding.NUTS, nuts_max_depth=depth, nuts_weight=weight)
+    b = ctypes.c_size_t(0)
+    assert lib.smc2_footprint(ctypes.byref(c), ctypes.byref(b)) == code
+    if code == 0:
+        b0 = ctypes.c_size_t(0)
+        assert lib.smc2_footprint(ctypes.byref(_cfg(proposal=binding.LANGEVIN)), ctypes.byref(b0)) == 0
+        assert b.value > b0.value
+
+
+def test_nuts_trace_and_point_trace_validate_arguments(lib):
+    """The verification calls refuse a NULL handle without any device work."""
+    assert lib.smc2_get_nuts_trace(None, None, None, None, None) == -1
+    assert lib.smc2_set_point_trace(None, 1) == -1
+    assert lib.smc2_get_point_trace(None, 0, None, None) == -1
