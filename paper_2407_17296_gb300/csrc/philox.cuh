@@ -69,20 +69,21 @@ __device__ __forceinline__ float exact_u24_scaled(uint32_t k) {
 __device__ __forceinline__ float u01_open(uint32_t u) {   // (0, 1]
     return exact_u24_scaled((u >> 8) + 1u);
 }
-__device__ __forceinline__ float u01_half(uint32_t u) {   // [0, 1)
-    return exact_u24_scaled(u >> 8);
-}
 
 // One Box-Muller pair from two words.  The angle is evaluated as
 // phi' = 2 pi (U[0,1) - 1/2) in [-pi, pi), where the hardware sine/cosine are accurate
 // (absolute error ~2^-21), and cos(phi') = -cos(2 pi U), sin(phi') = -sin(2 pi U) restore
 // the definition.  The radius keeps the accurate logf (a hardware base-2 logarithm, ~2^-22
 // absolute, moved cumulative weights of 128-particle filters by more than 1e-6 through the
-// normals it perturbs); sqrt(s) = s * rsqrt(s) with s = 0 (the uniform equal to 1) mapped to 0.
+// normals it perturbs); sqrt(s) = s * rsqrt(s), with rsqrt's argument raised to the smallest
+// normal float so that s = 0 (the uniform equal to 1) gives 0 (every other s is at least
+// 2^-23).  The angle folds U[0,1)'s scale 2^-24 into the constant: (k 2^-24) (2 pi) and
+// k (2 pi 2^-24) are the same exact product, so the fused multiply-add rounds the same value.
 __device__ __forceinline__ void box_muller(uint32_t ua, uint32_t ub, float& z0, float& z1) {
+    constexpr float kTwoPi = 6.2831853071795864769f;
     const float s = -2.0f * logf(u01_open(ua));
-    const float r = (s > 0.f) ? s * rsqrtf(s) : 0.f;
-    const float ph = fmaf(u01_half(ub), 6.2831853071795864769f, -3.1415926535897932385f);
+    const float r = s * rsqrtf(fmaxf(s, 1.17549435e-38f));
+    const float ph = fmaf(__uint2float_rn(ub >> 8), kTwoPi * 5.9604644775390625e-08f, -3.1415926535897932385f);
     float sn, cs;
     __sincosf(ph, &sn, &cs);
     z0 = -r * cs;
